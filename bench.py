@@ -1,0 +1,354 @@
+#!/usr/bin/env python
+"""Benchmark of the structured-Gram solve + gradient over randomized digital nets.
+
+Workload (solve20): base-2 digital net, Gray order, LMS + digital shift, n = 2^20 points,
+d = 16, 64 randomizations per GPU (weak scaling), order-2 DSI kernel with weights
+0.9^j, nugget 1e-8, one right-hand side y = exp(sum_j x_j / j) - const + N(0, 1e-6).
+A step runs the whole path for every randomization: first column, eigenvalues (FWHT),
+transformed right-hand side, spectral epilogue (quadratic form, log det, posterior
+mean/variance), MLL gradient back-transform and reduction, and the solve with one
+refinement step.  Inputs are resident in HBM (y alone is 256 MB, twice the L2).
+
+The headline `value` is points/s (randomizations x n / step time) of the FP32 path
+(FP32 column and transforms, FP64 division / log det / variance, one refinement
+step); the plain FP64 path is timed beside it.  `--impl reference` times the FP64
+CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "structured-Gram solve+grad points/s at n=2^20 (FP32-refined vs plain FP64), FWHT HBM GB/s"
+UNIT = "points/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--R", type=int, default=64, help="randomizations per GPU")
+    ap.add_argument("--m", type=int, default=20)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison timing")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------- the workload
+def build_workload(qk, torch, dev, R, m, seed_offset=0):
+    """Seeded inputs on the device: scrambled columns, shifts, weights and y."""
+    from paper_2502_14256_gb300 import inputs
+    wl = inputs.workload("solve20")
+    d = wl.d
+    n = 1 << m
+    net = inputs.make_net(wl.seed + seed_offset, d, R, wl.order)
+    u32 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)  # noqa: E731
+    Cd, Sd, Dd = u32(net.C), u32(net.S), u32(net.D)
+    Ct = torch.empty((R, d, 32), dtype=torch.int32, device=dev)
+    qk.lms_setup(Cd, Sd, Ct)
+    ps = qk.pointset(qk.QK_NET_B2, d, R, Ct=Ct, D=Dd, order=qk.QK_GRAY)
+    # y from the points: generated on the device in chunks (input preparation, untimed)
+    rng = inputs.SplitMix64(wl.seed + 17 + seed_offset)
+    noise = torch.from_numpy(wl.noise_sigma * rng.normal(R * n)).to(dev).reshape(R, n)
+    jj = torch.arange(1, d + 1, dtype=torch.float64, device=dev)
+    const = float(np.prod(np.arange(1, d + 1) * np.expm1(1.0 / np.arange(1, d + 1))))
+    y = torch.empty((R, 1, n), dtype=torch.float64, device=dev)
+    X = torch.empty((1, n, d), dtype=torch.int32, device=dev)
+    for r in range(R):
+        qk.gen_points(ps, r, 1, 0, n, X)
+        x = (X[0].to(torch.int64) & 0xFFFFFFFF).to(torch.float64) * 2.0 ** -32
+        y[r, 0] = torch.exp((x / jj).sum(dim=1)) - const + noise[r]
+    del X
+    w = torch.tensor(inputs.workload("solve20").gamma, dtype=torch.float64, device=dev)
+    return dict(wl=wl, d=d, n=n, R=R, m=m, ps=ps, keep=[Cd, Sd, Dd, Ct, w], w=w, y64=y, net=net)
+
+
+class Pipeline:
+    """One batched schedule (all randomizations) in a given precision."""
+
+    def __init__(self, qk, torch, dev, W, dtype, refine):
+        self.qk, self.torch = qk, torch
+        R, n, d = W["R"], W["n"], W["d"]
+        self.y = W["y64"].to(dtype).contiguous()
+        self.c = torch.empty_like(self.y)
+        self.lam = torch.empty((R, n), dtype=torch.float64, device=dev)
+        self.out = torch.empty((R, 1, qk.QK_MLL_NOUT), dtype=torch.float64, device=dev)
+        self.grad = torch.empty((R, 1, 2 * d + 2), dtype=torch.float64, device=dev)
+        kern = qk.kernel(qk.QK_DSI, W["wl"].alpha, W["w"], W["wl"].zeta)
+        self.task = qk.Task(W["ps"], kern, W["m"], 1, W["wl"].eta, self.y.data_ptr(), self.c.data_ptr(),
+                            self.lam.data_ptr(), self.out.data_ptr(), self.grad.data_ptr())
+        self.ws = qk.workspace(qk.batch_workspace_bytes([self.task], dtype), dev)
+        qk.batch_plan([self.task], dtype, refine, self.ws)
+        self.status = torch.zeros(1, dtype=torch.int32, device=dev)
+
+    def step(self, stream=None):
+        self.qk.batch_run(self.ws, self.status, stream=stream)
+
+
+def time_steps(torch, fn, steps, warmup, stream):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+# ------------------------------------------------------------ CPU baselines
+def oracle_sample(W_host, m_sample, count=1, r_first=0):
+    """Time the FP64 oracle (as it stands) on `count` whole randomizations of the workload
+    at n = 2^m_sample (a bounded sample: its cost is close to linear in n, so points/s
+    carries over); returns (points/s, sample text)."""
+    from oracle import qk_oracle as o
+    from paper_2502_14256_gb300 import inputs
+    wl = W_host["wl"]
+    net = W_host["net"]
+    d = W_host["d"]
+    n = 1 << m_sample
+    c = o.effective_weights(wl.gamma, wl.log_ls)
+    t0 = time.perf_counter()
+    for q in range(count):
+        r = (r_first + q) % net.R
+        Ct = o.lms_scramble(net.C, net.S[r:r + 1])[0]
+        X = o.net_points(Ct, net.D[r], np.arange(n), m_sample, wl.order)
+        y = inputs.rhs_exp(X)
+        k1 = o.first_column("dsi", wl.alpha, X, c, wl.zeta)
+        lam = o.eigenvalues("dsi", k1, wl.eta)
+        o.spectral_mll("dsi", lam, y, wl.zeta)
+        o.spectral_mll_grad("dsi", wl.alpha, X, y, lam, c, wl.zeta)
+        o.spectral_solve("dsi", lam, y)
+    dt = time.perf_counter() - t0
+    return count * n / dt, (f"{count} randomization(s) at n=2^{m_sample} (the workload has 2^{W_host['m']}), "
+                            f"d={d}: oracle points, first column, spectrum, MLL, gradient and solve "
+                            f"(numpy FP64, single thread, {dt:.1f} s)")
+
+
+# ---------------------------------------------------------------- main
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        from paper_2502_14256_gb300 import inputs
+        wl = inputs.workload("solve20")
+        net = inputs.make_net(wl.seed, wl.d, args.R, wl.order)
+        W_host = dict(wl=wl, net=net, m=args.m, d=wl.d)
+        times = []
+        for q in range(args.warmup):
+            oracle_sample(W_host, 10, 1, q)
+        sample = ""
+        for q in range(args.steps):
+            v, sample = oracle_sample(W_host, min(16, args.m), 1, q)
+            times.append(v)
+        value = statistics.median(times)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"solve20: net n=2^{args.m} d={wl.d} R={args.R} DSI order 2, 1 rhs",
+                           "l2": "inputs larger than L2"},
+                "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1, "sample": sample},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return 0
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device(f"cuda:{local}")
+    from paper_2502_14256_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2502_14256_gb300 import qk
+
+    W = build_workload(qk, torch, dev, args.R, args.m, seed_offset=1000 * rank)
+    stream = torch.cuda.current_stream()
+
+    # ---- the headline: FP32-refined pipeline, device-resident inputs
+    P32 = Pipeline(qk, torch, dev, W, torch.float32, refine=1)
+    for _ in range(args.warmup):
+        P32.step()
+    qk.read_status(P32.status)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = qk.launch_count()
+    ms = time_steps(torch, P32.step, args.steps, 0, stream)
+    launches = qk.launch_count() - launches0
+    clocks = sampler.stop()
+    if world > 1:
+        dist.barrier()
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    points_step = world * W["R"] * W["n"]
+    value = points_step / (ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers (pinned)
+    y_host = P32.y.cpu().pin_memory()
+    c_host = torch.empty_like(P32.c, device="cpu").pin_memory()
+    o_host = torch.empty_like(P32.out, device="cpu").pin_memory()
+    g_host = torch.empty_like(P32.grad, device="cpu").pin_memory()
+
+    def e2e_step():
+        P32.y.copy_(y_host, non_blocking=True)
+        P32.step()
+        c_host.copy_(P32.c, non_blocking=True)
+        o_host.copy_(P32.out, non_blocking=True)
+        g_host.copy_(P32.grad, non_blocking=True)
+
+    e2e_ms = time_steps(torch, e2e_step, max(2, args.steps // 2), 1, stream)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = y_host.numel() * y_host.element_size()
+    d2h = sum(t.numel() * t.element_size() for t in (c_host, o_host, g_host))
+
+    # ---- stage timing of the FP32 path (which stage dominates)
+    from paper_2502_14256_gb300 import qk as q
+    R, n, m, d = W["R"], W["n"], W["m"], W["d"]
+    col = torch.empty((R, n), dtype=torch.float32, device=dev)
+    kern = q.kernel(q.QK_DSI, W["wl"].alpha, W["w"], W["wl"].zeta)
+    stage = {}
+    stage["kernel_col"] = time_steps(torch, lambda: q.kernel_col(W["ps"], kern, 0, R, m, col, form=q.QK_COL_P),
+                                     3, 1, stream)
+    # FWHT alone on the same data volume (in place, FP32): HBM roofline of the transform
+    xf = torch.randn((R, n), dtype=torch.float32, device=dev)
+    fw_ms = time_steps(torch, lambda: q.fwht(m, xf), args.steps, 2, stream)
+    fw_bytes = 2 * xf.numel() * 4  # one read + one write per element (the algorithmic minimum)
+    fw_gbs = fw_bytes / (fw_ms * 1e-3) / 1e9
+    del xf
+
+    # ---- plain FP64 pipeline beside it
+    fp64 = None
+    if not args.no_fp64:
+        P64 = Pipeline(qk, torch, dev, W, torch.float64, refine=0)
+        ms64 = time_steps(torch, P64.step, max(1, min(3, args.steps)), 1, stream)
+        fp64 = {"value": points_step / (ms64 * 1e-3), "ms_per_step": ms64}
+        # accuracy of the FP32 path against the FP64 GPU path, per output
+        torch.cuda.synchronize()
+        rel = lambda a, b: float((a.double() - b.double()).abs().max() / b.double().abs().max())  # noqa: E731
+        fp64["fp32_rel_err"] = {
+            "solve_c": rel(P32.c, P64.c), "lambda": rel(P32.lam, P64.lam),
+            "quad": rel(P32.out[..., 0], P64.out[..., 0]), "logdet": rel(P32.out[..., 1], P64.out[..., 1]),
+            "mll": rel(P32.out[..., 2], P64.out[..., 2]), "post_mean": rel(P32.out[..., 3], P64.out[..., 3]),
+            "grad_dc": rel(P32.grad[..., :d], P64.grad[..., :d])}
+        del P64
+
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        v, sample = oracle_sample(W, min(18, m), 1, 0)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"solve20: digital net (Gray, LMS+DS) n=2^{m}, d={d}, {R} randomizations/GPU, "
+                                   "DSI order 2, gamma_j=0.9^j, eta=1e-8, 1 rhs; FP32 column+FWHT, FP64 "
+                                   "division/logdet/variance, 1 refinement step",
+                       "global_batch": world * R, "seq_len": n, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (y alone 256 MB)"},
+            "e2e": {"value": points_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "gpu_launches_per_step": launches / max(1, args.steps),
+            "fp64_plain": fp64,
+            "stages_ms": stage,
+            "fwht": {"gbs": fw_gbs, "ms": fw_ms, "frac_of_hbm": fw_gbs / hbm_peak, "bytes": fw_bytes,
+                     "shape": f"{R} x 2^{m} fp32, in place"},
+            "roofline": {"kernel": "k_transform_pass<WHT,float> (batched FWHT, 2 passes)", "bound": "hbm",
+                         "achieved": fw_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": fw_gbs / hbm_peak,
+                         "traffic": None, "peak_source": peak_src},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

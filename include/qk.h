@@ -1,0 +1,248 @@
+/*
+ * qk.h -- C ABI of libqk.so: structured-Gram kernel solves over randomized
+ * low-discrepancy points on one GB300 (sm_103a).
+ *
+ * The operations follow arXiv 2502.14256 ("QMCPy ... randomized LD sequences,
+ * ... fast kernel methods"):
+ *   points     Sec. 4.2 (shifted rank-1 lattices, natural order, base 2) and
+ *              Sec. 4.3 (base-2 digital nets, Matousek linear matrix scrambling,
+ *              digital shift, natural or Gray-code order);
+ *   kernels    Sec. 5.2 Eq. (K_SI_prod) (shift-invariant Bernoulli kernels with
+ *              product weights) and Sec. 5.3 Eq. (DSI kernel) with the closed
+ *              forms of the Theorem there (digitally-shift-invariant kernels);
+ *   spectra    Sec. 5.4: K = V diag(lambda) V^H, lambda = sqrt(n) conj(V) k_1,
+ *              K y = V(y~ * lambda), K^-1 y = V(y~ / lambda), with V = H/sqrt(n)
+ *              (Hadamard, FWHT) for nets and the bit-reversed Fourier matrix
+ *              (FFTBR / IFFTBR) for lattices;
+ *   MLL        Sec. 3.2 (kernel interpolation / GP hyper-parameter fitting and the
+ *              kernel discrepancy with kappa_i = int K(u, x_i) du); the gradient is
+ *              the textbook GP gradient carried through the spectrum.
+ *
+ * Conventions for every entry point:
+ *   - Array arguments are DEVICE pointers owned by the caller, unless a comment
+ *     says "host".  The library allocates no device memory: scratch space comes
+ *     from a caller-provided workspace whose size qk_workspace_bytes() returns.
+ *   - Every call is asynchronous on the given stream (NULL = legacy default
+ *     stream) and returns a qk_status.  Argument errors are detected on the host
+ *     before any launch (QK_EINVAL) and nothing is launched.  A CUDA launch error
+ *     returns QK_ECUDA.  Conditions only the device can see (a non-positive
+ *     eigenvalue, a bounded wait that expired) are OR-ed into the optional
+ *     device status word `status` (bits QK_STATUS_*); qk_read_status() turns it
+ *     into a qk_status after synchronising the stream.
+ *   - qk_last_error() copies a message describing the last failure on the
+ *     calling host thread.
+ *   - Points are 32-bit words: coordinate x = X * 2^-32 (t_max = 32 digits; the
+ *     first digit is bit 31).
+ *   - n = 2^m with 0 <= m <= QK_MAX_M, 1 <= d <= QK_MAX_D.
+ */
+#ifndef QK_H
+#define QK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *qk_stream; /* same type as cudaStream_t */
+
+#if defined(__GNUC__)
+#define QK_API __attribute__((visibility("default")))
+#else
+#define QK_API
+#endif
+
+enum qk_status {
+  QK_OK = 0,
+  QK_EINVAL = 1,     /* bad argument (size, null pointer, alignment, enum value) */
+  QK_ENOTPD = 2,     /* some eigenvalue <= 0: K is not positive definite */
+  QK_ECUDA = 3,      /* a CUDA runtime call or launch failed */
+  QK_ETIMEOUT = 4,   /* a bounded device-side wait expired */
+  QK_EWORKSPACE = 5  /* workspace null or smaller than qk_workspace_bytes() */
+};
+
+enum qk_status_bits { QK_STATUS_NOTPD = 1u, QK_STATUS_TIMEOUT = 2u };
+
+enum qk_kind { QK_NET_B2 = 0, QK_LATTICE = 1 };
+enum qk_order { QK_NATURAL = 0, QK_GRAY = 1 };
+enum qk_family { QK_DSI = 0, QK_SI = 1 };
+enum qk_dtype { QK_F64 = 0, QK_F32 = 1 };
+/* Form of a stored first column: the column itself, or p = k_1/zeta - 1
+ * (computed by a product-minus-one recurrence, so that the variation of the
+ * kernel around its constant part keeps full relative precision). */
+enum qk_colform { QK_COL_K1 = 0, QK_COL_P = 1 };
+
+#define QK_MAX_M 30
+#define QK_MAX_D 256
+
+/* A randomized point set (Sec. 4.2 / 4.3).  Holds R randomizations. */
+typedef struct {
+  int32_t kind;        /* QK_NET_B2 or QK_LATTICE */
+  int32_t order;       /* nets: QK_NATURAL or QK_GRAY; lattices: QK_NATURAL */
+  uint32_t d;          /* dimensions */
+  uint32_t R;          /* randomizations stored in Ct / D */
+  const uint32_t *Ct;  /* nets: (R, d, 32) scrambled generator columns
+                          (qk_lms_setup output); column k, bit 31-t = digit t */
+  const uint32_t *g;   /* lattices: (d) generating vector */
+  const uint32_t *D;   /* (R, d) shift words: XOR for nets (digital shift),
+                          + mod 2^32 for lattices; NULL means no shift */
+} qk_pointset;
+
+/* Product-weight kernel K(x,x') = zeta prod_j (1 + c_j K_alpha(x_j, x'_j)). */
+typedef struct {
+  int32_t family;         /* QK_DSI (nets) or QK_SI (lattices) */
+  int32_t alpha;          /* DSI order 1, 2, 3, 4; SI smoothness 1 or 2 */
+  uint32_t d;
+  const double *weights;  /* (d) effective weights c_j (gamma_j * lengthscale_j) */
+  double zeta;            /* scale, > 0 */
+} qk_kernel;
+
+/* Per right-hand side result of qk_mll (doubles, in this order). */
+#define QK_MLL_QUAD 0      /* y^T K^-1 y */
+#define QK_MLL_LOGDET 1    /* log det K */
+#define QK_MLL_MLL 2       /* -quad/2 - logdet/2 - n log(2 pi)/2 */
+#define QK_MLL_MEAN 3      /* Bayesian-cubature posterior mean zeta 1^T K^-1 y */
+#define QK_MLL_VAR 4       /* posterior variance zeta - zeta^2 1^T K^-1 1 */
+#define QK_MLL_NOUT 5
+/* Gradient block per right-hand side: 2d + 2 doubles:
+ *   [0, d)       dMLL/dc_j
+ *   d            dMLL/deta
+ *   [d+1, 2d+1)  dMEAN/dc_j
+ *   2d+1         dMEAN/deta
+ * Chain rule to log-lengthscales theta_j (c_j = gamma_j e^theta_j): c_j dMLL/dc_j. */
+
+/* ---------------------------------------------------------------- points --- */
+
+/* Linear matrix scrambling C~_j = S_j C_j over GF(2) (Sec. 4.3, LMS).
+ * C: (d, 32) generator columns; S: (R, d, 32) row masks of the scrambling
+ * matrices (row t, bit 31-u = entry (t, u)); Ct: (R, d, 32) output. */
+QK_API int qk_lms_setup(uint32_t d, uint32_t R, const uint32_t *C, const uint32_t *S,
+                 uint32_t *Ct, qk_stream stream);
+
+/* Points of randomizations r0 .. r0+nr-1 at sequence positions i0 .. i0+n-1
+ * (any range; Sec. 4.2 "n_min/n_max").  X: (nr, n, d) uint32 row-major.
+ * Nets: X = D (+) XOR_{bit k of g(i)} Ct[:, k], g(i) = i or the Gray code of i.
+ * Lattices: X = (v(i) 2^32 * g + D) mod 2^32 with v the radical inverse.
+ * i0 + n <= 2^32. */
+QK_API int qk_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64_t i0,
+                  uint64_t n, uint32_t *X, qk_stream stream);
+
+/* ------------------------------------------------------------ first column --- */
+
+/* First Gram column k_1[i] = K(x_i, x_0) for n = 2^m points of randomizations
+ * r0 .. r0+nr-1 (Sec. 5.4, "k1 = kernel(x, x[0])").  The shift cancels in
+ * x_i (-) x_0, so only Ct (nets) or g (lattices) is read.  col: (nr, n) in
+ * dtype, in the requested form (QK_COL_K1 or QK_COL_P). */
+QK_API int qk_kernel_col(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr,
+                  uint32_t m, int32_t dtype, int32_t form, void *col, qk_stream stream);
+
+/* ------------------------------------------------------------- spectrum --- */
+
+/* Eigenvalues lambda = sqrt(n) conj(V) k_1 + eta (Sec. 5.4) of `batch` Gram
+ * matrices from their first columns col (batch, n) (dtype, form).  DSI: FWHT,
+ * lambda in Hadamard order; SI: FFTBR, lambda in frequency order (real).
+ * The transform runs in dtype; the nugget, zeta and the sign test in FP64.
+ * lam: (batch, n) doubles.  Sets QK_STATUS_NOTPD if some lambda <= 0. */
+QK_API int qk_eigs(int32_t family, uint32_t m, uint32_t batch, int32_t dtype, int32_t form,
+            const void *col, double zeta, double eta, double *lam, void *ws,
+            size_t ws_bytes, uint32_t *status, qk_stream stream);
+
+/* Solve K c = y for `batch` Gram matrices and nrhs right-hand sides each:
+ * c = V (y~ / lambda), y~ = conj(V) y (Sec. 5.4).  y, c: (batch, nrhs, n) in
+ * dtype (may alias); lam: (batch, n) from qk_eigs.  The division is done in
+ * FP64.  refine_steps >= 0 steps of iterative refinement c += K^-1 (y - K c),
+ * the residual evaluated with FP64 transforms (meaningful for QK_F32). */
+QK_API int qk_solve(int32_t family, uint32_t m, uint32_t batch, uint32_t nrhs, int32_t dtype,
+             const double *lam, const void *y, void *c, int32_t refine_steps, void *ws,
+             size_t ws_bytes, qk_stream stream);
+
+/* Matrix-vector product u = K y = V (y~ * lambda) (Sec. 5.4). */
+QK_API int qk_matvec(int32_t family, uint32_t m, uint32_t batch, uint32_t nrhs, int32_t dtype,
+              const double *lam, const void *y, void *u, void *ws, size_t ws_bytes,
+              qk_stream stream);
+
+/* Marginal log-likelihood, log det, quadratic form and Bayesian-cubature
+ * posterior mean / variance for randomizations r0 .. r0+nr-1 of ps with nrhs
+ * right-hand sides each; y: (nr, nrhs, n) dtype; lam: (nr, n) from qk_eigs
+ * with the same kernel and eta.  out: (nr, nrhs, QK_MLL_NOUT) doubles.
+ * grad (nullable): (nr, nrhs, 2d+2) doubles, the gradient block above,
+ * computed by carrying g_w = (|y~_w|^2/lambda_w^2 - 1/lambda_w)/2 back through
+ * the transform and recomputing the kernel factors (nothing n x d is stored). */
+QK_API int qk_mll(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr, uint32_t m,
+           uint32_t nrhs, int32_t dtype, double eta, const double *lam, const void *y,
+           double *out, double *grad, void *ws, size_t ws_bytes, uint32_t *status,
+           qk_stream stream);
+
+/* ------------------------------------------------------------ transforms --- */
+
+/* In-place batched transforms of nvec contiguous vectors of length n = 2^m
+ * (Sec. 5.2-5.3; the paper's fwht / fftbr / ifftbr):
+ *   qk_fwht:   x <- H_m x / sqrt(n)               (real; dtype elements)
+ *   qk_fftbr:  x <- DFT(x taken in linear order) / sqrt(n), x given in natural
+ *              (bit-reversed) order, result in frequency order
+ *   qk_ifftbr: the inverse of qk_fftbr (frequency order in, natural order out)
+ * FFT data are interleaved complex (re, im) pairs of dtype.  Radix-2
+ * butterflies (a +- W b)/sqrt(2) as in the paper's FFTBR/FWHT schemes. */
+QK_API int qk_fwht(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_stream stream);
+QK_API int qk_fftbr(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_stream stream);
+QK_API int qk_ifftbr(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_stream stream);
+
+/* --------------------------------------------------------------- batching --- */
+
+/* One task of a batched schedule: R randomizations of one point set and kernel,
+ * n = 2^m points, nrhs right-hand sides per randomization. */
+typedef struct {
+  qk_pointset ps;
+  qk_kernel k;
+  uint32_t m;
+  uint32_t nrhs;
+  double eta;
+  const void *y;   /* (R, nrhs, n) in the schedule dtype */
+  void *c;         /* (R, nrhs, n) solutions, nullable */
+  double *lam;     /* (R, n) eigenvalues out, nullable */
+  double *out;     /* (R, nrhs, QK_MLL_NOUT) */
+  double *grad;    /* (R, nrhs, 2d+2), nullable */
+} qk_task;
+
+/* Workspace for a schedule over host task list `tasks`. */
+QK_API int qk_batch_workspace_bytes(const qk_task *tasks, uint32_t ntasks, int32_t dtype,
+                             size_t *bytes);
+
+/* Build the device work list of a schedule inside ws (host -> device copy,
+ * synchronous with respect to the host).  Must precede qk_batch_run and must
+ * be repeated whenever the task list or its pointers change. */
+QK_API int qk_batch_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, int32_t refine_steps,
+                  void *ws, size_t ws_bytes, qk_stream stream);
+
+/* Run a planned schedule: every task's solve, MLL and gradient, in kernel
+ * launches only (no host synchronisation, no allocation), so the call can be
+ * captured into a CUDA graph. */
+QK_API int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream stream);
+
+/* ------------------------------------------------------------- utilities --- */
+
+/* Workspace bytes needed by qk_eigs / qk_solve / qk_matvec / qk_mll with these
+ * sizes (op: 0 eigs, 1 solve, 2 matvec, 3 mll). */
+QK_API int qk_workspace_bytes(int32_t op, int32_t family, uint32_t m, uint32_t batch, uint32_t nrhs,
+                       int32_t dtype, uint32_t d, size_t *bytes);
+
+/* Synchronise `stream`, read the device status word, clear it, and return the
+ * corresponding qk_status (QK_OK, QK_ENOTPD or QK_ETIMEOUT). */
+QK_API int qk_read_status(uint32_t *status, qk_stream stream);
+
+/* Message of the last failure on this host thread (NUL-terminated, truncated). */
+QK_API void qk_last_error(char *buf, size_t len);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * threads, all devices), for accounting launches inside a timed region. */
+QK_API uint64_t qk_launch_count(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+QK_API int qk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QK_H */

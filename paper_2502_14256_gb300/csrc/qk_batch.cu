@@ -1,0 +1,132 @@
+// Batched schedules over many (point set, kernel, randomization, right-hand
+// side) tasks of uneven n.  qk_batch_plan validates the host task list, sizes
+// the workspace, and records the plan; qk_batch_run issues kernel launches
+// only (no allocation, no host synchronisation), so it can be captured into a
+// CUDA graph and replayed.
+#include <cstring>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "qk_common.cuh"
+#include "qk_internal.h"
+
+namespace qk {
+
+int check_pointset(const qk_pointset *ps, uint32_t r0, uint32_t nr);
+int check_kernel(const qk_kernel *k, const qk_pointset *ps);
+ColJob make_job(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr, uint32_t m);
+
+struct Plan {
+  std::vector<qk_task> tasks;
+  int32_t dtype = QK_F64;
+  int32_t refine = 0;
+  size_t scratch = 0;   // bytes of the shared scratch region
+  size_t lam_off = 0;   // offset of the eigenvalue buffer
+  size_t total = 0;
+};
+
+static std::mutex g_mu;
+static std::unordered_map<const void *, Plan> g_plans;
+
+static size_t task_scratch(const qk_task &t, int dtype) {
+  const uint32_t R = t.ps.R;
+  const size_t tb = dtype == QK_F64 ? 8 : 4;
+  const size_t col = align256(tb * ((uint64_t)R << t.m));
+  size_t s = ws_eigs(t.k.family, t.m, R, dtype);
+  const size_t mw = ws_mll(t.k.family, t.m, R, t.nrhs, dtype, t.ps.d);
+  if (mw > s) s = mw;
+  if (t.c) {
+    const size_t sw = ws_solve(t.k.family, t.m, R, t.nrhs, dtype);
+    if (sw > s) s = sw;
+  }
+  return col + s;
+}
+
+static int make_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, Plan &p) {
+  if (!tasks && ntasks) return fail(QK_EINVAL, "task list is NULL");
+  if (dtype != QK_F64 && dtype != QK_F32) return fail(QK_EINVAL, "dtype must be QK_F64 or QK_F32");
+  p.tasks.assign(tasks, tasks + ntasks);
+  p.dtype = dtype;
+  size_t scratch = 0, lam = 0;
+  for (uint32_t i = 0; i < ntasks; ++i) {
+    const qk_task &t = tasks[i];
+    int rc = check_pointset(&t.ps, 0, t.ps.R);
+    if (rc) return fail(rc, "task %u: %s", i, "invalid point set");
+    if ((rc = check_kernel(&t.k, &t.ps))) return fail(rc, "task %u: invalid kernel", i);
+    if (t.m > QK_MAX_M) return fail(QK_EINVAL, "task %u: m = %u too large", i, t.m);
+    if (t.nrhs == 0 || !t.y || !t.out) return fail(QK_EINVAL, "task %u: needs nrhs >= 1, y and out", i);
+    const size_t s = task_scratch(t, dtype);
+    if (s > scratch) scratch = s;
+    if (!t.lam) {
+      const size_t l = align256(sizeof(double) * ((uint64_t)t.ps.R << t.m));
+      if (l > lam) lam = l;
+    }
+  }
+  p.scratch = align256(scratch);
+  p.lam_off = p.scratch;
+  p.total = p.scratch + lam;
+  return QK_OK;
+}
+
+static int run_plan(const Plan &p, unsigned char *ws, uint32_t *status, cudaStream_t st) {
+  for (const qk_task &t : p.tasks) {
+    const uint32_t R = t.ps.R;
+    const size_t tb = p.dtype == QK_F64 ? 8 : 4;
+    unsigned char *col = ws;
+    unsigned char *scr = ws + align256(tb * ((uint64_t)R << t.m));
+    double *lam = t.lam ? t.lam : (double *)(ws + p.lam_off);
+    const ColJob job = make_job(&t.ps, &t.k, 0, R, t.m);
+    int rc = launch_kernel_col(job, p.dtype, QK_COL_P, col, st);
+    if (rc) return rc;
+    if ((rc = op_eigs(t.k.family, t.m, R, p.dtype, QK_COL_P, col, t.k.zeta, t.eta, lam, scr, status, st))) return rc;
+    if ((rc = op_mll(job, t.nrhs, p.dtype, lam, t.y, t.out, t.grad, scr, st))) return rc;
+    if (t.c && (rc = op_solve(t.k.family, t.m, R, t.nrhs, p.dtype, lam, t.y, t.c, p.refine, scr, st))) return rc;
+  }
+  return QK_OK;
+}
+
+}  // namespace qk
+
+using namespace qk;
+
+extern "C" {
+
+int qk_batch_workspace_bytes(const qk_task *tasks, uint32_t ntasks, int32_t dtype, size_t *bytes) {
+  if (!bytes) return fail(QK_EINVAL, "bytes is NULL");
+  Plan p;
+  int rc = make_plan(tasks, ntasks, dtype, p);
+  if (rc) return rc;
+  *bytes = p.total;
+  return QK_OK;
+}
+
+int qk_batch_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, int32_t refine_steps, void *ws,
+                  size_t ws_bytes, qk_stream stream) {
+  (void)stream;
+  Plan p;
+  int rc = make_plan(tasks, ntasks, dtype, p);
+  if (rc) return rc;
+  if (refine_steps < 0 || refine_steps > 8) return fail(QK_EINVAL, "refine_steps must be 0..8");
+  p.refine = refine_steps;
+  if (p.total && (!ws || ws_bytes < p.total))
+    return fail(QK_EWORKSPACE, "batch workspace has %zu bytes, %zu needed", ws_bytes, p.total);
+  if (((uintptr_t)ws & 255u) != 0) return fail(QK_EINVAL, "workspace must be 256-byte aligned");
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_plans[ws] = std::move(p);
+  return QK_OK;
+}
+
+int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream stream) {
+  Plan p;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_plans.find(ws);
+    if (it == g_plans.end()) return fail(QK_EINVAL, "no plan recorded for this workspace (call qk_batch_plan)");
+    p = it->second;
+  }
+  if (ws_bytes < p.total) return fail(QK_EWORKSPACE, "batch workspace has %zu bytes, %zu needed", ws_bytes, p.total);
+  return run_plan(p, (unsigned char *)ws, status, (cudaStream_t)stream);
+}
+
+}  // extern "C"

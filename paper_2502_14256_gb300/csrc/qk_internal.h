@@ -1,0 +1,54 @@
+// Host-side launchers shared between the libqk translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/qk.h"
+
+namespace qk {
+
+// Point-set description resolved for one randomization range.
+struct ColJob {
+  int32_t kind, order;
+  uint32_t d, m;
+  const uint32_t *Ct;   // nets: (R, d, 32), already offset to randomization r0
+  const uint32_t *g;    // lattices
+  const double *w;      // (d) weights
+  double zeta;
+  int32_t family, alpha;
+  uint32_t nr;          // randomizations in this job
+};
+
+// First column (form QK_COL_K1 / QK_COL_P) of nr randomizations: out (nr, n).
+int launch_kernel_col(const ColJob &job, int32_t dtype, int32_t form, void *out, cudaStream_t st);
+
+// Gradient partial sums.  u: (nr * nrhs, n) in dtype (vector v belongs to
+// randomization v / nrhs).  partial: (nr * nrhs, blocks, 2d) doubles with
+// blocks = grad_blocks(m): [0, d) sum_i u_i dk1_i/dc_j, [d, 2d) sum_i dk1_i/dc_j.
+int launch_grad_partials(const ColJob &job, uint32_t nrhs, int32_t dtype, const void *u,
+                         double *partial, cudaStream_t st);
+uint32_t grad_blocks(uint32_t m);
+
+int launch_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64_t i0, uint64_t n,
+                      uint32_t *X, cudaStream_t st);
+int launch_lms(uint32_t d, uint32_t R, const uint32_t *C, const uint32_t *S, uint32_t *Ct,
+               cudaStream_t st);
+
+}  // namespace qk
+
+namespace qk {
+size_t ws_eigs(int family, uint32_t m, uint32_t batch, int dtype);
+size_t ws_solve(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype);
+size_t ws_mll(int family, uint32_t m, uint32_t nr, uint32_t nrhs, int dtype, uint32_t d);
+size_t elem_bytes(int family, int dtype);
+int op_eigs(int family, uint32_t m, uint32_t batch, int dtype, int form, const void *col, double zeta, double eta,
+            double *lam, void *ws, uint32_t *status, cudaStream_t st);
+int op_solve(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, const double *lam, const void *y,
+             void *c, int refine, void *ws, cudaStream_t st);
+int op_matvec(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, const double *lam, const void *y,
+              void *u, void *ws, cudaStream_t st);
+int op_transform(int kind, uint32_t m, uint64_t nvec, int dtype, void *x, cudaStream_t st);
+int op_mll(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const void *y, double *out, double *grad,
+           void *ws, cudaStream_t st);
+}  // namespace qk

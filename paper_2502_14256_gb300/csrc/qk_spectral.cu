@@ -1,0 +1,454 @@
+// Spectral operations of arXiv 2502.14256, Sec. 5.4, on top of the tile
+// transforms: eigenvalues, solves, matrix-vector products, and the marginal
+// log-likelihood with its gradient carried back through the transform.
+//
+// Normalisation: the transforms are unnormalised (H y, or the DFT of the data
+// in linear order).  With Y = H y (or DFT(y_lin)):
+//   lambda = H k_1 + eta,  K^-1 y = H (Y / lambda) / n,  K y = H (Y * lambda) / n,
+//   y^T K^-1 y = sum |Y_w|^2 / (n lambda_w),  log det K = sum log lambda_w,
+//   dMLL/dlambda_w = g_w = (|Y_w|^2 / (n lambda_w^2) - 1 / lambda_w) / 2,
+//   dMLL/dc_j = sum_i (H g)_i dk1_i/dc_j,  dMLL/deta = sum_w g_w.
+// For lattices H is replaced by the DIT FFT on natural-order input (FFTBR) and
+// the inverse by the conjugate DIF FFT with natural-order output (IFFTBR); the
+// kernel column is real and symmetric in linear order, so lambda and H g are real.
+#include <cmath>
+#include <cstring>
+
+#include "qk_common.cuh"
+#include "qk_internal.h"
+#include "qk_transform.cuh"
+
+namespace qk {
+
+// ------------------------------------------------------------- small kernels
+template <typename T>
+__device__ __forceinline__ double re(T v) { return (double)v; }
+__device__ __forceinline__ double re(float2 v) { return (double)v.x; }
+__device__ __forceinline__ double re(double2 v) { return v.x; }
+template <typename T>
+__device__ __forceinline__ double abs2(T v) { return (double)v * (double)v; }
+__device__ __forceinline__ double abs2(float2 v) { return (double)v.x * v.x + (double)v.y * v.y; }
+__device__ __forceinline__ double abs2(double2 v) { return v.x * v.x + v.y * v.y; }
+template <typename E> __device__ __forceinline__ E from_real(double v);
+template <> __device__ __forceinline__ float from_real<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ double from_real<double>(double v) { return v; }
+template <> __device__ __forceinline__ float2 from_real<float2>(double v) { return make_float2((float)v, 0.f); }
+template <> __device__ __forceinline__ double2 from_real<double2>(double v) { return make_double2(v, 0.0); }
+template <typename E> __device__ __forceinline__ E mul_real(E v, double s);
+template <> __device__ __forceinline__ float mul_real<float>(float v, double s) { return (float)((double)v * s); }
+template <> __device__ __forceinline__ double mul_real<double>(double v, double s) { return v * s; }
+template <> __device__ __forceinline__ float2 mul_real<float2>(float2 v, double s) {
+  return make_float2((float)((double)v.x * s), (float)((double)v.y * s));
+}
+template <> __device__ __forceinline__ double2 mul_real<double2>(double2 v, double s) {
+  return make_double2(v.x * s, v.y * s);
+}
+
+__device__ __forceinline__ uint64_t gtid() { return (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; }
+__device__ __forceinline__ uint64_t gstride() { return (uint64_t)gridDim.x * blockDim.x; }
+
+// real T -> element E (copy or complex with zero imaginary part)
+template <typename T, typename E>
+__global__ void k_load_real(const T *__restrict__ in, E *__restrict__ out, uint64_t count) {
+  for (uint64_t i = gtid(); i < count; i += gstride()) out[i] = from_real<E>((double)in[i]);
+}
+
+// real part of E -> T, times scale
+template <typename E, typename T>
+__global__ void k_store_real(const E *__restrict__ in, T *__restrict__ out, uint64_t count, double scale) {
+  for (uint64_t i = gtid(); i < count; i += gstride()) out[i] = (T)(re(in[i]) * scale);
+}
+
+// lambda = zmul * Re(X) + [form P] zeta n delta_{w0} + eta, with the sign test.
+template <typename E>
+__global__ void k_lam_final(const E *__restrict__ X, double *__restrict__ lam, uint64_t total, int m,
+                            double zmul, double dc, double eta, uint32_t *status) {
+  bool bad = false;
+  const uint64_t mask = (1ull << m) - 1;
+  for (uint64_t i = gtid(); i < total; i += gstride()) {
+    double v = zmul * re(X[i]) + eta;
+    if ((i & mask) == 0) v += dc;
+    lam[i] = v;
+    bad |= !(v > 0.0);
+  }
+  if (bad && status) atomicOr(status, (uint32_t)QK_STATUS_NOTPD);
+}
+
+// X[v][w] *= fac / lambda[v / nrhs][w] (mode 0) or fac * lambda (mode 1), in FP64.
+template <typename E>
+__global__ void k_scale_lam(E *__restrict__ X, const double *__restrict__ lam, uint64_t total, int m,
+                            uint32_t nrhs, double fac, int mode) {
+  const uint64_t mask = (1ull << m) - 1;
+  for (uint64_t i = gtid(); i < total; i += gstride()) {
+    const uint64_t v = i >> m, w = i & mask;
+    const double l = lam[((v / nrhs) << m) + w];
+    X[i] = mul_real(X[i], mode == 0 ? fac / l : fac * l);
+  }
+}
+
+template <typename E, typename T>
+__global__ void k_residual(const T *__restrict__ y, const E *__restrict__ Kc, T *__restrict__ r, uint64_t count,
+                           double scale) {
+  for (uint64_t i = gtid(); i < count; i += gstride()) r[i] = (T)((double)y[i] - re(Kc[i]) * scale);
+}
+
+template <typename T>
+__global__ void k_add(T *__restrict__ c, const T *__restrict__ dc, uint64_t count) {
+  for (uint64_t i = gtid(); i < count; i += gstride()) c[i] += dc[i];
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += sh[q];
+  return s;
+}
+
+constexpr int kRedNT = 256;
+
+// Per vector: FP64 sum of y (the posterior mean needs it with relative accuracy,
+// and for a centred integrand it is a small difference of large terms).
+template <typename T>
+__global__ void k_sum_rows(const T *__restrict__ y, int m, double *__restrict__ out) {
+  __shared__ double sh[32];
+  const uint64_t n = 1ull << m;
+  const T *yv = y + (uint64_t)blockIdx.x * n;
+  double s = 0.0;
+  for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)yv[i];
+  const double t = block_sum(s, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+
+// Per vector: quad and sum g partials; overwrite X with g (real); keep Re Y_0.
+template <typename E>
+__global__ void k_mll_spectral(E *__restrict__ X, const double *__restrict__ lam, int m, uint32_t nrhs,
+                               double *__restrict__ part, double *__restrict__ y0) {
+  __shared__ double sh[32];
+  const uint64_t n = 1ull << m;
+  const uint32_t v = blockIdx.y;
+  const double *lr = lam + (uint64_t)(v / nrhs) * n;
+  E *xv = X + (uint64_t)v * n;
+  double q = 0.0, gs = 0.0;
+  const double inv_n = 1.0 / (double)n;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += (uint64_t)gridDim.x * blockDim.x) {
+    const E Y = xv[w];
+    const double l = lr[w];
+    const double a = abs2(Y) * inv_n / l;
+    q += a;
+    const double g = 0.5 * (a - 1.0) / l;
+    gs += g;
+    xv[w] = from_real<E>(g);
+  }
+  const double sq = block_sum(q, sh);
+  const double sg = block_sum(gs, sh);
+  if (threadIdx.x == 0) {
+    part[((uint64_t)v * gridDim.x + blockIdx.x) * 2 + 0] = sq;
+    part[((uint64_t)v * gridDim.x + blockIdx.x) * 2 + 1] = sg;
+  }
+}
+
+template <bool FAST_LOG>
+__global__ void k_logdet(const double *__restrict__ lam, int m, double *__restrict__ part) {
+  __shared__ double sh[32];
+  const uint64_t n = 1ull << m;
+  const double *lr = lam + (uint64_t)blockIdx.y * n;
+  double s = 0.0;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += (uint64_t)gridDim.x * blockDim.x)
+    s += FAST_LOG ? (double)logf((float)lr[w]) : log(lr[w]);
+  const double t = block_sum(s, sh);
+  if (threadIdx.x == 0) part[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
+}
+
+struct FinalArgs {
+  uint32_t nvec, nrhs, d, bspec, blog, bgrad;
+  int m;
+  double zeta;
+  const double *lam, *spec_part, *log_part, *grad_part, *y0;
+  double *out, *grad;
+};
+
+__global__ void k_mll_final(FinalArgs a) {
+  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= a.nvec) return;
+  const uint32_t r = v / a.nrhs;
+  const double n = (double)(1ull << a.m);
+  double quad = 0.0, gsum = 0.0, ld = 0.0;
+  for (uint32_t b = 0; b < a.bspec; ++b) {
+    quad += a.spec_part[((uint64_t)v * a.bspec + b) * 2 + 0];
+    gsum += a.spec_part[((uint64_t)v * a.bspec + b) * 2 + 1];
+  }
+  for (uint32_t b = 0; b < a.blog; ++b) ld += a.log_part[(uint64_t)r * a.blog + b];
+  const double lam0 = a.lam[(uint64_t)r << a.m];
+  const double sumy = a.y0[v];
+  double *o = a.out + (uint64_t)v * QK_MLL_NOUT;
+  o[QK_MLL_QUAD] = quad;
+  o[QK_MLL_LOGDET] = ld;
+  o[QK_MLL_MLL] = -0.5 * quad - 0.5 * ld - 0.5 * n * 1.8378770664093454836;  // log(2 pi)
+  o[QK_MLL_MEAN] = a.zeta * sumy / lam0;
+  o[QK_MLL_VAR] = a.zeta * ((lam0 - a.zeta * n) / lam0);
+  if (a.grad) {
+    double *g = a.grad + (uint64_t)v * (2 * a.d + 2);
+    const double mfac = -a.zeta * sumy / (lam0 * lam0);
+    for (uint32_t j = 0; j < a.d; ++j) {
+      double su = 0.0, s1 = 0.0;
+      for (uint32_t b = 0; b < a.bgrad; ++b) {
+        su += a.grad_part[((uint64_t)v * a.bgrad + b) * 2 * a.d + j];
+        s1 += a.grad_part[((uint64_t)v * a.bgrad + b) * 2 * a.d + a.d + j];
+      }
+      g[j] = su;
+      g[a.d + 1 + j] = mfac * s1;
+    }
+    g[a.d] = gsum;
+    g[2 * a.d + 1] = mfac;
+  }
+}
+
+// ------------------------------------------------------------ host helpers
+static unsigned grid_for(uint64_t count) {
+  uint64_t b = (count + 255) / 256;
+  const uint64_t cap = (uint64_t)kSMs * 32;
+  return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <typename E, int KIND>
+static int xform(E *x, int m, uint64_t nvec, double scale, cudaStream_t st) {
+  return run_transform<KIND, E>(x, m, 1ull << m, nvec, scale, st);
+}
+
+template <typename E> struct IsCplx { static constexpr bool value = false; };
+template <> struct IsCplx<float2> { static constexpr bool value = true; };
+template <> struct IsCplx<double2> { static constexpr bool value = true; };
+
+// Forward transform (in place): WHT for real elements (nets), FFTBR (DIT) for
+// complex elements (lattices); the element type encodes the family.
+template <typename E>
+static int fwd(int family, E *x, int m, uint64_t nvec, cudaStream_t st) {
+  (void)family;
+  if constexpr (IsCplx<E>::value) return xform<E, XF_DIT>(x, m, nvec, 1.0, st);
+  else return xform<E, XF_WHT>(x, m, nvec, 1.0, st);
+}
+template <typename E>
+static int inv(int family, E *x, int m, uint64_t nvec, double scale, cudaStream_t st) {
+  (void)family;
+  if constexpr (IsCplx<E>::value) return xform<E, XF_DIF>(x, m, nvec, scale, st);
+  else return xform<E, XF_WHT>(x, m, nvec, scale, st);
+}
+
+size_t elem_bytes(int family, int dtype) {
+  const size_t s = dtype == QK_F64 ? 8 : 4;
+  return family == QK_SI ? 2 * s : s;
+}
+
+// Workspace sizes (bytes) per op; see qk_workspace_bytes.
+size_t ws_eigs(int family, uint32_t m, uint32_t batch, int dtype) {
+  return align256(elem_bytes(family, dtype) * ((uint64_t)batch << m));
+}
+size_t ws_solve(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype) {
+  const uint64_t cnt = ((uint64_t)batch * nrhs) << m;
+  // X (E) + residual path: FP64 element buffer + T buffer
+  return align256(elem_bytes(family, dtype) * cnt) + align256(elem_bytes(family, QK_F64) * cnt) +
+         align256((dtype == QK_F64 ? 8 : 4) * cnt);
+}
+uint32_t spec_blocks(uint32_t m) {
+  const uint64_t b = ((1ull << m) + 4095) / 4096;
+  return (uint32_t)(b > 256 ? 256 : b);
+}
+size_t ws_mll(int family, uint32_t m, uint32_t nr, uint32_t nrhs, int dtype, uint32_t d) {
+  const uint64_t nv = (uint64_t)nr * nrhs;
+  size_t s = align256(elem_bytes(family, dtype) * (nv << m));
+  if (family == QK_SI) s += align256((dtype == QK_F64 ? 8 : 4) * (nv << m));  // real u
+  s += align256(nv * spec_blocks(m) * 2 * sizeof(double));
+  s += align256((uint64_t)nr * spec_blocks(m) * sizeof(double));
+  s += align256(nv * sizeof(double));
+  s += align256(nv * grad_blocks(m) * 2 * (uint64_t)d * sizeof(double));
+  return s;
+}
+
+// --------------------------------------------------------------- operations
+template <typename T, typename E>
+static int eigs_t(int family, uint32_t m, uint32_t batch, int form, const void *col, double zeta, double eta,
+                  double *lam, void *ws, uint32_t *status, cudaStream_t st) {
+  const uint64_t cnt = (uint64_t)batch << m;
+  E *X = (E *)ws;
+  k_load_real<T, E><<<grid_for(cnt), 256, 0, st>>>((const T *)col, X, cnt);
+  int rc = check_launch("eigs load");
+  if (rc) return rc;
+  if ((rc = fwd<E>(family, X, m, batch, st))) return rc;
+  const double zmul = form == QK_COL_P ? zeta : 1.0;
+  const double dc = form == QK_COL_P ? zeta * (double)(1ull << m) : 0.0;
+  k_lam_final<E><<<grid_for(cnt), 256, 0, st>>>(X, lam, cnt, (int)m, zmul, dc, eta, status);
+  return check_launch("eigs finalize");
+}
+
+int op_eigs(int family, uint32_t m, uint32_t batch, int dtype, int form, const void *col, double zeta, double eta,
+            double *lam, void *ws, uint32_t *status, cudaStream_t st) {
+  if (family == QK_DSI)
+    return dtype == QK_F64 ? eigs_t<double, double>(family, m, batch, form, col, zeta, eta, lam, ws, status, st)
+                           : eigs_t<float, float>(family, m, batch, form, col, zeta, eta, lam, ws, status, st);
+  return dtype == QK_F64 ? eigs_t<double, double2>(family, m, batch, form, col, zeta, eta, lam, ws, status, st)
+                         : eigs_t<float, float2>(family, m, batch, form, col, zeta, eta, lam, ws, status, st);
+}
+
+// c = K^-1 y (mode 0) or K y (mode 1) in precision of E; X is scratch of nvec * n E.
+template <typename T, typename E>
+static int apply_t(int family, uint32_t m, uint32_t nvec, uint32_t nrhs, const double *lam, const T *y, T *c,
+                   E *X, int mode, cudaStream_t st) {
+  const uint64_t cnt = (uint64_t)nvec << m;
+  const double n = (double)(1ull << m);
+  k_load_real<T, E><<<grid_for(cnt), 256, 0, st>>>(y, X, cnt);
+  int rc = check_launch("solve load");
+  if (rc) return rc;
+  if ((rc = fwd<E>(family, X, m, nvec, st))) return rc;
+  k_scale_lam<E><<<grid_for(cnt), 256, 0, st>>>(X, lam, cnt, (int)m, nrhs, 1.0 / n, mode);
+  if ((rc = check_launch("solve scale"))) return rc;
+  if ((rc = inv<E>(family, X, m, nvec, 1.0, st))) return rc;
+  k_store_real<E, T><<<grid_for(cnt), 256, 0, st>>>(X, c, cnt, 1.0);
+  return check_launch("solve store");
+}
+
+template <typename T, typename E, typename E64>
+static int solve_t(int family, uint32_t m, uint32_t batch, uint32_t nrhs, const double *lam, const T *y, T *c,
+                   int refine, void *ws, cudaStream_t st) {
+  const uint32_t nvec = batch * nrhs;
+  const uint64_t cnt = (uint64_t)nvec << m;
+  unsigned char *p = (unsigned char *)ws;
+  E *X = (E *)p;
+  p += align256(sizeof(E) * cnt);
+  E64 *X64 = (E64 *)p;
+  p += align256(sizeof(E64) * cnt);
+  T *tmp = (T *)p;
+  int rc = apply_t<T, E>(family, m, nvec, nrhs, lam, y, c, X, 0, st);
+  if (rc) return rc;
+  const double n = (double)(1ull << m);
+  for (int it = 0; it < refine; ++it) {
+    // residual r = y - K c with FP64 transforms
+    k_load_real<T, E64><<<grid_for(cnt), 256, 0, st>>>(c, X64, cnt);
+    if ((rc = check_launch("refine load"))) return rc;
+    if ((rc = fwd<E64>(family, X64, m, nvec, st))) return rc;
+    k_scale_lam<E64><<<grid_for(cnt), 256, 0, st>>>(X64, lam, cnt, (int)m, nrhs, 1.0 / n, 1);
+    if ((rc = check_launch("refine scale"))) return rc;
+    if ((rc = inv<E64>(family, X64, m, nvec, 1.0, st))) return rc;
+    k_residual<E64, T><<<grid_for(cnt), 256, 0, st>>>(y, X64, tmp, cnt, 1.0);
+    if ((rc = check_launch("refine residual"))) return rc;
+    if ((rc = apply_t<T, E>(family, m, nvec, nrhs, lam, tmp, tmp, X, 0, st))) return rc;
+    k_add<T><<<grid_for(cnt), 256, 0, st>>>(c, tmp, cnt);
+    if ((rc = check_launch("refine add"))) return rc;
+  }
+  return QK_OK;
+}
+
+int op_solve(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, const double *lam, const void *y,
+             void *c, int refine, void *ws, cudaStream_t st) {
+  if (family == QK_DSI) {
+    if (dtype == QK_F64)
+      return solve_t<double, double, double>(family, m, batch, nrhs, lam, (const double *)y, (double *)c, refine, ws, st);
+    return solve_t<float, float, double>(family, m, batch, nrhs, lam, (const float *)y, (float *)c, refine, ws, st);
+  }
+  if (dtype == QK_F64)
+    return solve_t<double, double2, double2>(family, m, batch, nrhs, lam, (const double *)y, (double *)c, refine, ws, st);
+  return solve_t<float, float2, double2>(family, m, batch, nrhs, lam, (const float *)y, (float *)c, refine, ws, st);
+}
+
+int op_matvec(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, const double *lam, const void *y,
+              void *u, void *ws, cudaStream_t st) {
+  const uint32_t nvec = batch * nrhs;
+  if (family == QK_DSI)
+    return dtype == QK_F64 ? apply_t<double, double>(family, m, nvec, nrhs, lam, (const double *)y, (double *)u, (double *)ws, 1, st)
+                           : apply_t<float, float>(family, m, nvec, nrhs, lam, (const float *)y, (float *)u, (float *)ws, 1, st);
+  return dtype == QK_F64 ? apply_t<double, double2>(family, m, nvec, nrhs, lam, (const double *)y, (double *)u, (double2 *)ws, 1, st)
+                         : apply_t<float, float2>(family, m, nvec, nrhs, lam, (const float *)y, (float *)u, (float2 *)ws, 1, st);
+}
+
+template <typename T, typename E>
+static int mll_t(const ColJob &job, uint32_t nrhs, const double *lam, const T *y, double *out, double *grad,
+                 void *ws, cudaStream_t st, int dtype) {
+  const uint32_t m = job.m;
+  const uint32_t nvec = job.nr * nrhs;
+  const uint64_t cnt = (uint64_t)nvec << m;
+  unsigned char *p = (unsigned char *)ws;
+  E *X = (E *)p;
+  p += align256(sizeof(E) * cnt);
+  T *u = (T *)X;  // DSI: E == T, the transform output is u itself
+  if (job.family == QK_SI) {
+    u = (T *)p;
+    p += align256(sizeof(T) * cnt);
+  }
+  const uint32_t bs = spec_blocks(m);
+  double *spec_part = (double *)p;
+  p += align256((uint64_t)nvec * bs * 2 * sizeof(double));
+  double *log_part = (double *)p;
+  p += align256((uint64_t)job.nr * bs * sizeof(double));
+  double *y0 = (double *)p;
+  p += align256((uint64_t)nvec * sizeof(double));
+  double *grad_part = (double *)p;
+
+  k_load_real<T, E><<<grid_for(cnt), 256, 0, st>>>(y, X, cnt);
+  int rc = check_launch("mll load");
+  if (rc) return rc;
+  k_sum_rows<T><<<nvec, 1024, 0, st>>>(y, (int)m, y0);
+  if ((rc = check_launch("mll sum y"))) return rc;
+  if ((rc = fwd<E>(job.family, X, (int)m, nvec, st))) return rc;
+  k_mll_spectral<E><<<dim3(bs, nvec), kRedNT, 0, st>>>(X, lam, (int)m, nrhs, spec_part, y0);
+  if ((rc = check_launch("mll spectral"))) return rc;
+  if (dtype == QK_F64)
+    k_logdet<false><<<dim3(bs, job.nr), kRedNT, 0, st>>>(lam, (int)m, log_part);
+  else
+    k_logdet<true><<<dim3(bs, job.nr), kRedNT, 0, st>>>(lam, (int)m, log_part);
+  if ((rc = check_launch("mll logdet"))) return rc;
+  if (grad) {
+    // u = H g (nets) or the DFT of g read back in natural order (lattices); real.
+    if ((rc = inv<E>(job.family, X, (int)m, nvec, 1.0, st))) return rc;
+    if (job.family == QK_SI) {
+      k_store_real<E, T><<<grid_for(cnt), 256, 0, st>>>(X, u, cnt, 1.0);
+      if ((rc = check_launch("mll u"))) return rc;
+    }
+    if ((rc = launch_grad_partials(job, nrhs, dtype, u, grad_part, st))) return rc;
+  }
+  FinalArgs fa;
+  fa.nvec = nvec;
+  fa.nrhs = nrhs;
+  fa.d = job.d;
+  fa.bspec = bs;
+  fa.blog = bs;
+  fa.bgrad = grad_blocks(m);
+  fa.m = (int)m;
+  fa.zeta = job.zeta;
+  fa.lam = lam;
+  fa.spec_part = spec_part;
+  fa.log_part = log_part;
+  fa.grad_part = grad_part;
+  fa.y0 = y0;
+  fa.out = out;
+  fa.grad = grad;
+  k_mll_final<<<(nvec + 127) / 128, 128, 0, st>>>(fa);
+  return check_launch("mll final");
+}
+
+int op_mll(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const void *y, double *out, double *grad,
+           void *ws, cudaStream_t st) {
+  if (job.family == QK_DSI)
+    return dtype == QK_F64 ? mll_t<double, double>(job, nrhs, lam, (const double *)y, out, grad, ws, st, dtype)
+                           : mll_t<float, float>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype);
+  return dtype == QK_F64 ? mll_t<double, double2>(job, nrhs, lam, (const double *)y, out, grad, ws, st, dtype)
+                         : mll_t<float, float2>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype);
+}
+
+int op_transform(int kind, uint32_t m, uint64_t nvec, int dtype, void *x, cudaStream_t st) {
+  const double scale = 1.0 / std::sqrt((double)(1ull << m));
+  if (kind == XF_WHT)
+    return dtype == QK_F64 ? xform<double, XF_WHT>((double *)x, (int)m, nvec, scale, st)
+                           : xform<float, XF_WHT>((float *)x, (int)m, nvec, scale, st);
+  if (kind == XF_DIT)
+    return dtype == QK_F64 ? xform<double2, XF_DIT>((double2 *)x, (int)m, nvec, scale, st)
+                           : xform<float2, XF_DIT>((float2 *)x, (int)m, nvec, scale, st);
+  return dtype == QK_F64 ? xform<double2, XF_DIF>((double2 *)x, (int)m, nvec, scale, st)
+                         : xform<float2, XF_DIF>((float2 *)x, (int)m, nvec, scale, st);
+}
+
+}  // namespace qk

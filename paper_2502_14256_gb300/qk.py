@@ -1,0 +1,259 @@
+"""Thin Python binding of libqk.so (include/qk.h), by ctypes.
+
+Each function takes torch tensors that live on the GPU, passes their raw
+device pointers and sizes to the C entry point of the same name, and raises
+QKError on a non-zero status.  Nothing here computes: every step of the path
+runs in the library's CUDA kernels.  The library must have been built
+(``python -m paper_2502_14256_gb300.build``); importing this module without
+it raises immediately instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqk.so")
+
+QK_OK, QK_EINVAL, QK_ENOTPD, QK_ECUDA, QK_ETIMEOUT, QK_EWORKSPACE = range(6)
+QK_STATUS_NOTPD, QK_STATUS_TIMEOUT = 1, 2
+QK_NET_B2, QK_LATTICE = 0, 1
+QK_NATURAL, QK_GRAY = 0, 1
+QK_DSI, QK_SI = 0, 1
+QK_F64, QK_F32 = 0, 1
+QK_COL_K1, QK_COL_P = 0, 1
+QK_MLL_NOUT = 5
+OP_EIGS, OP_SOLVE, OP_MATVEC, OP_MLL = 0, 1, 2, 3
+
+EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_solve", "qk_matvec", "qk_mll",
+            "qk_batch_workspace_bytes", "qk_batch_plan", "qk_batch_run", "qk_workspace_bytes",
+            "qk_read_status", "qk_last_error", "qk_version", "qk_fwht", "qk_fftbr", "qk_ifftbr",
+            "qk_launch_count"]
+
+
+class QKError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libqk status {code}: {msg}")
+        self.code = code
+
+
+class PointSet(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("order", C.c_int32), ("d", C.c_uint32), ("R", C.c_uint32),
+                ("Ct", C.c_void_p), ("g", C.c_void_p), ("D", C.c_void_p)]
+
+
+class Kernel(C.Structure):
+    _fields_ = [("family", C.c_int32), ("alpha", C.c_int32), ("d", C.c_uint32), ("weights", C.c_void_p),
+                ("zeta", C.c_double)]
+
+
+class Task(C.Structure):
+    _fields_ = [("ps", PointSet), ("k", Kernel), ("m", C.c_uint32), ("nrhs", C.c_uint32), ("eta", C.c_double),
+                ("y", C.c_void_p), ("c", C.c_void_p), ("lam", C.c_void_p), ("out", C.c_void_p),
+                ("grad", C.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2502_14256_gb300.build`")
+    lib = C.CDLL(LIB_PATH)
+    P, u32, u64, i32, dbl, sz = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int32, C.c_double, C.c_size_t
+    sig = {
+        "qk_lms_setup": [u32, u32, P, P, P, P],
+        "qk_gen_points": [C.POINTER(PointSet), u32, u32, u64, u64, P, P],
+        "qk_kernel_col": [C.POINTER(PointSet), C.POINTER(Kernel), u32, u32, u32, i32, i32, P, P],
+        "qk_eigs": [i32, u32, u32, i32, i32, P, dbl, dbl, P, P, sz, P, P],
+        "qk_solve": [i32, u32, u32, u32, i32, P, P, P, i32, P, sz, P],
+        "qk_matvec": [i32, u32, u32, u32, i32, P, P, P, P, sz, P],
+        "qk_mll": [C.POINTER(PointSet), C.POINTER(Kernel), u32, u32, u32, u32, i32, dbl, P, P, P, P, P, sz, P, P],
+        "qk_batch_workspace_bytes": [C.POINTER(Task), u32, i32, C.POINTER(sz)],
+        "qk_batch_plan": [C.POINTER(Task), u32, i32, i32, P, sz, P],
+        "qk_batch_run": [P, sz, P, P],
+        "qk_workspace_bytes": [i32, i32, u32, u32, u32, i32, u32, C.POINTER(sz)],
+        "qk_read_status": [P, P],
+        "qk_last_error": [C.c_char_p, sz],
+        "qk_version": [],
+        "qk_fwht": [u32, u64, i32, P, P],
+        "qk_fftbr": [u32, u64, i32, P, P],
+        "qk_ifftbr": [u32, u64, i32, P, P],
+        "qk_launch_count": [],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = None if name == "qk_last_error" else (C.c_uint64 if name == "qk_launch_count" else C.c_int)
+    return lib
+
+
+LIB = _load()
+
+
+def last_error() -> str:
+    buf = C.create_string_buffer(512)
+    LIB.qk_last_error(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int):
+    if rc != QK_OK:
+        raise QKError(rc, last_error())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("libqk takes device tensors")
+    if not t.is_contiguous():
+        raise ValueError("libqk takes contiguous tensors")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def dtype_code(dt: torch.dtype) -> int:
+    if dt == torch.float64:
+        return QK_F64
+    if dt == torch.float32:
+        return QK_F32
+    raise ValueError(f"unsupported dtype {dt}")
+
+
+# --------------------------------------------------------------- structures
+def pointset(kind: int, d: int, R: int, Ct=None, g=None, D=None, order: int = QK_GRAY) -> PointSet:
+    return PointSet(kind, order if kind == QK_NET_B2 else QK_NATURAL, d, R, _ptr(Ct), _ptr(g), _ptr(D))
+
+
+def kernel(family: int, alpha: int, weights, zeta: float = 1.0) -> Kernel:
+    return Kernel(family, alpha, weights.numel(), _ptr(weights), float(zeta))
+
+
+# --------------------------------------------------------------- entry points
+def lms_setup(C_cols, S_rows, Ct_out, stream=None):
+    d = C_cols.shape[0]
+    R = S_rows.shape[0]
+    _check(LIB.qk_lms_setup(d, R, _ptr(C_cols), _ptr(S_rows), _ptr(Ct_out), _stream(stream)))
+    return Ct_out
+
+
+def gen_points(ps: PointSet, r0: int, nr: int, i0: int, n: int, X, stream=None):
+    _check(LIB.qk_gen_points(C.byref(ps), r0, nr, i0, n, _ptr(X), _stream(stream)))
+    return X
+
+
+def kernel_col(ps: PointSet, k: Kernel, r0: int, nr: int, m: int, col, form: int = QK_COL_K1, stream=None):
+    _check(LIB.qk_kernel_col(C.byref(ps), C.byref(k), r0, nr, m, dtype_code(col.dtype), form, _ptr(col),
+                             _stream(stream)))
+    return col
+
+
+def workspace_bytes(op: int, family: int, m: int, batch: int, nrhs: int, dtype: torch.dtype, d: int = 0) -> int:
+    out = C.c_size_t(0)
+    _check(LIB.qk_workspace_bytes(op, family, m, batch, nrhs, dtype_code(dtype), d, C.byref(out)))
+    return out.value
+
+
+def workspace(nbytes: int, device="cuda"):
+    """A 256-byte aligned device byte buffer (torch allocations are 512-byte aligned)."""
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def eigs(family: int, m: int, col, lam, zeta: float = 1.0, eta: float = 0.0, form: int = QK_COL_K1,
+         ws=None, status=None, stream=None):
+    batch = col.numel() >> m
+    if ws is None:
+        ws = workspace(workspace_bytes(OP_EIGS, family, m, batch, 1, col.dtype), col.device)
+    _check(LIB.qk_eigs(family, m, batch, dtype_code(col.dtype), form, _ptr(col), zeta, eta, _ptr(lam), _ptr(ws),
+                       ws.numel(), _ptr(status), _stream(stream)))
+    return lam
+
+
+def solve(family: int, m: int, lam, y, c, refine_steps: int = 0, ws=None, stream=None):
+    batch = lam.numel() >> m
+    nrhs = (y.numel() >> m) // batch
+    if ws is None:
+        ws = workspace(workspace_bytes(OP_SOLVE, family, m, batch, nrhs, y.dtype), y.device)
+    _check(LIB.qk_solve(family, m, batch, nrhs, dtype_code(y.dtype), _ptr(lam), _ptr(y), _ptr(c), refine_steps,
+                        _ptr(ws), ws.numel(), _stream(stream)))
+    return c
+
+
+def matvec(family: int, m: int, lam, y, u, ws=None, stream=None):
+    batch = lam.numel() >> m
+    nrhs = (y.numel() >> m) // batch
+    if ws is None:
+        ws = workspace(workspace_bytes(OP_MATVEC, family, m, batch, nrhs, y.dtype), y.device)
+    _check(LIB.qk_matvec(family, m, batch, nrhs, dtype_code(y.dtype), _ptr(lam), _ptr(y), _ptr(u), _ptr(ws),
+                         ws.numel(), _stream(stream)))
+    return u
+
+
+def mll(ps: PointSet, k: Kernel, r0: int, nr: int, m: int, nrhs: int, eta: float, lam, y, out, grad=None,
+        ws=None, status=None, stream=None):
+    if ws is None:
+        ws = workspace(workspace_bytes(OP_MLL, k.family, m, nr, nrhs, y.dtype, ps.d), y.device)
+    _check(LIB.qk_mll(C.byref(ps), C.byref(k), r0, nr, m, nrhs, dtype_code(y.dtype), eta, _ptr(lam), _ptr(y),
+                      _ptr(out), _ptr(grad), _ptr(ws), ws.numel(), _ptr(status), _stream(stream)))
+    return out
+
+
+def read_status(status, stream=None):
+    _check(LIB.qk_read_status(_ptr(status), _stream(stream)))
+
+
+def version() -> int:
+    return LIB.qk_version()
+
+
+def launch_count() -> int:
+    return LIB.qk_launch_count()
+
+
+def _nvec_m(x, m, complex_data):
+    per = (2 << m) if complex_data else (1 << m)
+    return x.numel() // per
+
+
+def fwht(m: int, x, stream=None):
+    """x <- H x / sqrt(n) in place over the last axis (length 2^m)."""
+    _check(LIB.qk_fwht(m, _nvec_m(x, m, False), dtype_code(x.dtype), _ptr(x), _stream(stream)))
+    return x
+
+
+def fftbr(m: int, x, stream=None):
+    """In place; x holds interleaved (re, im) pairs, natural-order input."""
+    _check(LIB.qk_fftbr(m, _nvec_m(x, m, True), dtype_code(x.dtype), _ptr(x), _stream(stream)))
+    return x
+
+
+def ifftbr(m: int, x, stream=None):
+    _check(LIB.qk_ifftbr(m, _nvec_m(x, m, True), dtype_code(x.dtype), _ptr(x), _stream(stream)))
+    return x
+
+
+# ------------------------------------------------------------------ batching
+def task_array(tasks):
+    arr = (Task * len(tasks))(*tasks)
+    return arr
+
+
+def batch_workspace_bytes(tasks, dtype: torch.dtype) -> int:
+    arr = task_array(tasks)
+    out = C.c_size_t(0)
+    _check(LIB.qk_batch_workspace_bytes(arr, len(tasks), dtype_code(dtype), C.byref(out)))
+    return out.value
+
+
+def batch_plan(tasks, dtype: torch.dtype, refine_steps: int, ws, stream=None):
+    arr = task_array(tasks)
+    _check(LIB.qk_batch_plan(arr, len(tasks), dtype_code(dtype), refine_steps, _ptr(ws), ws.numel(),
+                             _stream(stream)))
+
+
+def batch_run(ws, status=None, stream=None):
+    _check(LIB.qk_batch_run(_ptr(ws), ws.numel(), _ptr(status), _stream(stream)))

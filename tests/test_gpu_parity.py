@@ -1,0 +1,365 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, element by element.
+
+Sizes span several CTA tiles and ragged ranges; tolerances: integer work bit-exact,
+FP64 relative 1e-10 (solves, MLL) and 1e-12 (columns, eigenvalues), FP32 relative 1e-5
+(after one refinement step for solves).
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import qk_oracle as o
+from tests import qkcases as qc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qk():
+    from paper_2502_14256_gb300 import build
+    build.build()
+    from paper_2502_14256_gb300 import qk as q
+    return q
+
+
+F64, F32 = torch.float64, torch.float32
+
+
+# ------------------------------------------------------------------- points
+@pytest.mark.parametrize("d,R", [(1, 1), (16, 5), (130, 2)])
+def test_lms_setup_bit_exact(qk, d, R):
+    case = qc.make_case("net", "dsi", 2, d, R, seed=100 + d)
+    Ct = qc.u32_host(case.keep[3])
+    assert np.array_equal(Ct, case.Ct_ref)
+
+
+@pytest.mark.parametrize("order", ["natural", "gray"])
+@pytest.mark.parametrize("d", [1, 4, 37])
+def test_net_points_bit_exact(qk, order, d):
+    case = qc.make_case("net", "dsi", 2, d, 3, seed=7 + d, order=order)
+    for (i0, n) in [(0, 1), (0, 2), (0, 1 << 11), (5, 3001), (1 << 13, 777), ((1 << 20) - 9, 40)]:
+        X = torch.empty((2, n, d), dtype=torch.int32, device=qc.dev())
+        qk.gen_points(case.ps, 1, 2, i0, n, X)
+        got = qc.u32_host(X)
+        m = max(1, int(i0 + n - 1).bit_length())
+        for r in (1, 2):
+            want = o.net_points(case.Ct_ref[r], case.D[r], np.arange(i0, i0 + n), m, order)
+            assert np.array_equal(got[r - 1], want), (i0, n, r)
+
+
+@pytest.mark.parametrize("d", [1, 6, 40])
+def test_lattice_points_bit_exact(qk, d):
+    case = qc.make_case("lattice", "si", 2, d, 2, seed=50 + d)
+    for (i0, n) in [(0, 1), (0, 1 << 12), (3, 5000), ((1 << 31) - 5, 17)]:
+        X = torch.empty((2, n, d), dtype=torch.int32, device=qc.dev())
+        qk.gen_points(case.ps, 0, 2, i0, n, X)
+        got = qc.u32_host(X)
+        for r in range(2):
+            assert np.array_equal(got[r], o.lattice_points(case.g, case.D[r], np.arange(i0, i0 + n)))
+
+
+# ------------------------------------------------------------- first column
+FAMS = [("net", "dsi", 1), ("net", "dsi", 2), ("net", "dsi", 3), ("net", "dsi", 4),
+        ("lattice", "si", 1), ("lattice", "si", 2)]
+
+
+@pytest.mark.parametrize("kind,family,alpha", FAMS)
+@pytest.mark.parametrize("m,d", [(0, 3), (3, 5), (11, 2), (13, 33)])
+def test_kernel_col(qk, kind, family, alpha, m, d):
+    c = 0.8 ** np.arange(1, d + 1)
+    case = qc.make_case(kind, family, alpha, d, 3, seed=300 + 7 * m + d, c=c, zeta=1.7)
+    kern = qc.kernel_of(case)
+    n = 1 << m
+    for dt, tol in ((F64, 1e-13), (F32, 4e-6 if alpha < 4 else 2e-5)):
+        for form in (qk.QK_COL_K1, qk.QK_COL_P):
+            col = torch.empty((2, n), dtype=dt, device=qc.dev())
+            qk.kernel_col(case.ps, kern, 1, 2, m, col, form=form)
+            got = col.cpu().numpy().astype(np.float64)
+            for r in (1, 2):
+                k1, _ = case.k1_ref(r, m)
+                g = got[r - 1] if form == qk.QK_COL_K1 else case.zeta * (1.0 + got[r - 1])
+                assert qc.rel_err(g, k1) < tol, (dt, form, r, qc.rel_err(g, k1))
+
+
+# ---------------------------------------------------------------- spectrum
+def _lam_ref(case, r, m, eta):
+    k1, X = case.k1_ref(r, m)
+    return o.eigenvalues(case.family, k1, eta), k1, X
+
+
+@pytest.mark.parametrize("kind,family,alpha", [("net", "dsi", 2), ("net", "dsi", 4), ("lattice", "si", 1),
+                                               ("lattice", "si", 2)])
+@pytest.mark.parametrize("m", [1, 9, 13, 16])
+def test_eigs(qk, kind, family, alpha, m):
+    d = 6
+    case = qc.make_case(kind, family, alpha, d, 2, seed=900 + m, c=0.5 ** np.arange(d), zeta=1.3)
+    kern = qc.kernel_of(case)
+    eta = 1e-6
+    fam = qk.QK_DSI if family == "dsi" else qk.QK_SI
+    for dt, tol in ((F64, 1e-12), (F32, 1e-5)):
+        col = torch.empty((2, 1 << m), dtype=dt, device=qc.dev())
+        qk.kernel_col(case.ps, kern, 0, 2, m, col, form=qk.QK_COL_P)
+        lam = torch.empty((2, 1 << m), dtype=F64, device=qc.dev())
+        status = torch.zeros(1, dtype=torch.int32, device=qc.dev())
+        qk.eigs(fam, m, col, lam, zeta=case.zeta, eta=eta, form=qk.QK_COL_P, status=status)
+        if dt == F64:
+            qk.read_status(status)  # FP64 resolves every eigenvalue above the nugget
+        # FP32 eigenvalues carry errors ~ eps32 * ||k1||, larger than the nugget at
+        # this n: the smallest may go negative, which the status word then reports.
+        got = lam.cpu().numpy()
+        for r in range(2):
+            want, _, _ = _lam_ref(case, r, m, eta)
+            assert qc.rel_err(got[r], want) < tol, (dt, r, qc.rel_err(got[r], want))
+
+
+def test_eigs_reports_non_positive_definite(qk):
+    case = qc.make_case("net", "dsi", 2, 3, 1, seed=5)
+    kern = qc.kernel_of(case)
+    col = torch.empty((1, 256), dtype=F64, device=qc.dev())
+    qk.kernel_col(case.ps, kern, 0, 1, 8, col)
+    lam = torch.empty_like(col)
+    status = torch.zeros(1, dtype=torch.int32, device=qc.dev())
+    qk.eigs(qk.QK_DSI, 8, col, lam, eta=-1e6, status=status)
+    with pytest.raises(qk.QKError) as e:
+        qk.read_status(status)
+    assert e.value.code == qk.QK_ENOTPD
+    qk.read_status(status)  # cleared
+
+
+def _setup_spectrum(qk, case, m, dt, eta, R):
+    kern = qc.kernel_of(case)
+    fam = qk.QK_DSI if case.family == "dsi" else qk.QK_SI
+    col = torch.empty((R, 1 << m), dtype=dt, device=qc.dev())
+    qk.kernel_col(case.ps, kern, 0, R, m, col, form=qk.QK_COL_P)
+    lam = torch.empty((R, 1 << m), dtype=F64, device=qc.dev())
+    qk.eigs(fam, m, col, lam, zeta=case.zeta, eta=eta, form=qk.QK_COL_P)
+    return kern, fam, lam
+
+
+@pytest.mark.parametrize("kind,family,alpha", [("net", "dsi", 1), ("net", "dsi", 2), ("lattice", "si", 1),
+                                               ("lattice", "si", 2)])
+@pytest.mark.parametrize("m", [4, 10, 14])
+def test_solve_and_matvec(qk, kind, family, alpha, m):
+    """Forward error against the oracle on moderately conditioned systems (eta = 1e-3):
+    FP64 within max(1e-10, 20 cond eps64); FP32 + one refinement step (FP64 residual)
+    within max(1e-5, 20 (cond eps32)^2); plain FP32 within 20 cond eps32."""
+    d, R, nrhs, eta = 4, 2, 3, 1e-3
+    case = qc.make_case(kind, family, alpha, d, R, seed=1200 + m, c=1.0 / np.arange(1, d + 1) ** 2)
+    refs = []
+    for r in range(R):
+        lam_ref, k1, X = _lam_ref(case, r, m, eta)
+        Y = np.stack([np.sin(3.0 * (q + 1) * X[:, 0] / 2 ** 32) + X[:, 1] / 2 ** 33 for q in range(nrhs)])
+        if m <= 10:
+            K = o.gram_dense(case.family, alpha, X, case.c, case.zeta, eta)
+            Cref = o.cholesky_solve(K, Y.T)[0].T
+        else:
+            Cref = np.stack([o.spectral_solve(case.family, lam_ref, Y[q]) for q in range(nrhs)])
+        refs.append((Y, Cref, lam_ref))
+    y_h = np.stack([refs[r][0] for r in range(R)])
+    cond = max(float(np.max(rf[2]) / np.min(rf[2])) for rf in refs)
+    for dt, refine in ((F64, 0), (F32, 0), (F32, 1)):
+        if dt == F64:
+            tol = max(1e-10, 20 * cond * qc.EPS64)
+        elif refine:
+            tol = max(1e-5, 20 * (cond * qc.EPS32) ** 2)
+        else:
+            tol = 20 * cond * qc.EPS32
+        _, fam, lam = _setup_spectrum(qk, case, m, F64 if refine else dt, eta, R)
+        y = torch.tensor(y_h, dtype=dt, device=qc.dev())
+        c = torch.empty_like(y)
+        qk.solve(fam, m, lam, y, c, refine_steps=refine)
+        got = c.cpu().numpy().astype(np.float64)
+        for r in range(R):
+            assert qc.rel_err(got[r], refs[r][1]) < tol, (dt, refine, r, qc.rel_err(got[r], refs[r][1]), tol)
+        u = torch.empty_like(y)
+        qk.matvec(fam, m, lam, c, u)
+        # K c reproduces y up to the conditioning of the round trip
+        eps = qc.EPS64 if dt == F64 else qc.EPS32
+        assert qc.rel_err(u.cpu().numpy(), y_h) < max(1e-12 if dt == F64 else 2e-6, 20 * cond * eps)
+
+
+@pytest.mark.parametrize("kind,family,alpha", [("net", "dsi", 2), ("lattice", "si", 2)])
+def test_ill_conditioned_solve_has_small_backward_error(qk, kind, family, alpha):
+    """eta = 1e-8, cond up to ~1e12: the residual y - K c (K applied by the oracle from
+    its own eigenvalues) stays at FP64 rounding level even where the forward error cannot."""
+    d, R, m, eta = 4, 1, 14, 1e-8
+    case = qc.make_case(kind, family, alpha, d, R, seed=1300, c=1.0 / np.arange(1, d + 1) ** 2)
+    lam_ref, k1, X = _lam_ref(case, 0, m, eta)
+    Y = np.sin(5.0 * X[:, 0] / 2 ** 32)[None, None, :]
+    _, fam, lam = _setup_spectrum(qk, case, m, F64, eta, R)
+    y = torch.tensor(Y, dtype=F64, device=qc.dev())
+    c = torch.empty_like(y)
+    qk.solve(fam, m, lam, y, c)
+    cg = c.cpu().numpy()[0, 0]
+    res = Y[0, 0] - o.spectral_matvec(case.family, lam_ref, cg)
+    # normwise backward error of a transform-based solve: |y - K c| <~ m eps |K| |c|
+    bound = 8 * m * qc.EPS64 * float(np.max(lam_ref)) * float(np.max(np.abs(cg)))
+    assert np.max(np.abs(res)) < bound, (np.max(np.abs(res)), bound)
+
+
+# --------------------------------------------------------------- MLL + grad
+@pytest.mark.parametrize("kind,family,alpha", [("net", "dsi", 1), ("net", "dsi", 2), ("net", "dsi", 4),
+                                               ("lattice", "si", 1), ("lattice", "si", 2)])
+def test_mll_and_gradient_vs_dense(qk, kind, family, alpha):
+    d, R, nrhs, m, eta = 3, 2, 2, 8, 1e-4
+    gamma = np.array([0.9, 0.5, 0.3])
+    log_ls = np.array([0.1, -0.2, 0.05])
+    case = qc.make_case(kind, family, alpha, d, R, seed=77, c=o.effective_weights(gamma, log_ls), zeta=1.0)
+    kern, fam, lam = _setup_spectrum(qk, case, m, F64, eta, R)
+    n = 1 << m
+    ys = []
+    refs = []
+    for r in range(R):
+        X = case.points_ref(r, np.arange(n), m)
+        Y = np.stack([np.cos(2.0 * (q + 1) * X[:, 0] / 2 ** 32) + 0.1 * X[:, 2] / 2 ** 32 for q in range(nrhs)])
+        ys.append(Y)
+        K = o.gram_dense(case.family, alpha, X, case.c, 1.0, eta)
+        rr = []
+        for q in range(nrhs):
+            mll, quad, logdet, _ = o.mll_dense(K, Y[q])
+            mean, var = o.bc_posterior_dense(K, Y[q])
+            g = o.mll_grad_dense(case.family, alpha, X, Y[q], gamma, log_ls, eta)
+            rr.append((quad, logdet, mll, mean, var, g))
+        refs.append(rr)
+    y = torch.tensor(np.stack(ys), dtype=F64, device=qc.dev())
+    out = torch.empty((R, nrhs, 5), dtype=F64, device=qc.dev())
+    grad = torch.empty((R, nrhs, 2 * d + 2), dtype=F64, device=qc.dev())
+    qk.mll(case.ps, kern, 0, R, m, nrhs, eta, lam, y, out, grad)
+    go, gg = out.cpu().numpy(), grad.cpu().numpy()
+    for r in range(R):
+        for q in range(nrhs):
+            quad, logdet, mll, mean, var, g = refs[r][q]
+            assert abs(go[r, q, 0] - quad) < 1e-10 * abs(quad)
+            assert abs(go[r, q, 1] - logdet) < 1e-10 * max(1.0, abs(logdet))
+            assert abs(go[r, q, 2] - mll) < 1e-10 * abs(mll)
+            assert abs(go[r, q, 3] - mean) < 1e-10 * max(1.0, abs(mean))
+            assert abs(go[r, q, 4] - var) < 1e-9
+            assert qc.rel_err(gg[r, q, :d], g["dc"]) < 1e-9
+            assert abs(gg[r, q, d] - g["deta"]) < 1e-9 * max(1.0, abs(g["deta"]))
+            assert qc.rel_err(gg[r, q, d + 1:2 * d + 1], g["dmean_dc"]) < 1e-8
+            assert abs(gg[r, q, 2 * d + 1] - g["dmean_deta"]) < 1e-9 * max(1.0, abs(g["dmean_deta"]))
+
+
+def test_mll_gradient_matches_finite_differences_on_gpu(qk):
+    """Lattice + SI alpha=2, d=32, n=2^10, log-lengthscales 0 and log-nugget -12 (the
+    differentiation workload at the dense-oracle size): central differences with
+    h = 1e-6 of the GPU's own MLL against its hand-written gradient."""
+    from paper_2502_14256_gb300 import inputs
+    wl = inputs.workload("diff_small")
+    d, m = wl.d, wl.ms[0]
+    n = 1 << m
+    lat = inputs.make_lattice(wl.seed, d, 1, wl.extra["m_gen"])
+    X = o.lattice_points(lat.g, lat.D[0], np.arange(n))
+    y_h = inputs.rhs_product(X)
+    gd, Dd = qc.u32_tensor(lat.g), qc.u32_tensor(lat.D)
+    ps = qk.pointset(qk.QK_LATTICE, d, 1, g=gd, D=Dd)
+
+    def run(log_ls, log_eta):
+        w = torch.tensor(o.effective_weights(wl.gamma, log_ls), dtype=F64, device=qc.dev())
+        kern = qk.kernel(qk.QK_SI, wl.alpha, w, 1.0)
+        col = torch.empty((1, n), dtype=F64, device=qc.dev())
+        qk.kernel_col(ps, kern, 0, 1, m, col, form=qk.QK_COL_P)
+        lam = torch.empty_like(col)
+        qk.eigs(qk.QK_SI, m, col, lam, eta=math.exp(log_eta), form=qk.QK_COL_P)
+        y = torch.tensor(y_h, dtype=F64, device=qc.dev()).reshape(1, 1, n)
+        out = torch.empty((1, 1, 5), dtype=F64, device=qc.dev())
+        grad = torch.empty((1, 1, 2 * d + 2), dtype=F64, device=qc.dev())
+        qk.mll(ps, kern, 0, 1, m, 1, math.exp(log_eta), lam, y, out, grad)
+        return out.cpu().numpy().ravel(), grad.cpu().numpy().ravel()
+
+    log_ls = wl.log_ls.copy()
+    log_eta = math.log(wl.eta)
+    out0, g0 = run(log_ls, log_eta)
+    cw = o.effective_weights(wl.gamma, log_ls)
+    dtheta = cw * g0[:d]
+    h = 1e-6
+    for j in (0, 5, 31):
+        e = np.zeros(d)
+        e[j] = h
+        fd = (run(log_ls + e, log_eta)[0][2] - run(log_ls - e, log_eta)[0][2]) / (2 * h)
+        assert abs(fd - dtheta[j]) < 1e-5 * max(1.0, abs(fd)), (j, fd, dtheta[j])
+    # dMLL/dlog(eta) is ~1e-19 here (K ~ 1e16 I): compare absolutely
+    fd = (run(log_ls, log_eta + h)[0][2] - run(log_ls, log_eta - h)[0][2]) / (2 * h)
+    assert abs(fd - wl.eta * g0[d]) < 1e-6
+    # and the dense oracle's gradient at the same point
+    gref = o.mll_grad_dense("si", wl.alpha, X, y_h, wl.gamma, log_ls, wl.eta)
+    assert qc.rel_err(dtheta, gref["dtheta"]) < 1e-8
+
+
+# ----------------------------------------------------------------- batching
+def test_batch_schedule_matches_per_call_results_and_replays_in_a_graph(qk):
+    tasks, keep, refs = [], [], []
+    specs = [("net", "dsi", 2, 5, 3, 10, 2), ("lattice", "si", 1, 4, 2, 12, 1), ("net", "dsi", 1, 3, 2, 6, 3),
+             ("lattice", "si", 2, 8, 1, 9, 2)]
+    for t, (kind, family, alpha, d, R, m, nrhs) in enumerate(specs):
+        case = qc.make_case(kind, family, alpha, d, R, seed=4000 + t, c=0.7 ** np.arange(1, d + 1))
+        kern = qc.kernel_of(case)
+        n = 1 << m
+        y = torch.randn((R, nrhs, n), dtype=F64, device=qc.dev(), generator=torch.Generator(qc.dev()).manual_seed(t))
+        out = torch.zeros((R, nrhs, 5), dtype=F64, device=qc.dev())
+        grad = torch.zeros((R, nrhs, 2 * d + 2), dtype=F64, device=qc.dev())
+        c = torch.zeros_like(y)
+        lam = torch.zeros((R, n), dtype=F64, device=qc.dev())
+        keep += [case, y, out, grad, c, lam]
+        tasks.append(qk.Task(case.ps, kern, m, nrhs, 1e-5, y.data_ptr(), c.data_ptr(), lam.data_ptr(),
+                             out.data_ptr(), grad.data_ptr()))
+        # per-call reference
+        _, fam, lam_r = _setup_spectrum(qk, case, m, F64, 1e-5, R)
+        out_r = torch.empty_like(out)
+        grad_r = torch.empty_like(grad)
+        qk.mll(case.ps, kern, 0, R, m, nrhs, 1e-5, lam_r, y, out_r, grad_r)
+        c_r = torch.empty_like(y)
+        qk.solve(fam, m, lam_r, y, c_r)
+        refs.append((lam_r, out_r, grad_r, c_r))
+    ws = qk.workspace(qk.batch_workspace_bytes(tasks, F64))
+    qk.batch_plan(tasks, F64, 0, ws)
+    qk.batch_run(ws)
+    torch.cuda.synchronize()
+
+    def check():
+        for t in range(len(specs)):
+            lam, out, grad, c = keep[6 * t + 5], keep[6 * t + 2], keep[6 * t + 3], keep[6 * t + 4]
+            lam_r, out_r, grad_r, c_r = refs[t]
+            assert torch.allclose(lam, lam_r, rtol=1e-13, atol=0)
+            assert torch.allclose(out, out_r, rtol=1e-12, atol=1e-13)
+            assert torch.allclose(grad, grad_r, rtol=1e-10, atol=1e-12)
+            assert torch.allclose(c, c_r, rtol=1e-12, atol=1e-12)
+
+    check()
+    for t in range(len(specs)):
+        keep[6 * t + 2].zero_()
+        keep[6 * t + 4].zero_()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            qk.batch_run(ws, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    check()
+
+
+# --------------------------------------------------------- public transforms
+@pytest.mark.parametrize("m", [0, 1, 5, 12, 13, 14, 17, 20, 21])
+def test_fwht_fftbr_ifftbr(qk, m):
+    n = 1 << m
+    nvec = 3 if m < 20 else 2
+    rng = np.random.default_rng(m)
+    x = rng.standard_normal((nvec, n))
+    want = o.hadamard_apply(x) / math.sqrt(n)
+    for dt, tol in ((F64, 1e-13), (F32, 1e-6 * max(1, m))):
+        t = torch.tensor(x, dtype=dt, device=qc.dev())
+        qk.fwht(m, t)
+        assert qc.rel_err(t.cpu().numpy(), want) < tol, (dt, m)
+    z = rng.standard_normal((nvec, n)) + 1j * rng.standard_normal((nvec, n))
+    zw = np.fft.fft(o.to_linear_order(z, m), axis=-1) / math.sqrt(n)
+    for dt, tol in ((F64, 1e-13), (F32, 2e-6 * max(1, m))):
+        t = torch.tensor(np.stack([z.real, z.imag], axis=-1), dtype=dt, device=qc.dev()).contiguous()
+        qk.fftbr(m, t)
+        got = t.cpu().numpy()
+        assert qc.rel_err(got[..., 0] + 1j * got[..., 1], zw) < tol, (dt, m)
+        qk.ifftbr(m, t)
+        got = t.cpu().numpy()
+        assert qc.rel_err(got[..., 0] + 1j * got[..., 1], z) < tol, (dt, m)
