@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--R", type=int, default=64, help="randomizations per GPU")
     ap.add_argument("--m", type=int, default=20)
+    ap.add_argument("--refine", type=int, default=1, help="refinement steps of the FP32 solve")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -127,7 +128,8 @@ class Pipeline:
     def __init__(self, qk, torch, dev, W, dtype, refine):
         self.qk, self.torch = qk, torch
         R, n, d = W["R"], W["n"], W["d"]
-        self.y = W["y64"].to(dtype).contiguous()
+        # both precisions see the same inputs: y rounded to FP32 once
+        self.y = W["y64"].to(torch.float32).to(dtype).contiguous()
         self.c = torch.empty_like(self.y)
         self.lam = torch.empty((R, n), dtype=torch.float64, device=dev)
         self.out = torch.empty((R, 1, qk.QK_MLL_NOUT), dtype=torch.float64, device=dev)
@@ -235,7 +237,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     # ---- the headline: FP32-refined pipeline, device-resident inputs
-    P32 = Pipeline(qk, torch, dev, W, torch.float32, refine=1)
+    P32 = Pipeline(qk, torch, dev, W, torch.float32, refine=args.refine)
     for _ in range(args.warmup):
         P32.step()
     qk.read_status(P32.status)

@@ -29,7 +29,14 @@ struct Plan {
 static std::mutex g_mu;
 static std::unordered_map<const void *, Plan> g_plans;
 
-static size_t task_scratch(const qk_task &t, int dtype) {
+// A task runs fused (qk_fused.cu) when its family and size allow it and no
+// refinement is requested; otherwise it runs as the sequence of standalone ops.
+static bool use_fused(const qk_task &t, int dtype, int refine) {
+  return refine == 0 && fused_supported(t, dtype);
+}
+
+static size_t task_scratch(const qk_task &t, int dtype, int refine) {
+  if (use_fused(t, dtype, refine)) return fused_ws_bytes(t, dtype);
   const uint32_t R = t.ps.R;
   const size_t tb = dtype == QK_F64 ? 8 : 4;
   const size_t col = align256(tb * ((uint64_t)R << t.m));
@@ -43,11 +50,12 @@ static size_t task_scratch(const qk_task &t, int dtype) {
   return col + s;
 }
 
-static int make_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, Plan &p) {
+static int make_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, int32_t refine, Plan &p) {
   if (!tasks && ntasks) return fail(QK_EINVAL, "task list is NULL");
   if (dtype != QK_F64 && dtype != QK_F32) return fail(QK_EINVAL, "dtype must be QK_F64 or QK_F32");
   p.tasks.assign(tasks, tasks + ntasks);
   p.dtype = dtype;
+  p.refine = refine;
   size_t scratch = 0, lam = 0;
   for (uint32_t i = 0; i < ntasks; ++i) {
     const qk_task &t = tasks[i];
@@ -56,9 +64,9 @@ static int make_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, Plan 
     if ((rc = check_kernel(&t.k, &t.ps))) return fail(rc, "task %u: invalid kernel", i);
     if (t.m > QK_MAX_M) return fail(QK_EINVAL, "task %u: m = %u too large", i, t.m);
     if (t.nrhs == 0 || !t.y || !t.out) return fail(QK_EINVAL, "task %u: needs nrhs >= 1, y and out", i);
-    const size_t s = task_scratch(t, dtype);
+    const size_t s = task_scratch(t, dtype, refine);
     if (s > scratch) scratch = s;
-    if (!t.lam) {
+    if (!t.lam && !use_fused(t, dtype, refine)) {
       const size_t l = align256(sizeof(double) * ((uint64_t)t.ps.R << t.m));
       if (l > lam) lam = l;
     }
@@ -77,6 +85,11 @@ static int run_plan(const Plan &p, unsigned char *ws, uint32_t *status, cudaStre
     unsigned char *scr = ws + align256(tb * ((uint64_t)R << t.m));
     double *lam = t.lam ? t.lam : (double *)(ws + p.lam_off);
     const ColJob job = make_job(&t.ps, &t.k, 0, R, t.m);
+    if (use_fused(t, p.dtype, p.refine)) {
+      int rc = run_fused(t, job, p.dtype, ws, status, st);
+      if (rc) return rc;
+      continue;
+    }
     int rc = launch_kernel_col(job, p.dtype, QK_COL_P, col, st);
     if (rc) return rc;
     if ((rc = op_eigs(t.k.family, t.m, R, p.dtype, QK_COL_P, col, t.k.zeta, t.eta, lam, scr, status, st))) return rc;
@@ -95,20 +108,21 @@ extern "C" {
 int qk_batch_workspace_bytes(const qk_task *tasks, uint32_t ntasks, int32_t dtype, size_t *bytes) {
   if (!bytes) return fail(QK_EINVAL, "bytes is NULL");
   Plan p;
-  int rc = make_plan(tasks, ntasks, dtype, p);
+  int rc = make_plan(tasks, ntasks, dtype, 0, p);
   if (rc) return rc;
-  *bytes = p.total;
+  Plan pr;  // refinement may need the larger unfused workspace
+  if ((rc = make_plan(tasks, ntasks, dtype, 1, pr))) return rc;
+  *bytes = p.total > pr.total ? p.total : pr.total;
   return QK_OK;
 }
 
 int qk_batch_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, int32_t refine_steps, void *ws,
                   size_t ws_bytes, qk_stream stream) {
   (void)stream;
-  Plan p;
-  int rc = make_plan(tasks, ntasks, dtype, p);
-  if (rc) return rc;
   if (refine_steps < 0 || refine_steps > 8) return fail(QK_EINVAL, "refine_steps must be 0..8");
-  p.refine = refine_steps;
+  Plan p;
+  int rc = make_plan(tasks, ntasks, dtype, refine_steps, p);
+  if (rc) return rc;
   if (p.total && (!ws || ws_bytes < p.total))
     return fail(QK_EWORKSPACE, "batch workspace has %zu bytes, %zu needed", ws_bytes, p.total);
   if (((uintptr_t)ws & 255u) != 0) return fail(QK_EINVAL, "workspace must be 256-byte aligned");

@@ -39,7 +39,7 @@ inline void smem_optin(size_t bytes) {
 }
 
 // Round x up to a multiple of 256 bytes (workspace sub-allocation alignment).
-inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+__host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // ---------------------------------------------------------------- device side
 template <typename T> struct Cplx;
@@ -60,6 +60,21 @@ __device__ __forceinline__ float word_to_unit(float, uint32_t Z) {
 }
 __device__ __forceinline__ double word_to_unit(double, uint32_t Z) {
   return __hiloint2double((int)(0x3FF00000u | (Z >> 12)), (int)(Z << 20)) - 1.0;
+}
+
+// Sum of v over the CTA (blockDim.x a multiple of 32, at most 1024); the result is
+// valid in thread 0.  sh: 32 doubles of shared scratch.  All threads must call it.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += sh[q];
+  return s;
 }
 
 // Spread the low 10 bits of v so that bit p lands on bit 3p (30-bit result).

@@ -88,8 +88,12 @@ __device__ __forceinline__ T factor(uint32_t w) {
   else return si_factor<T, ALPHA>(w);
 }
 
+// Fused multiply-add in the precision of the arguments (never promoted).
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return fma(a, b, c); }
+
 // p <- (1 + p)(1 + a) - 1, keeping p = prod(1 + a_j) - 1 with relative precision.
 template <typename T>
-__device__ __forceinline__ T pm1_step(T p, T a) { return fma(p, a, p + a); }
+__device__ __forceinline__ T pm1_step(T p, T a) { return fmadd(p, a, p + a); }
 
 }  // namespace qk

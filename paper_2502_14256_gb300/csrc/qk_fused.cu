@@ -1,0 +1,446 @@
+// Fused solve + marginal log-likelihood + gradient for digital nets with DSI
+// kernels (arXiv 2502.14256, Sec. 5.3-5.4), n = 2^m with LOGT < m <= 2 LOGT - 5.
+//
+// The length-n Hadamard transform is split at bit LOGT (tile = 2^LOGT elements:
+// 8192 FP32 / 4096 FP64).  Three phases per randomization r:
+//   A  (contiguous tiles)  first column p = k_1/zeta - 1 by the column sweep, stored;
+//      low LOGT bits of the WHT of p and of every right-hand side y -> p', y';
+//      FP64 partial sums of p and y.
+//   B  (column tiles: the m - LOGT high bits x a run of contiguous low indices)
+//      high bits of the WHT -> lambda = zeta H p + zeta n [w = 0] + eta (and
+//      log lambda), Y = H y; epilogue c^_w = Y_w/(n lambda_w),
+//      g_w = (Y_w^2/(n lambda_w^2) - 1/lambda_w)/2 with partial sums of the
+//      quadratic form and of g; high bits of the inverse WHT of c^ and g.
+//   C  (contiguous tiles)  low bits of the inverse -> c = K^-1 y (stored) and
+//      u = H g; gradient sweep sum_i u_i dk1_i/dc_j, sum_i dk1_i/dc_j, with the
+//      factors recomputed and k_1 from the stored p.
+// A final kernel reduces the partial sums into the MLL outputs and gradient.
+//
+// Inside a tile every thread holds the L elements e = threadIdx.x + 256 l: the
+// tile bits carried by l (the top log2 L bits) are transformed in registers, the
+// low 8 bits in padded shared memory in radix-16 rounds.
+#include <cmath>
+#include <vector>
+
+#include "qk_column.cuh"
+#include "qk_common.cuh"
+#include "qk_factors.cuh"
+#include "qk_internal.h"
+
+namespace qk {
+
+template <typename T> struct FCfg;
+template <> struct FCfg<float> { static constexpr int LOGT = 13, LOGL = 5, L = 32, PAD = 5; };
+template <> struct FCfg<double> { static constexpr int LOGT = 12, LOGL = 4, L = 16, PAD = 4; };
+constexpr int kFNT = 256, kLOGNT = 8;
+
+struct FTask {
+  ColJob job;
+  uint32_t nrhs, tiles;  // tiles = n >> LOGT
+  int cB;                // phase-B contiguous column bits (= 2 LOGT - m)
+  double eta;
+  const void *y;
+  void *c;
+  double *lam, *out, *grad;
+  void *p, *pT, *yT, *gT;               // (R, n), (R, n), (R, nrhs, n), (R, nrhs, n)
+  double *sp, *sy, *ld, *qg, *gr;       // partial sums
+  uint32_t *status;
+};
+
+template <typename T>
+__device__ __forceinline__ int fpad(int e) { return e + (e >> FCfg<T>::PAD); }
+
+template <typename T>
+__host__ __device__ constexpr size_t tile_smem_bytes() {
+  return (size_t)((1 << FCfg<T>::LOGT) + ((1 << FCfg<T>::LOGT) >> FCfg<T>::PAD)) * sizeof(T);
+}
+
+// Radix-2^R WHT round on tile bits [b, b+R) held in shared memory.
+template <typename T, int R>
+__device__ __forceinline__ void smem_round(T *sm, int b) {
+  constexpr int G = (1 << FCfg<T>::LOGT) >> R;
+  for (int g = threadIdx.x; g < G; g += kFNT) {
+    const int e0 = (g & ((1 << b) - 1)) | ((g >> b) << (b + R));
+    T v[1 << R];
+#pragma unroll
+    for (int q = 0; q < (1 << R); ++q) v[q] = sm[fpad<T>(e0 | (q << b))];
+#pragma unroll
+    for (int h = 0; h < R; ++h)
+#pragma unroll
+      for (int q = 0; q < (1 << R); ++q)
+        if (!(q & (1 << h))) {
+          const T a = v[q], bb = v[q | (1 << h)];
+          v[q] = a + bb;
+          v[q | (1 << h)] = a - bb;
+        }
+#pragma unroll
+    for (int q = 0; q < (1 << R); ++q) sm[fpad<T>(e0 | (q << b))] = v[q];
+  }
+}
+
+// WHT butterflies over tile bits [c, LOGT) of the tile held as v[l] at e = tid + 256 l;
+// the result is returned in v with the same mapping.  sm: the padded tile scratch.
+template <typename T>
+__device__ __forceinline__ void tile_wht(T (&v)[FCfg<T>::L], T *sm, int c) {
+  constexpr int L = FCfg<T>::L, LOGL = FCfg<T>::LOGL;
+#pragma unroll
+  for (int h = 0; h < LOGL; ++h) {
+    if (kLOGNT + h >= c) {
+#pragma unroll
+      for (int q = 0; q < L; ++q)
+        if (!(q & (1 << h))) {
+          const T a = v[q], b = v[q | (1 << h)];
+          v[q] = a + b;
+          v[q | (1 << h)] = a - b;
+        }
+    }
+  }
+  if (c < kLOGNT) {
+#pragma unroll
+    for (int l = 0; l < L; ++l) sm[fpad<T>(threadIdx.x + (l << kLOGNT))] = v[l];
+    __syncthreads();
+    for (int b = c; b < kLOGNT; b += 4) {
+      const int r = (kLOGNT - b) < 4 ? (kLOGNT - b) : 4;
+      if (r == 4) smem_round<T, 4>(sm, b);
+      else if (r == 3) smem_round<T, 3>(sm, b);
+      else if (r == 2) smem_round<T, 2>(sm, b);
+      else smem_round<T, 1>(sm, b);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = sm[fpad<T>(threadIdx.x + (l << kLOGNT))];
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ float fused_log(float v) { return logf(v); }
+__device__ __forceinline__ double fused_log(double v) { return log(v); }
+
+// ------------------------------------------------------------------ phase A
+template <typename T, int FAM, int ALPHA>
+__global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
+  constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const ColJob &job = ft.job;
+  const uint32_t d = job.d;
+  double *wd;
+  DiffTables tb;
+  carve_tables<L>(smem, d, &wd, tb);
+  T *wT = reinterpret_cast<T *>(wd);
+  T *sm = reinterpret_cast<T *>(smem + align256(col_smem_bytes<L>(d)));
+  double *red = reinterpret_cast<double *>(smem + align256(col_smem_bytes<L>(d)) + tile_smem_bytes<T>());
+  const uint32_t r = blockIdx.y, tile = blockIdx.x;
+  const uint64_t n = 1ull << job.m, base = (uint64_t)tile << LOGT;
+  const int t = threadIdx.x;
+  for (uint32_t q = t; q < d; q += kFNT) wT[q] = (T)job.w[q];
+  build_tables<L>(job, job.Ct + (size_t)r * d * 32, job.g, base, tb);
+  __syncthreads();
+  uint32_t bi[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) bi[l] = __brev((uint32_t)(base + t + (l << kLOGNT)));
+  T p[L];
+  column_sweep<T, FAM, ALPHA, L>(job, tb, wT, bi, p);
+  T *P = reinterpret_cast<T *>(ft.p) + (uint64_t)r * n + base;
+  T ps = T(0);
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    P[t + (l << kLOGNT)] = p[l];
+    ps += p[l];
+  }
+  const double sps = block_sum((double)ps, red);
+  if (t == 0) ft.sp[(uint64_t)r * ft.tiles + tile] = sps;
+  tile_wht<T>(p, sm, 0);
+  T *PT = reinterpret_cast<T *>(ft.pT) + (uint64_t)r * n + base;
+#pragma unroll
+  for (int l = 0; l < L; ++l) PT[t + (l << kLOGNT)] = p[l];
+  for (uint32_t q = 0; q < ft.nrhs; ++q) {
+    const uint64_t v = (uint64_t)r * ft.nrhs + q;
+    const T *Y = reinterpret_cast<const T *>(ft.y) + v * n + base;
+    T yv[L];
+    T ys = T(0);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      yv[l] = Y[t + (l << kLOGNT)];
+      ys += yv[l];
+    }
+    const double sys = block_sum((double)ys, red);
+    if (t == 0) ft.sy[v * ft.tiles + tile] = sys;
+    tile_wht<T>(yv, sm, 0);
+    T *YT = reinterpret_cast<T *>(ft.yT) + v * n + base;
+#pragma unroll
+    for (int l = 0; l < L; ++l) YT[t + (l << kLOGNT)] = yv[l];
+  }
+}
+
+// ------------------------------------------------------------------ phase B
+template <typename T>
+__global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
+  constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sm = reinterpret_cast<T *>(smem);
+  T *ilv = reinterpret_cast<T *>(smem + tile_smem_bytes<T>());      // 1 / lambda, tile layout
+  T *gst = reinterpret_cast<T *>(smem + 2 * tile_smem_bytes<T>());  // g before its transform
+  double *red = reinterpret_cast<double *>(smem + 3 * tile_smem_bytes<T>());
+  const uint32_t r = blockIdx.y, tau = blockIdx.x;
+  const int c = ft.cB, t = threadIdx.x;
+  const uint64_t n = 1ull << ft.job.m;
+  // element (t, l) of the tile is w = (row << LOGT) | (tau << c) | col, e = t + 256 l
+  const uint32_t tcol = tau << c;  // fused sizes keep n <= 2^(2 LOGT - 5) < 2^32
+  auto widx = [&](int l) -> uint32_t {
+    const uint32_t e = t + (l << kLOGNT);
+    return ((e >> c) << LOGT) | tcol | (e & ((1u << c) - 1));
+  };
+  const T *PT = reinterpret_cast<const T *>(ft.pT) + (uint64_t)r * n;
+  T lam[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) lam[l] = PT[widx(l)];
+  tile_wht<T>(lam, sm, c);
+  const T zeta = (T)ft.job.zeta, eta = (T)ft.eta, zn = (T)(ft.job.zeta * (double)n);
+  bool bad = false;
+  T lds = T(0);
+  double *LAM = ft.lam ? ft.lam + (uint64_t)r * n : nullptr;
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    const uint32_t wl = widx(l);
+    T v = fmadd(zeta, lam[l], eta);
+    if (wl == 0) v += zn;
+    bad |= !(v > T(0));
+    lds += fused_log(v);
+    if (LAM) LAM[wl] = (double)v;
+    ilv[fpad<T>(t + (l << kLOGNT))] = T(1) / v;  // each thread reads back only its own entries
+  }
+  if (bad && ft.status) atomicOr(ft.status, (uint32_t)QK_STATUS_NOTPD);
+  const double ldsum = block_sum((double)lds, red);
+  if (t == 0) ft.ld[(uint64_t)r * ft.tiles + tau] = ldsum;
+  const T inv_n = T(1) / (T)n;
+  for (uint32_t q = 0; q < ft.nrhs; ++q) {
+    const uint64_t v = (uint64_t)r * ft.nrhs + q;
+    T *YT = reinterpret_cast<T *>(ft.yT) + v * n;
+    T *GT = reinterpret_cast<T *>(ft.gT) + v * n;
+    T y[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) y[l] = YT[widx(l)];
+    tile_wht<T>(y, sm, c);
+    T quad = T(0), gs = T(0);
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      const int e = fpad<T>(t + (l << kLOGNT));  // this thread's own entries only
+      const T il = ilv[e];
+      const T ch = y[l] * inv_n * il;  // c^_w = Y_w / (n lambda_w)
+      const T a = ch * y[l];           // Y_w^2 / (n lambda_w)
+      quad += a;
+      const T gg = T(0.5) * (a - T(1)) * il;
+      gs += gg;
+      y[l] = ch;
+      gst[e] = gg;
+    }
+    tile_wht<T>(y, sm, c);
+#pragma unroll
+    for (int l = 0; l < L; ++l) YT[widx(l)] = y[l];
+#pragma unroll
+    for (int l = 0; l < L; ++l) y[l] = gst[fpad<T>(t + (l << kLOGNT))];
+    tile_wht<T>(y, sm, c);
+#pragma unroll
+    for (int l = 0; l < L; ++l) GT[widx(l)] = y[l];
+    const double sq = block_sum((double)quad, red);
+    const double sg = block_sum((double)gs, red);
+    if (t == 0) {
+      ft.qg[(v * ft.tiles + tau) * 2 + 0] = sq;
+      ft.qg[(v * ft.tiles + tau) * 2 + 1] = sg;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ phase C
+template <typename T, int FAM, int ALPHA>
+__global__ void __launch_bounds__(kFNT) k_fused_C(FTask ft) {
+  constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const ColJob &job = ft.job;
+  const uint32_t d = job.d;
+  double *wd;
+  DiffTables tb;
+  carve_tables<L>(smem, d, &wd, tb);
+  T *wT = reinterpret_cast<T *>(wd);
+  T *sm = reinterpret_cast<T *>(smem + align256(col_smem_bytes<L>(d)));
+  double *red = reinterpret_cast<double *>(smem + align256(col_smem_bytes<L>(d)) + tile_smem_bytes<T>());
+  const uint32_t v = blockIdx.y, r = v / ft.nrhs, tile = blockIdx.x;
+  const uint64_t n = 1ull << job.m, base = (uint64_t)tile << LOGT;
+  const int t = threadIdx.x;
+  const T *YT = reinterpret_cast<const T *>(ft.yT) + (uint64_t)v * n + base;
+  const T *GT = reinterpret_cast<const T *>(ft.gT) + (uint64_t)v * n + base;
+  T cc[L], uu[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) cc[l] = YT[t + (l << kLOGNT)];
+  tile_wht<T>(cc, sm, 0);
+  if (ft.c) {
+    T *Cv = reinterpret_cast<T *>(ft.c) + (uint64_t)v * n + base;
+#pragma unroll
+    for (int l = 0; l < L; ++l) Cv[t + (l << kLOGNT)] = cc[l];
+  }
+  if (!ft.grad) return;
+#pragma unroll
+  for (int l = 0; l < L; ++l) uu[l] = GT[t + (l << kLOGNT)];
+  tile_wht<T>(uu, sm, 0);
+  for (uint32_t q = t; q < d; q += kFNT) wT[q] = (T)job.w[q];
+  build_tables<L>(job, job.Ct + (size_t)r * d * 32, job.g, base, tb);
+  const T *P = reinterpret_cast<const T *>(ft.p) + (uint64_t)r * n + base;
+  const T zeta = (T)job.zeta;
+  T k1[L];
+  uint32_t bi[L];
+  bool ok[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    k1[l] = zeta * (T(1) + P[t + (l << kLOGNT)]);
+    bi[l] = __brev((uint32_t)(base + t + (l << kLOGNT)));
+    ok[l] = true;
+  }
+  __syncthreads();
+  gradient_sweep<T, FAM, ALPHA, L>(job, tb, wT, bi, k1, uu, ok, red);
+  __syncthreads();
+  double *dst = ft.gr + ((uint64_t)v * ft.tiles + tile) * 2 * d;
+  for (uint32_t q = t; q < 2 * d; q += kFNT) {
+    double s = 0.0;
+#pragma unroll
+    for (int wp = 0; wp < kFNT / 32; ++wp) s += red[(size_t)wp * 2 * d + q];
+    dst[q] = s;
+  }
+}
+
+// ------------------------------------------------------------------ final
+__global__ void __launch_bounds__(256) k_fused_final(FTask ft) {
+  __shared__ double sh[32];
+  const uint32_t v = blockIdx.x, r = v / ft.nrhs;
+  const uint32_t tiles = ft.tiles, d = ft.job.d;
+  const double n = (double)(1ull << ft.job.m), zeta = ft.job.zeta;
+  double q = 0, gsum = 0, ld = 0, sp = 0, sy = 0;
+  for (uint32_t b = threadIdx.x; b < tiles; b += blockDim.x) {
+    q += ft.qg[((uint64_t)v * tiles + b) * 2 + 0];
+    gsum += ft.qg[((uint64_t)v * tiles + b) * 2 + 1];
+    ld += ft.ld[(uint64_t)r * tiles + b];
+    sp += ft.sp[(uint64_t)r * tiles + b];
+    sy += ft.sy[(uint64_t)v * tiles + b];
+  }
+  q = block_sum(q, sh);
+  gsum = block_sum(gsum, sh);
+  ld = block_sum(ld, sh);
+  sp = block_sum(sp, sh);
+  sy = block_sum(sy, sh);
+  __shared__ double res[5];
+  if (threadIdx.x == 0) {
+    res[0] = q, res[1] = gsum, res[2] = ld, res[3] = sp, res[4] = sy;
+  }
+  __syncthreads();
+  const double lam0 = zeta * (n + res[3]) + ft.eta;  // lambda_0 from the FP64 sum of p
+  const double mfac = -zeta * res[4] / (lam0 * lam0);
+  if (threadIdx.x == 0) {
+    double *o = ft.out + (uint64_t)v * QK_MLL_NOUT;
+    o[QK_MLL_QUAD] = res[0];
+    o[QK_MLL_LOGDET] = res[2];
+    o[QK_MLL_MLL] = -0.5 * res[0] - 0.5 * res[2] - 0.5 * n * 1.8378770664093454836;
+    o[QK_MLL_MEAN] = zeta * res[4] / lam0;
+    o[QK_MLL_VAR] = zeta * ((zeta * res[3] + ft.eta) / lam0);  // zeta (lambda_0 - zeta n) / lambda_0
+  }
+  if (!ft.grad) return;
+  double *g = ft.grad + (uint64_t)v * (2 * d + 2);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint32_t j = warp; j < 2 * d; j += blockDim.x >> 5) {
+    double s = 0.0;
+    for (uint32_t b = lane; b < tiles; b += 32) s += ft.gr[((uint64_t)v * tiles + b) * 2 * d + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+      if (j < d) g[j] = s;
+      else g[d + 1 + (j - d)] = mfac * s;
+    }
+  }
+  if (threadIdx.x == 0) {
+    g[d] = res[1];
+    g[2 * d + 1] = mfac;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+bool fused_supported(const qk_task &t, int dtype) {
+  if (t.k.family != QK_DSI || t.ps.kind != QK_NET_B2) return false;
+  const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
+  return (int)t.m > LOGT && (int)t.m <= 2 * LOGT - 5;
+}
+
+static size_t fused_elem(int dtype) { return dtype == QK_F64 ? 8 : 4; }
+
+size_t fused_ws_bytes(const qk_task &t, int dtype) {
+  const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
+  const uint64_t R = t.ps.R, n = 1ull << t.m, tiles = n >> LOGT, nv = R * t.nrhs;
+  const size_t e = fused_elem(dtype);
+  size_t s = 2 * align256(e * R * n) + 2 * align256(e * nv * n);
+  s += 2 * align256(8 * R * tiles) + align256(8 * nv * tiles) + align256(16 * nv * tiles);
+  s += align256(8 * nv * tiles * 2 * (uint64_t)t.ps.d);
+  return s;
+}
+
+template <typename T, int FAM, int ALPHA>
+static int launch_fused_t(const FTask &ft, cudaStream_t st) {
+  constexpr int L = FCfg<T>::L;
+  const uint32_t R = ft.job.nr, d = ft.job.d;
+  const size_t colb = align256(col_smem_bytes<L>(d));
+  const size_t smA = colb + tile_smem_bytes<T>() + 32 * sizeof(double);
+  const size_t smB = 3 * tile_smem_bytes<T>() + 32 * sizeof(double);
+  const size_t smC = colb + tile_smem_bytes<T>() + (size_t)(kFNT / 32) * 2 * d * sizeof(double);
+  smem_optin<k_fused_A<T, FAM, ALPHA>>(smA);
+  smem_optin<k_fused_B<T>>(smB);
+  smem_optin<k_fused_C<T, FAM, ALPHA>>(smC);
+  k_fused_A<T, FAM, ALPHA><<<dim3(ft.tiles, R), kFNT, smA, st>>>(ft);
+  int rc = check_launch("fused A");
+  if (rc) return rc;
+  k_fused_B<T><<<dim3(ft.tiles, R), kFNT, smB, st>>>(ft);
+  if ((rc = check_launch("fused B"))) return rc;
+  if (ft.c || ft.grad) {
+    k_fused_C<T, FAM, ALPHA><<<dim3(ft.tiles, R * ft.nrhs), kFNT, smC, st>>>(ft);
+    if ((rc = check_launch("fused C"))) return rc;
+  }
+  k_fused_final<<<R * ft.nrhs, 256, 0, st>>>(ft);
+  return check_launch("fused final");
+}
+
+template <typename T>
+static int dispatch_fused(const FTask &ft, cudaStream_t st) {
+  switch (ft.job.alpha) {
+    case 1: return launch_fused_t<T, 0, 1>(ft, st);
+    case 2: return launch_fused_t<T, 0, 2>(ft, st);
+    case 3: return launch_fused_t<T, 0, 3>(ft, st);
+    case 4: return launch_fused_t<T, 0, 4>(ft, st);
+    default: return fail(QK_EINVAL, "DSI order must be 1..4");
+  }
+}
+
+int run_fused(const qk_task &t, const ColJob &job, int dtype, void *ws, uint32_t *status, cudaStream_t st) {
+  const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
+  const uint64_t R = t.ps.R, n = 1ull << t.m, tiles = n >> LOGT, nv = R * t.nrhs;
+  const size_t e = fused_elem(dtype);
+  unsigned char *p = (unsigned char *)ws;
+  FTask ft;
+  ft.job = job;
+  ft.nrhs = t.nrhs;
+  ft.tiles = (uint32_t)tiles;
+  ft.cB = 2 * LOGT - (int)t.m;
+  ft.eta = t.eta;
+  ft.y = t.y;
+  ft.c = t.c;
+  ft.lam = t.lam;
+  ft.out = t.out;
+  ft.grad = t.grad;
+  ft.status = status;
+  ft.p = p, p += align256(e * R * n);
+  ft.pT = p, p += align256(e * R * n);
+  ft.yT = p, p += align256(e * nv * n);
+  ft.gT = p, p += align256(e * nv * n);
+  ft.sp = (double *)p, p += align256(8 * R * tiles);
+  ft.ld = (double *)p, p += align256(8 * R * tiles);
+  ft.sy = (double *)p, p += align256(8 * nv * tiles);
+  ft.qg = (double *)p, p += align256(16 * nv * tiles);
+  ft.gr = (double *)p;
+  return dtype == QK_F64 ? dispatch_fused<double>(ft, st) : dispatch_fused<float>(ft, st);
+}
+
+}  // namespace qk

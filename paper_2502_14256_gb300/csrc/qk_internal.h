@@ -35,6 +35,9 @@ int launch_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64_t 
 int launch_lms(uint32_t d, uint32_t R, const uint32_t *C, const uint32_t *S, uint32_t *Ct,
                cudaStream_t st);
 
+bool fused_supported(const qk_task &t, int dtype);
+size_t fused_ws_bytes(const qk_task &t, int dtype);
+int run_fused(const qk_task &t, const ColJob &job, int dtype, void *ws, uint32_t *status, cudaStream_t st);
 }  // namespace qk
 
 namespace qk {

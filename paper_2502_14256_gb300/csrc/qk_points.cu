@@ -15,6 +15,7 @@
 #include "qk_common.cuh"
 #include "qk_factors.cuh"
 #include "qk_internal.h"
+#include "qk_column.cuh"
 
 namespace qk {
 
@@ -47,19 +48,6 @@ int launch_lms(uint32_t d, uint32_t R, const uint32_t *C, const uint32_t *S, uin
 }
 
 // ---------------------------------------------------------- point generation
-__device__ __forceinline__ uint32_t order_map(int order, uint32_t v) {
-  return order == QK_GRAY ? (v ^ (v >> 1)) : v;
-}
-
-__device__ __forceinline__ uint32_t xor_columns(const uint32_t *col, uint32_t v) {
-  uint32_t acc = 0;
-  while (v) {
-    acc ^= col[__ffs(v) - 1];
-    v &= v - 1;
-  }
-  return acc;
-}
-
 __global__ void k_points_net(uint32_t d, int order, const uint32_t *__restrict__ Ct,
                              const uint32_t *__restrict__ D, uint32_t r0, uint64_t i0, uint64_t n,
                              uint32_t *__restrict__ X) {
@@ -113,95 +101,24 @@ int launch_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64_t 
   return check_launch("qk_gen_points");
 }
 
-// ------------------------------------------------- difference-word generator
-struct DiffTables {
-  uint32_t *zlane;  // [j][lane]
-  uint32_t *zwarp;  // [warp][j]
-  uint32_t *zl;     // [l][j]
-  uint32_t *gs;     // lattices: [j]
-};
-
-// Build the per-CTA tables for randomization-local pointer Cr (d x 32 columns).
-__device__ void build_tables(const ColJob &job, const uint32_t *Cr, const uint32_t *g,
-                             uint64_t tile_base, DiffTables &tb) {
-  const uint32_t d = job.d;
-  if (job.kind == QK_NET_B2) {
-    for (uint32_t q = threadIdx.x; q < 32 * d; q += kNT) {
-      const uint32_t j = q >> 5, ln = q & 31;
-      tb.zlane[q] = xor_columns(Cr + j * 32, order_map(job.order, ln));
-    }
-    for (uint32_t q = threadIdx.x; q < (kNT / 32) * d; q += kNT) {
-      const uint32_t w = q / d, j = q - w * d;
-      tb.zwarp[q] = xor_columns(Cr + j * 32, order_map(job.order, w << 5));
-    }
-    for (uint32_t q = threadIdx.x; q < kL * d; q += kNT) {
-      const uint32_t l = q / d, j = q - l * d;
-      tb.zl[q] = xor_columns(Cr + j * 32, order_map(job.order, (uint32_t)(tile_base | ((uint64_t)l << 8))));
-    }
-  } else {
-    for (uint32_t q = threadIdx.x; q < d; q += kNT) tb.gs[q] = g[q];
-  }
-}
-
-__host__ __device__ inline size_t col_smem_bytes(uint32_t d) {
-  return (size_t)d * sizeof(double) + (size_t)(32 + kNT / 32 + kL) * d * sizeof(uint32_t);
-}
-
-// Accumulate p = prod_j (1 + c_j K_j) - 1 for the kL points of this thread.
-template <typename T, int FAM, int ALPHA>
-__device__ __forceinline__ void column_sweep(const ColJob &job, const DiffTables &tb, const T *wT,
-                                             const uint32_t (&bi)[kL], T (&p)[kL]) {
-  const uint32_t d = job.d;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int l = 0; l < kL; ++l) p[l] = T(0);
-  for (uint32_t j = 0; j < d; ++j) {
-    const T wj = wT[j];
-    if constexpr (FAM == 0) {
-      const uint32_t base = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * d + j];
-#pragma unroll
-      for (int l = 0; l < kL; ++l) {
-        const T a = wj * factor<T, FAM, ALPHA>(base ^ tb.zl[l * d + j]);
-        p[l] = pm1_step(p[l], a);
-      }
-    } else {
-      const uint32_t gj = tb.gs[j];
-#pragma unroll
-      for (int l = 0; l < kL; ++l) {
-        const T a = wj * factor<T, FAM, ALPHA>(bi[l] * gj);
-        p[l] = pm1_step(p[l], a);
-      }
-    }
-  }
-}
-
-__device__ __forceinline__ void carve(unsigned char *smem, uint32_t d, double **w, DiffTables &tb) {
-  *w = reinterpret_cast<double *>(smem);
-  uint32_t *u = reinterpret_cast<uint32_t *>(smem + (size_t)d * sizeof(double));
-  tb.zlane = u;
-  tb.zwarp = tb.zlane + 32 * d;
-  tb.zl = tb.zwarp + (kNT / 32) * d;
-  tb.gs = u;
-}
-
 template <typename T, int FAM, int ALPHA>
 __global__ void __launch_bounds__(kNT) k_kernel_col(ColJob job, int form, T *__restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem[];
   double *wd;
   DiffTables tb;
-  carve(smem, job.d, &wd, tb);
+  carve_tables<kL>(smem, job.d, &wd, tb);
   T *wT = reinterpret_cast<T *>(wd);
   const uint32_t rl = blockIdx.y;
   const uint64_t n = 1ull << job.m;
   const uint64_t tile_base = (uint64_t)blockIdx.x * kTile;
   for (uint32_t q = threadIdx.x; q < job.d; q += kNT) wT[q] = (T)job.w[q];
-  build_tables(job, job.Ct ? job.Ct + (size_t)rl * job.d * 32 : nullptr, job.g, tile_base, tb);
+  build_tables<kL>(job, job.Ct ? job.Ct + (size_t)rl * job.d * 32 : nullptr, job.g, tile_base, tb);
   __syncthreads();
   uint32_t bi[kL];
 #pragma unroll
   for (int l = 0; l < kL; ++l) bi[l] = __brev((uint32_t)(tile_base + threadIdx.x + (l << 8)));
   T p[kL];
-  column_sweep<T, FAM, ALPHA>(job, tb, wT, bi, p);
+  column_sweep<T, FAM, ALPHA, kL>(job, tb, wT, bi, p);
   const T zeta = (T)job.zeta;
 #pragma unroll
   for (int l = 0; l < kL; ++l) {
@@ -214,7 +131,7 @@ template <typename T, int FAM, int ALPHA>
 static void launch_col_t(const ColJob &job, int form, T *out, cudaStream_t st) {
   const uint64_t n = 1ull << job.m;
   dim3 grid(ceil_div_u(n, kTile), job.nr);
-  const size_t smem = col_smem_bytes(job.d);
+  const size_t smem = col_smem_bytes<kL>(job.d);
   smem_optin<k_kernel_col<T, FAM, ALPHA>>(smem);
   k_kernel_col<T, FAM, ALPHA><<<grid, kNT, smem, st>>>(job, form, out);
 }
@@ -246,40 +163,24 @@ int launch_kernel_col(const ColJob &job, int32_t dtype, int32_t form, void *out,
 }
 
 // ------------------------------------------------------- gradient partials
-// dk_1[i]/dc_j = zeta K_ij prod_{j' != j} f_ij' with f_ij = 1 + c_j K_ij.  Computed as
-// zeta (1 + p_i) K_ij / f_ij, or by the explicit product when f_ij == 0.
-template <typename T, int FAM, int ALPHA>
-__device__ T dk_explicit(const ColJob &job, const DiffTables &tb, const T *wT, uint32_t bi_l, int l,
-                         uint32_t jx) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T prod = (T)job.zeta;
-  for (uint32_t j = 0; j < job.d; ++j) {
-    uint32_t w;
-    if constexpr (FAM == 0) w = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * job.d + j] ^ tb.zl[l * job.d + j];
-    else w = bi_l * tb.gs[j];
-    const T K = factor<T, FAM, ALPHA>(w);
-    prod *= (j == jx) ? K : (T(1) + wT[j] * K);
-  }
-  return prod;
-}
-
+// dk_1[i]/dc_j = zeta K_ij prod_{j' != j} f_ij' with f_ij = 1 + c_j K_ij, computed as
+// zeta (1 + p_i) K_ij / f_ij (explicit product where f_ij == 0).
 template <typename T, int FAM, int ALPHA>
 __global__ void __launch_bounds__(kNT) k_grad_partials(ColJob job, uint32_t nrhs, const T *__restrict__ u,
                                                        double *__restrict__ partial) {
   extern __shared__ __align__(16) unsigned char smem[];
   double *wd;
   DiffTables tb;
-  carve(smem, job.d, &wd, tb);
+  carve_tables<kL>(smem, job.d, &wd, tb);
   T *wT = reinterpret_cast<T *>(wd);
   const uint32_t d = job.d;
-  double *red = reinterpret_cast<double *>(smem + col_smem_bytes(d));  // [warp][2d]
-  const uint32_t v = blockIdx.y;   // vector = r * nrhs + rhs
+  double *red = reinterpret_cast<double *>(smem + col_smem_bytes<kL>(d));  // [warp][2d]
+  const uint32_t v = blockIdx.y;  // vector = r * nrhs + rhs
   const uint32_t rl = v / nrhs;
   const uint64_t n = 1ull << job.m;
   const uint64_t tile_base = (uint64_t)blockIdx.x * kTile;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t q = threadIdx.x; q < d; q += kNT) wT[q] = (T)job.w[q];
-  build_tables(job, job.Ct ? job.Ct + (size_t)rl * d * 32 : nullptr, job.g, tile_base, tb);
+  build_tables<kL>(job, job.Ct ? job.Ct + (size_t)rl * d * 32 : nullptr, job.g, tile_base, tb);
   __syncthreads();
   uint32_t bi[kL];
   T uu[kL], k1[kL];
@@ -292,37 +193,11 @@ __global__ void __launch_bounds__(kNT) k_grad_partials(ColJob job, uint32_t nrhs
     uu[l] = ok[l] ? u[(size_t)v * n + i] : T(0);
   }
   T p[kL];
-  column_sweep<T, FAM, ALPHA>(job, tb, wT, bi, p);
+  column_sweep<T, FAM, ALPHA, kL>(job, tb, wT, bi, p);
   const T zeta = (T)job.zeta;
 #pragma unroll
   for (int l = 0; l < kL; ++l) k1[l] = ok[l] ? zeta * (T(1) + p[l]) : T(0);
-  for (uint32_t j = 0; j < d; ++j) {
-    const T wj = wT[j];
-    T su = T(0), s1 = T(0);
-    uint32_t base = 0, gj = 0;
-    if constexpr (FAM == 0) base = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * d + j];
-    else gj = tb.gs[j];
-#pragma unroll
-    for (int l = 0; l < kL; ++l) {
-      const uint32_t w = (FAM == 0) ? (base ^ tb.zl[l * d + j]) : (bi[l] * gj);
-      const T K = factor<T, FAM, ALPHA>(w);
-      const T f = T(1) + wj * K;
-      T dk = (f != T(0)) ? k1[l] * K / f : dk_explicit<T, FAM, ALPHA>(job, tb, wT, bi[l], l, j);
-      if (!ok[l]) dk = T(0);
-      su += uu[l] * dk;
-      s1 += dk;
-    }
-    double du = (double)su, d1 = (double)s1;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      du += __shfl_xor_sync(0xffffffffu, du, o);
-      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-    }
-    if (lane == 0) {
-      red[(size_t)warp * 2 * d + j] = du;
-      red[(size_t)warp * 2 * d + d + j] = d1;
-    }
-  }
+  gradient_sweep<T, FAM, ALPHA, kL>(job, tb, wT, bi, k1, uu, ok, red);
   __syncthreads();
   double *dst = partial + ((size_t)v * gridDim.x + blockIdx.x) * 2 * d;
   for (uint32_t q = threadIdx.x; q < 2 * d; q += kNT) {
@@ -338,7 +213,7 @@ uint32_t grad_blocks(uint32_t m) { return ceil_div_u(1ull << m, kTile); }
 template <typename T, int FAM, int ALPHA>
 static void launch_grad_t(const ColJob &job, uint32_t nrhs, const T *u, double *partial, cudaStream_t st) {
   dim3 grid(grad_blocks(job.m), job.nr * nrhs);
-  const size_t smem = col_smem_bytes(job.d) + (size_t)(kNT / 32) * 2 * job.d * sizeof(double);
+  const size_t smem = col_smem_bytes<kL>(job.d) + (size_t)(kNT / 32) * 2 * job.d * sizeof(double);
   smem_optin<k_grad_partials<T, FAM, ALPHA>>(smem);
   k_grad_partials<T, FAM, ALPHA><<<grid, kNT, smem, st>>>(job, nrhs, u, partial);
 }

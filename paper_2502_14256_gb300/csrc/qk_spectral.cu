@@ -97,19 +97,6 @@ __global__ void k_add(T *__restrict__ c, const T *__restrict__ dc, uint64_t coun
   for (uint64_t i = gtid(); i < count; i += gstride()) c[i] += dc[i];
 }
 
-__device__ __forceinline__ double block_sum(double v, double *sh) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += sh[q];
-  return s;
-}
-
 constexpr int kRedNT = 256;
 
 // Per vector: FP64 sum of y (the posterior mean needs it with relative accuracy,

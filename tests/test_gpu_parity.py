@@ -363,3 +363,69 @@ def test_fwht_fftbr_ifftbr(qk, m):
         qk.ifftbr(m, t)
         got = t.cpu().numpy()
         assert qc.rel_err(got[..., 0] + 1j * got[..., 1], z) < tol, (dt, m)
+
+
+# ------------------------------------------------------------ fused pipeline
+def _batch_outputs(qk, case, m, nrhs, dt, y_h, eta, refine=0):
+    kern = qc.kernel_of(case)
+    R, n, d = case.R, 1 << m, case.d
+    y = torch.tensor(y_h, dtype=dt, device=qc.dev())
+    c = torch.zeros_like(y)
+    lam = torch.zeros((R, n), dtype=F64, device=qc.dev())
+    out = torch.zeros((R, nrhs, 5), dtype=F64, device=qc.dev())
+    grad = torch.zeros((R, nrhs, 2 * d + 2), dtype=F64, device=qc.dev())
+    task = qk.Task(case.ps, kern, m, nrhs, eta, y.data_ptr(), c.data_ptr(), lam.data_ptr(), out.data_ptr(),
+                   grad.data_ptr())
+    ws = qk.workspace(qk.batch_workspace_bytes([task], dt))
+    status = torch.zeros(1, dtype=torch.int32, device=qc.dev())
+    qk.batch_plan([task], dt, refine, ws)
+    qk.batch_run(ws, status)
+    qk.read_status(status)
+    return {k: v.cpu().numpy().astype(np.float64) for k, v in dict(c=c, lam=lam, out=out, grad=grad).items()}
+
+
+@pytest.mark.parametrize("dt", [F64, F32])
+@pytest.mark.parametrize("m,alpha,order,nrhs", [(13, 2, "gray", 2), (14, 1, "gray", 1), (16, 4, "natural", 3),
+                                                (20, 2, "gray", 1), (21, 2, "natural", 1)])
+def test_fused_schedule_matches_oracle(qk, dt, m, alpha, order, nrhs):
+    """The batched schedule (fused three-phase kernels where the size allows) against
+    the oracle's spectral formulas: lambda, solve, quadratic form, log det, MLL,
+    posterior mean/variance and gradients, per randomization and right-hand side."""
+    if dt == F64 and m > 20:
+        pytest.skip("FP64 fused sizes end at 2^20; larger runs the standalone path, covered elsewhere")
+    d, R, eta = 5, 2, 1e-6
+    gamma = 0.8 ** np.arange(1, d + 1)
+    case = qc.make_case("net", "dsi", alpha, d, R, seed=2000 + m, c=gamma, zeta=1.2, order=order)
+    n = 1 << m
+    rng = np.random.default_rng(m)
+    y_h = np.empty((R, nrhs, n))
+    refs = []
+    for r in range(R):
+        k1, X = case.k1_ref(r, m)
+        lam_ref = o.eigenvalues("dsi", k1, eta)
+        for q in range(nrhs):
+            y_h[r, q] = np.cos((q + 1) * X[:, 0] / 2 ** 31) + 0.01 * rng.standard_normal(n)
+        refs.append((X, lam_ref))
+    got = _batch_outputs(qk, case, m, nrhs, dt, y_h, eta)
+    tol = dict(lam=1e-12, c=1e-10, quad=1e-11, logdet=1e-12, mll=1e-11, mean=1e-10, var=1e-10, grad=1e-9) \
+        if dt == F64 else dict(lam=2e-6, c=2e-4, quad=2e-5, logdet=1e-5, mll=1e-5, mean=2e-4, var=1e-5, grad=2e-4)
+    for r in range(R):
+        X, lam_ref = refs[r]
+        assert qc.rel_err(got["lam"][r], lam_ref) < tol["lam"], (r, qc.rel_err(got["lam"][r], lam_ref))
+        for q in range(nrhs):
+            y = y_h[r, q]
+            c_ref = o.spectral_solve("dsi", lam_ref, y)
+            sp = o.spectral_mll("dsi", lam_ref, y, case.zeta)
+            gr = o.spectral_mll_grad("dsi", alpha, X, y, lam_ref, case.c, case.zeta)
+            ctol = max(tol["c"], 20 * float(lam_ref.max() / lam_ref.min()) * (qc.EPS64 if dt == F64 else qc.EPS32))
+            assert qc.rel_err(got["c"][r, q], c_ref) < ctol, (r, q, qc.rel_err(got["c"][r, q], c_ref))
+            o_ = got["out"][r, q]
+            assert abs(o_[0] - sp["quad"]) < tol["quad"] * abs(sp["quad"])
+            assert abs(o_[1] - sp["logdet"]) < tol["logdet"] * max(1.0, abs(sp["logdet"]))
+            assert abs(o_[2] - sp["mll"]) < tol["mll"] * abs(sp["mll"])
+            assert abs(o_[3] - sp["post_mean"]) < tol["mean"] * max(1.0, abs(sp["post_mean"]))
+            assert abs(o_[4] - sp["post_var"]) < tol["var"] * case.zeta
+            g_ = got["grad"][r, q]
+            assert qc.rel_err(g_[:d], gr["dc"]) < tol["grad"], (qc.rel_err(g_[:d], gr["dc"]))
+            assert abs(g_[d] - gr["deta"]) < tol["grad"] * max(1.0, abs(gr["deta"]))
+            assert qc.rel_err(g_[d + 1:2 * d + 1], gr["dmean_dc"]) < tol["grad"] * 10
