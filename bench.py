@@ -125,7 +125,7 @@ def build_workload(qk, torch, dev, R, m, seed_offset=0):
 class Pipeline:
     """One batched schedule (all randomizations) in a given precision."""
 
-    def __init__(self, qk, torch, dev, W, dtype, refine):
+    def __init__(self, qk, torch, dev, W, dtype, refine, keep_lam=False):
         self.qk, self.torch = qk, torch
         R, n, d = W["R"], W["n"], W["d"]
         # both precisions see the same inputs: y rounded to FP32 once
@@ -135,8 +135,10 @@ class Pipeline:
         self.out = torch.empty((R, 1, qk.QK_MLL_NOUT), dtype=torch.float64, device=dev)
         self.grad = torch.empty((R, 1, 2 * d + 2), dtype=torch.float64, device=dev)
         kern = qk.kernel(qk.QK_DSI, W["wl"].alpha, W["w"], W["wl"].zeta)
+        # eigenvalues are an output only when asked for (the timed step does not write them)
         self.task = qk.Task(W["ps"], kern, W["m"], 1, W["wl"].eta, self.y.data_ptr(), self.c.data_ptr(),
-                            self.lam.data_ptr(), self.out.data_ptr(), self.grad.data_ptr())
+                            self.lam.data_ptr() if keep_lam else None, self.out.data_ptr(),
+                            self.grad.data_ptr())
         self.ws = qk.workspace(qk.batch_workspace_bytes([self.task], dtype), dev)
         qk.batch_plan([self.task], dtype, refine, self.ws)
         self.status = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -297,10 +299,14 @@ def main():
     # ---- plain FP64 pipeline beside it
     fp64 = None
     if not args.no_fp64:
-        P64 = Pipeline(qk, torch, dev, W, torch.float64, refine=0)
+        P64 = Pipeline(qk, torch, dev, W, torch.float64, refine=0, keep_lam=True)
         ms64 = time_steps(torch, P64.step, max(1, min(3, args.steps)), 1, stream)
         fp64 = {"value": points_step / (ms64 * 1e-3), "ms_per_step": ms64}
-        # accuracy of the FP32 path against the FP64 GPU path, per output
+        # accuracy of the FP32 path against the FP64 GPU path, per output (one untimed
+        # FP32 run that also writes its eigenvalues)
+        P32L = Pipeline(qk, torch, dev, W, torch.float32, refine=args.refine, keep_lam=True)
+        P32L.step()
+        P32 = P32L
         torch.cuda.synchronize()
         rel = lambda a, b: float((a.double() - b.double()).abs().max() / b.double().abs().max())  # noqa: E731
         fp64["fp32_rel_err"] = {

@@ -31,27 +31,161 @@ __device__ __forceinline__ uint32_t xor_columns(const uint32_t *col, uint32_t v)
   return acc;
 }
 
+// DSI kernels as polynomials in the converted word fz = (T)Z with coefficients that
+// depend only on beta, i.e. on clz(Z) (the Theorem of Sec. 5.3; x = fz 2^-32):
+//   order 1: K = 1 - 3 t1                         (1 at Z = 0)
+//   order 2: K = (3/2 - 5/2 t1) - beta 2^-32 fz
+//   order 3: K = (-1 + 43/18 (1 - t2)) - 5 (1 - t1) 2^-32 fz + beta 2^-64 fz^2
+//   order 4: K = (-1 + 701/294 (1 - t3)) - 43/9 (1 - t2) 2^-32 fz + 5 (1 - t1) 2^-64 fz^2
+//                - 2/3 beta 2^-96 fz^3 - beta/24 S'(Z)
+// Row r = clz(Z) in 0..32 (r = 32 is Z = 0: beta = t = 0); rows are padded to a
+// power-of-two stride so that each lookup is one (or two) vector loads.
+// S'(Z) = sum of 8^-a over set digits x_{a+1} is read from a 256-entry byte table:
+// S' = T[b0] + 2^-24 T[b1] + 2^-48 T[b2] + ... for the bytes b0, b1, ... of Z.
+constexpr int kTabRows = 33, kTabNC = 8, kOctRows = 256;
+
+// Row stride (elements) for order alpha: 1, 2, 4, 8 -> rows load as one vector.
+__host__ __device__ constexpr int tab_stride(int alpha) { return alpha == 1 ? 1 : (alpha == 2 ? 2 : (alpha == 3 ? 4 : 8)); }
+
+template <typename T>
+__host__ __device__ inline size_t dsi_tab_bytes() {
+  return (size_t)(kTabRows * kTabNC + kOctRows) * sizeof(T);
+}
+
 struct DiffTables {
   uint32_t *zlane;  // [j][lane]
   uint32_t *zwarp;  // [warp][j]
-  uint32_t *zl;     // [l][j]
+  uint32_t *zl;     // [j][l]
   uint32_t *gs;     // lattices: [j]
+  void *ktab;       // DSI coefficient rows [33][kTabNC] then the byte table [256], of T
 };
 
-// Shared bytes: weights (d doubles) + tables ((32 + 8 + L) d words).
+// Shared bytes: weights (d doubles) + DSI tables (as doubles) + index tables ((32 + 8 + L) d words).
+__host__ __device__ inline size_t weights_bytes(uint32_t d) { return ((size_t)d * sizeof(double) + 15) & ~(size_t)15; }
+
 template <int L>
 __host__ __device__ inline size_t col_smem_bytes(uint32_t d) {
-  return (size_t)d * sizeof(double) + (size_t)(32 + kColNT / 32 + L) * d * sizeof(uint32_t);
+  return weights_bytes(d) + dsi_tab_bytes<double>() + (size_t)(32 + kColNT / 32 + L) * d * sizeof(uint32_t);
 }
 
 template <int L>
 __device__ __forceinline__ void carve_tables(unsigned char *smem, uint32_t d, double **w, DiffTables &tb) {
   *w = reinterpret_cast<double *>(smem);
-  uint32_t *u = reinterpret_cast<uint32_t *>(smem + (size_t)d * sizeof(double));
+  tb.ktab = smem + weights_bytes(d);  // 16-byte aligned for the vector row loads
+  uint32_t *u = reinterpret_cast<uint32_t *>(smem + weights_bytes(d) + dsi_tab_bytes<double>());
   tb.zlane = u;
   tb.zwarp = tb.zlane + 32 * d;
   tb.zl = tb.zwarp + (kColNT / 32) * d;
   tb.gs = u;
+}
+
+// Fill the DSI coefficient rows (computed in FP64, stored as T).
+template <typename T, int ALPHA>
+__device__ void build_dsi_tab(T *tab) {
+  for (int q = threadIdx.x; q < kTabRows + kOctRows; q += kColNT) {
+    if (q < kTabRows) {
+      const int beta = q < 32 ? q + 1 : 0;
+      const double t1 = q < 32 ? exp2neg(0.0, beta) : 0.0, t2 = t1 * t1, t3 = t2 * t1;
+      const double b = (double)beta;
+      double A = 0, B = 0, C = 0, D = 0, E = 0;
+      if (ALPHA == 1) {
+        A = q < 32 ? 1.0 - 3.0 * t1 : 1.0;
+      } else if (ALPHA == 2) {
+        A = 1.5 - 2.5 * t1;
+        B = -b * 0x1p-32;
+      } else if (ALPHA == 3) {
+        A = -1.0 + (43.0 / 18.0) * (1.0 - t2);
+        B = -5.0 * (1.0 - t1) * 0x1p-32;
+        C = b * 0x1p-64;
+      } else {
+        A = -1.0 + (701.0 / 294.0) * (1.0 - t3);
+        B = -(43.0 / 9.0) * (1.0 - t2) * 0x1p-32;
+        C = 5.0 * (1.0 - t1) * 0x1p-64;
+        D = -(2.0 / 3.0) * b * 0x1p-96;
+        E = -b / 24.0;
+      }
+      // Rows of order 3 and 4 carry the rounding residuals of their constant (and, for
+      // order 4, linear) coefficients, so that FP32 rows add no per-row bias.
+      constexpr int S = tab_stride(ALPHA);
+      T *row = tab + q * S;
+      const double co[5] = {A, B, C, D, E};
+      for (int k = 0; k < S && k < 5; ++k) row[k] = (T)co[k];
+      for (int k = 5; k < S; ++k) row[k] = T(0);
+      if (ALPHA == 3) row[3] = (T)(A - (double)(T)A);
+      if (ALPHA == 4) {
+        row[5] = (T)(A - (double)(T)A);
+        row[6] = (T)(B - (double)(T)B);
+      }
+    } else {
+      const int byte = q - kTabRows;  // S' of the 8 digits of one byte (a = 0..7)
+      double s = 0.0;
+      for (int a = 0; a < 8; ++a)
+        if ((byte >> (7 - a)) & 1) s += exp2neg(0.0, 3 * a);
+      tab[kTabRows * kTabNC + byte] = (T)s;
+    }
+  }
+}
+
+__device__ __forceinline__ float word_to(float, uint32_t Z) { return __uint2float_rn(Z); }
+__device__ __forceinline__ double word_to(double, uint32_t Z) {
+  return __hiloint2double(0x43300000, (int)Z) - 4503599627370496.0;  // exact
+}
+
+// K_alpha(Z) for a DSI kernel from the shared coefficient rows (vector row loads).
+template <typename T, int ALPHA>
+__device__ __forceinline__ T dsi_tab_eval(const T *tab, uint32_t Z) {
+  constexpr int S = tab_stride(ALPHA);
+  const T *row = tab + __clz(Z) * S;
+  if constexpr (ALPHA == 1) {
+    return row[0];
+  } else {
+    const T fz = word_to(T(), Z);
+    if constexpr (ALPHA == 2) {
+      T a, b;
+      if constexpr (sizeof(T) == 4) {
+        const float2 v = *reinterpret_cast<const float2 *>(row);
+        a = v.x, b = v.y;
+      } else {
+        const double2 v = *reinterpret_cast<const double2 *>(row);
+        a = v.x, b = v.y;
+      }
+      return fmadd(b, fz, a);
+    } else {
+      T c0, c1, c2, c3;
+      if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(row);
+        c0 = v.x, c1 = v.y, c2 = v.z, c3 = v.w;
+      } else {
+        const double2 v0 = *reinterpret_cast<const double2 *>(row);
+        const double2 v1 = *reinterpret_cast<const double2 *>(row + 2);
+        c0 = v0.x, c1 = v0.y, c2 = v1.x, c3 = v1.y;
+      }
+      if constexpr (ALPHA == 3) {
+        return fmadd(fmadd(c2, fz, c1), fz, c0) + c3;  // c3: residual of c0
+      } else {
+        const T *oct = tab + kTabRows * kTabNC;
+        T sp = oct[Z >> 24] + T(0x1p-24) * oct[(Z >> 16) & 255u];
+        if constexpr (sizeof(T) == 8) sp += T(0x1p-48) * oct[(Z >> 8) & 255u];
+        T c4, c5, c6;
+        if constexpr (sizeof(T) == 4) {
+          const float4 v = *reinterpret_cast<const float4 *>(row + 4);
+          c4 = v.x, c5 = v.y, c6 = v.z;
+        } else {
+          const double2 v = *reinterpret_cast<const double2 *>(row + 4);
+          c4 = v.x, c5 = v.y, c6 = row[6];
+        }
+        const T poly = fmadd(fmadd(c3, fz, c2), fz, c1) * fz + c0;
+        return fmadd(c4, sp, poly) + fmadd(c6, fz, c5);
+      }
+    }
+  }
+}
+
+// K_alpha for either family: DSI from the table, SI from the Bernoulli form.
+template <typename T, int FAM, int ALPHA>
+__device__ __forceinline__ T kfac(const DiffTables &tb, uint32_t w) {
+  if constexpr (FAM == 0) return dsi_tab_eval<T, ALPHA>(reinterpret_cast<const T *>(tb.ktab), w);
+  else return si_factor<T, ALPHA>(w);
 }
 
 // Fill the tables for one CTA tile (Cr = this randomization's d x 32 columns).
@@ -69,7 +203,7 @@ __device__ void build_tables(const ColJob &job, const uint32_t *Cr, const uint32
       tb.zwarp[q] = xor_columns(Cr + j * 32, order_map(job.order, w << 5));
     }
     for (uint32_t q = threadIdx.x; q < L * d; q += kColNT) {
-      const uint32_t l = q / d, j = q - l * d;
+      const uint32_t j = q / L, l = q - j * L;
       tb.zl[q] = xor_columns(Cr + j * 32, order_map(job.order, (uint32_t)(tile_base | ((uint64_t)l << 8))));
     }
   } else {
@@ -77,11 +211,19 @@ __device__ void build_tables(const ColJob &job, const uint32_t *Cr, const uint32
   }
 }
 
+// All per-CTA tables: index tables plus, for DSI kernels, the coefficient rows.
+template <typename T, int FAM, int ALPHA, int L>
+__device__ __forceinline__ void build_all(const ColJob &job, const uint32_t *Cr, const uint32_t *g,
+                                          uint64_t tile_base, DiffTables &tb) {
+  build_tables<L>(job, Cr, g, tile_base, tb);
+  if constexpr (FAM == 0) build_dsi_tab<T, ALPHA>(reinterpret_cast<T *>(tb.ktab));
+}
+
 // Difference word of this thread's point l in dimension j.
 template <int FAM, int L>
 __device__ __forceinline__ uint32_t diff_word(const DiffTables &tb, uint32_t d, uint32_t base, uint32_t bi, int l,
                                               uint32_t j) {
-  if constexpr (FAM == 0) return base ^ tb.zl[l * d + j];
+  if constexpr (FAM == 0) return base ^ tb.zl[j * L + l];  // l is a compile-time offset
   else return bi * tb.gs[j];
 }
 
@@ -99,7 +241,7 @@ __device__ __forceinline__ void column_sweep(const ColJob &job, const DiffTables
     if constexpr (FAM == 0) base = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * d + j];
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-      const T a = wj * factor<T, FAM, ALPHA>(diff_word<FAM, L>(tb, d, base, bi[l], l, (FAM == 0) ? j : j));
+      const T a = wj * kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
       p[l] = pm1_step(p[l], a);
     }
   }
@@ -113,18 +255,24 @@ __device__ T dk_explicit(const ColJob &job, const DiffTables &tb, const T *wT, u
   for (uint32_t j = 0; j < job.d; ++j) {
     uint32_t base = 0;
     if constexpr (FAM == 0) base = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * job.d + j];
-    const T K = factor<T, FAM, ALPHA>(diff_word<FAM, L>(tb, job.d, base, bi_l, l, j));
+    const T K = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, job.d, base, bi_l, l, j));
     prod *= (j == jx) ? K : (T(1) + wT[j] * K);
   }
   return prod;
 }
 
+__device__ __forceinline__ float ratio(float a, float b) { return __fdividef(a, b); }  // 2 ulp
+__device__ __forceinline__ double ratio(double a, double b) { return a / b; }
+
 // Gradient sweep: for each dimension j, warp-reduced FP64 sums over this warp's
-// points of u_i dk1_i/dc_j and dk1_i/dc_j, written to red[warp][2d].
-template <typename T, int FAM, int ALPHA, int L>
+// points of u_i dk1_i/dc_j and dk1_i/dc_j, written to red[warp][2d], with
+// dk1_i/dc_j = k1_i K_ij / (1 + c_j K_ij).  wk[l] = u_l k1_l; uget(l) returns u_l and
+// is called only for the rare exact zero of 1 + c_j K_ij, handled after the loop by
+// the explicit product over the other dimensions.
+template <typename T, int FAM, int ALPHA, int L, typename UF>
 __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTables &tb, const T *wT,
-                                               const uint32_t (&bi)[L], const T (&k1)[L], const T (&uu)[L],
-                                               const bool (&ok)[L], double *red) {
+                                               const uint32_t (&bi)[L], const T (&k1)[L], const T (&wk)[L],
+                                               const bool (&ok)[L], UF uget, double *red) {
   const uint32_t d = job.d;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t j = 0; j < d; ++j) {
@@ -132,14 +280,31 @@ __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTabl
     T su = T(0), s1 = T(0);
     uint32_t base = 0;
     if constexpr (FAM == 0) base = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * d + j];
+    uint32_t zero_mask = 0;
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-      const T K = factor<T, FAM, ALPHA>(diff_word<FAM, L>(tb, d, base, bi[l], l, j));
-      const T f = T(1) + wj * K;
-      T dk = (f != T(0)) ? k1[l] * K / f : dk_explicit<T, FAM, ALPHA, L>(job, tb, wT, bi[l], l, j);
-      if (!ok[l]) dk = T(0);
-      su += uu[l] * dk;
-      s1 += dk;
+      const T K = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
+      const T f = fmadd(wj, K, T(1));
+      zero_mask |= (f == T(0)) ? (1u << l) : 0u;
+      const T q = ok[l] ? ratio(K, f) : T(0);
+      su = fmadd(wk[l], q, su);
+      s1 = fmadd(k1[l], q, s1);
+    }
+    if (zero_mask) {  // exact zeros of 1 + c_j K: use prod_{j' != j} (1 + c_j' K_j') directly
+      su = T(0), s1 = T(0);
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        if (!ok[l]) continue;
+        T dk;
+        if (zero_mask & (1u << l)) {
+          dk = dk_explicit<T, FAM, ALPHA, L>(job, tb, wT, bi[l], l, j);
+        } else {
+          const T K = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
+          dk = k1[l] * ratio(K, fmadd(wj, K, T(1)));
+        }
+        su = fmadd(uget(l), dk, su);
+        s1 += dk;
+      }
     }
     double du = (double)su, d1 = (double)s1;
 #pragma unroll

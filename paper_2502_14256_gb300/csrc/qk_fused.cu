@@ -113,6 +113,15 @@ __device__ __forceinline__ void tile_wht(T (&v)[FCfg<T>::L], T *sm, int c) {
   }
 }
 
+// s + c tracks a sum with the rounding error of each addition carried in c (Kahan).
+template <typename T>
+__device__ __forceinline__ void kahan_add(T &s, T &c, T v) {
+  const T y = v - c;
+  const T t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
 __device__ __forceinline__ float fused_log(float v) { return logf(v); }
 __device__ __forceinline__ double fused_log(double v) { return log(v); }
 
@@ -133,7 +142,7 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
   const uint64_t n = 1ull << job.m, base = (uint64_t)tile << LOGT;
   const int t = threadIdx.x;
   for (uint32_t q = t; q < d; q += kFNT) wT[q] = (T)job.w[q];
-  build_tables<L>(job, job.Ct + (size_t)r * d * 32, job.g, base, tb);
+  build_all<T, FAM, ALPHA, L>(job, job.Ct + (size_t)r * d * 32, job.g, base, tb);
   __syncthreads();
   uint32_t bi[L];
 #pragma unroll
@@ -141,13 +150,13 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
   T p[L];
   column_sweep<T, FAM, ALPHA, L>(job, tb, wT, bi, p);
   T *P = reinterpret_cast<T *>(ft.p) + (uint64_t)r * n + base;
-  T ps = T(0);
+  T ps = T(0), pc = T(0);  // compensated (Kahan) thread partial: the sum cancels
 #pragma unroll
   for (int l = 0; l < L; ++l) {
     P[t + (l << kLOGNT)] = p[l];
-    ps += p[l];
+    kahan_add(ps, pc, p[l]);
   }
-  const double sps = block_sum((double)ps, red);
+  const double sps = block_sum((double)ps - (double)pc, red);
   if (t == 0) ft.sp[(uint64_t)r * ft.tiles + tile] = sps;
   tile_wht<T>(p, sm, 0);
   T *PT = reinterpret_cast<T *>(ft.pT) + (uint64_t)r * n + base;
@@ -157,13 +166,13 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
     const uint64_t v = (uint64_t)r * ft.nrhs + q;
     const T *Y = reinterpret_cast<const T *>(ft.y) + v * n + base;
     T yv[L];
-    T ys = T(0);
+    T ys = T(0), yc = T(0);
 #pragma unroll
     for (int l = 0; l < L; ++l) {
       yv[l] = Y[t + (l << kLOGNT)];
-      ys += yv[l];
+      kahan_add(ys, yc, yv[l]);
     }
-    const double sys = block_sum((double)ys, red);
+    const double sys = block_sum((double)ys - (double)yc, red);
     if (t == 0) ft.sy[v * ft.tiles + tile] = sys;
     tile_wht<T>(yv, sm, 0);
     T *YT = reinterpret_cast<T *>(ft.yT) + v * n + base;
@@ -253,7 +262,7 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
 
 // ------------------------------------------------------------------ phase C
 template <typename T, int FAM, int ALPHA>
-__global__ void __launch_bounds__(kFNT) k_fused_C(FTask ft) {
+__global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
   extern __shared__ __align__(16) unsigned char smem[];
   const ColJob &job = ft.job;
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(kFNT) k_fused_C(FTask ft) {
   for (int l = 0; l < L; ++l) uu[l] = GT[t + (l << kLOGNT)];
   tile_wht<T>(uu, sm, 0);
   for (uint32_t q = t; q < d; q += kFNT) wT[q] = (T)job.w[q];
-  build_tables<L>(job, job.Ct + (size_t)r * d * 32, job.g, base, tb);
+  build_all<T, FAM, ALPHA, L>(job, job.Ct + (size_t)r * d * 32, job.g, base, tb);
   const T *P = reinterpret_cast<const T *>(ft.p) + (uint64_t)r * n + base;
   const T zeta = (T)job.zeta;
   T k1[L];
@@ -294,9 +303,12 @@ __global__ void __launch_bounds__(kFNT) k_fused_C(FTask ft) {
     k1[l] = zeta * (T(1) + P[t + (l << kLOGNT)]);
     bi[l] = __brev((uint32_t)(base + t + (l << kLOGNT)));
     ok[l] = true;
+    uu[l] *= k1[l];  // from here on uu holds u k1
   }
   __syncthreads();
-  gradient_sweep<T, FAM, ALPHA, L>(job, tb, wT, bi, k1, uu, ok, red);
+  // u itself stays in the transform tile (sm) after tile_wht; each thread reads its own
+  gradient_sweep<T, FAM, ALPHA, L>(job, tb, wT, bi, k1, uu, ok,
+                                   [&](int l) { return sm[fpad<T>(t + (l << kLOGNT))]; }, red);
   __syncthreads();
   double *dst = ft.gr + ((uint64_t)v * ft.tiles + tile) * 2 * d;
   for (uint32_t q = t; q < 2 * d; q += kFNT) {

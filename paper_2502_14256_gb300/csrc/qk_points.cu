@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kNT) k_kernel_col(ColJob job, int form, T *__r
   const uint64_t n = 1ull << job.m;
   const uint64_t tile_base = (uint64_t)blockIdx.x * kTile;
   for (uint32_t q = threadIdx.x; q < job.d; q += kNT) wT[q] = (T)job.w[q];
-  build_tables<kL>(job, job.Ct ? job.Ct + (size_t)rl * job.d * 32 : nullptr, job.g, tile_base, tb);
+  build_all<T, FAM, ALPHA, kL>(job, job.Ct ? job.Ct + (size_t)rl * job.d * 32 : nullptr, job.g, tile_base, tb);
   __syncthreads();
   uint32_t bi[kL];
 #pragma unroll
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kNT) k_grad_partials(ColJob job, uint32_t nrhs
   const uint64_t n = 1ull << job.m;
   const uint64_t tile_base = (uint64_t)blockIdx.x * kTile;
   for (uint32_t q = threadIdx.x; q < d; q += kNT) wT[q] = (T)job.w[q];
-  build_tables<kL>(job, job.Ct ? job.Ct + (size_t)rl * d * 32 : nullptr, job.g, tile_base, tb);
+  build_all<T, FAM, ALPHA, kL>(job, job.Ct ? job.Ct + (size_t)rl * d * 32 : nullptr, job.g, tile_base, tb);
   __syncthreads();
   uint32_t bi[kL];
   T uu[kL], k1[kL];
@@ -195,9 +195,13 @@ __global__ void __launch_bounds__(kNT) k_grad_partials(ColJob job, uint32_t nrhs
   T p[kL];
   column_sweep<T, FAM, ALPHA, kL>(job, tb, wT, bi, p);
   const T zeta = (T)job.zeta;
+  T wk[kL];
 #pragma unroll
-  for (int l = 0; l < kL; ++l) k1[l] = ok[l] ? zeta * (T(1) + p[l]) : T(0);
-  gradient_sweep<T, FAM, ALPHA, kL>(job, tb, wT, bi, k1, uu, ok, red);
+  for (int l = 0; l < kL; ++l) {
+    k1[l] = ok[l] ? zeta * (T(1) + p[l]) : T(0);
+    wk[l] = uu[l] * k1[l];
+  }
+  gradient_sweep<T, FAM, ALPHA, kL>(job, tb, wT, bi, k1, wk, ok, [&](int l) { return uu[l]; }, red);
   __syncthreads();
   double *dst = partial + ((size_t)v * gridDim.x + blockIdx.x) * 2 * d;
   for (uint32_t q = threadIdx.x; q < 2 * d; q += kNT) {

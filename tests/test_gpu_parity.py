@@ -366,6 +366,19 @@ def test_fwht_fftbr_ifftbr(qk, m):
 
 
 # ------------------------------------------------------------ fused pipeline
+def _abs_dk_sums(family, alpha, X, c, zeta):
+    """sum_i |dk1_i/dc_j| for every j (the scale of the cancelling gradient sums)."""
+    n, d = X.shape
+    out = np.empty(d)
+    fac = [o.factor_values(family, alpha, o.pair_difference(family, X[:, j], X[0, j])) for j in range(d)]
+    for j in range(d):
+        dk = np.full(n, float(zeta))
+        for jj in range(d):
+            dk *= fac[jj] if jj == j else 1.0 + c[jj] * fac[jj]
+        out[j] = float(np.sum(np.abs(dk)))
+    return out
+
+
 def _batch_outputs(qk, case, m, nrhs, dt, y_h, eta, refine=0):
     kern = qc.kernel_of(case)
     R, n, d = case.R, 1 << m, case.d
@@ -393,7 +406,9 @@ def test_fused_schedule_matches_oracle(qk, dt, m, alpha, order, nrhs):
     posterior mean/variance and gradients, per randomization and right-hand side."""
     if dt == F64 and m > 20:
         pytest.skip("FP64 fused sizes end at 2^20; larger runs the standalone path, covered elsewhere")
-    d, R, eta = 5, 2, 1e-6
+    # FP32 eigenvalues carry absolute errors ~ eps32 ||p||_2; the FP32 checks use a nugget
+    # that keeps the spectrum above that (FP64 uses 1e-6)
+    d, R, eta = 5, 2, (1e-6 if dt == F64 else 1e-3)
     gamma = 0.8 ** np.arange(1, d + 1)
     case = qc.make_case("net", "dsi", alpha, d, R, seed=2000 + m, c=gamma, zeta=1.2, order=order)
     n = 1 << m
@@ -428,4 +443,14 @@ def test_fused_schedule_matches_oracle(qk, dt, m, alpha, order, nrhs):
             g_ = got["grad"][r, q]
             assert qc.rel_err(g_[:d], gr["dc"]) < tol["grad"], (qc.rel_err(g_[:d], gr["dc"]))
             assert abs(g_[d] - gr["deta"]) < tol["grad"] * max(1.0, abs(gr["deta"]))
-            assert qc.rel_err(g_[d + 1:2 * d + 1], gr["dmean_dc"]) < tol["grad"] * 10
+            # dMEAN/dc_j = -zeta sum(y) / lambda_0^2 * sum_i dk1_i/dc_j, a mean-zero sum:
+            # summed in FP32 it loses about sqrt(L) eps32 sum_i |dk1_i/dc_j| (L = 32 terms
+            # per thread before the FP64 reduction)
+            if dt == F64:
+                assert qc.rel_err(g_[d + 1:2 * d + 1], gr["dmean_dc"]) < tol["grad"] * 10
+            else:
+                absum = _abs_dk_sums("dsi", alpha, X, case.c, case.zeta)
+                lam0 = float(lam_ref[0])
+                scale = abs(case.zeta * float(np.sum(y)) / lam0 ** 2) * absum
+                bound = 2e-4 * np.abs(gr["dmean_dc"]) + 8 * math.sqrt(32) * qc.EPS32 * scale
+                assert np.all(np.abs(g_[d + 1:2 * d + 1] - gr["dmean_dc"]) < bound)
