@@ -148,6 +148,24 @@ QK_API int qk_eigs(int32_t family, uint32_t m, uint32_t batch, int32_t dtype, in
             const void *col, double zeta, double eta, double *lam, void *ws,
             size_t ws_bytes, uint32_t *status, qk_stream stream);
 
+/* Eigenvalues exactly as qk_eigs, for callers that cannot allocate device memory
+ * at the call site (for instance a plug-in whose host application owns all GPU
+ * memory through its own allocator, or a fixed-footprint service that forbids
+ * allocations after start-up): no workspace argument, the scratch space is a static
+ * device array of QK_EIGS_STATIC_MAX_BYTES owned by the library, held on every GPU
+ * that loads it until the process exits.  The paper has no counterpart to this
+ * entry point.  Requests needing more scratch than that (batch * 2^m elements of the
+ * transform type: 8 bytes for FP64 nets, 4 for FP32 nets, 16 and 8 for lattices)
+ * return QK_EINVAL and launch nothing.  The first call on each device looks up the
+ * array's device address with that device current; make it before any stream
+ * capture.  All calls share the array and it keeps the last call's contents (none
+ * needs to start at zero); calls whose kernels overlap on the GPU race on it and
+ * must be serialised by the caller. */
+#define QK_EIGS_STATIC_MAX_BYTES ((size_t)4 << 20)
+QK_API int qk_eigs_static(int32_t family, uint32_t m, uint32_t batch, int32_t dtype, int32_t form,
+                          const void *col, double zeta, double eta, double *lam, uint32_t *status,
+                          qk_stream stream);
+
 /* Solve K c = y for `batch` Gram matrices and nrhs right-hand sides each:
  * c = V (y~ / lambda), y~ = conj(V) y (Sec. 5.4).  y, c: (batch, nrhs, n) in
  * dtype (may alias); lam: (batch, n) from qk_eigs.  The division is done in

@@ -30,7 +30,7 @@ OP_EIGS, OP_SOLVE, OP_MATVEC, OP_MLL = 0, 1, 2, 3
 EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_solve", "qk_matvec", "qk_mll",
             "qk_batch_workspace_bytes", "qk_batch_plan", "qk_batch_run", "qk_workspace_bytes",
             "qk_read_status", "qk_last_error", "qk_version", "qk_fwht", "qk_fftbr", "qk_ifftbr",
-            "qk_launch_count"]
+            "qk_launch_count", "qk_eigs_static"]
 
 
 class QKError(RuntimeError):
@@ -79,6 +79,7 @@ def _load():
         "qk_fftbr": [u32, u64, i32, P, P],
         "qk_ifftbr": [u32, u64, i32, P, P],
         "qk_launch_count": [],
+        "qk_eigs_static": [i32, u32, u32, i32, i32, P, dbl, dbl, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -170,6 +171,16 @@ def eigs(family: int, m: int, col, lam, zeta: float = 1.0, eta: float = 0.0, for
         ws = workspace(workspace_bytes(OP_EIGS, family, m, batch, 1, col.dtype), col.device)
     _check(LIB.qk_eigs(family, m, batch, dtype_code(col.dtype), form, _ptr(col), zeta, eta, _ptr(lam), _ptr(ws),
                        ws.numel(), _ptr(status), _stream(stream)))
+    return lam
+
+
+def eigs_static(family: int, m: int, col, lam, zeta: float = 1.0, eta: float = 0.0, form: int = QK_COL_K1,
+                status=None, stream=None):
+    """qk_eigs without a workspace: the library's static device scratch is used
+    (for callers that cannot allocate; see include/qk.h for its size limit)."""
+    batch = col.numel() >> m
+    _check(LIB.qk_eigs_static(family, m, batch, dtype_code(col.dtype), form, _ptr(col), zeta, eta, _ptr(lam),
+                              _ptr(status), _stream(stream)))
     return lam
 
 
