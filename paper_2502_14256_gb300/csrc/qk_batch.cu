@@ -29,14 +29,15 @@ struct Plan {
 static std::mutex g_mu;
 static std::unordered_map<const void *, Plan> g_plans;
 
-// A task runs fused (qk_fused.cu) when its family and size allow it and no
-// refinement is requested; otherwise it runs as the sequence of standalone ops.
+// A task runs fused (qk_fused.cu) when its family and size allow it; otherwise it
+// runs as the sequence of standalone ops.
 static bool use_fused(const qk_task &t, int dtype, int refine) {
-  return refine == 0 && fused_supported(t, dtype);
+  (void)refine;
+  return fused_supported(t, dtype);
 }
 
 static size_t task_scratch(const qk_task &t, int dtype, int refine) {
-  if (use_fused(t, dtype, refine)) return fused_ws_bytes(t, dtype);
+  if (use_fused(t, dtype, refine)) return fused_ws_bytes(t, dtype, refine);
   const uint32_t R = t.ps.R;
   const size_t tb = dtype == QK_F64 ? 8 : 4;
   const size_t col = align256(tb * ((uint64_t)R << t.m));
@@ -86,7 +87,7 @@ static int run_plan(const Plan &p, unsigned char *ws, uint32_t *status, cudaStre
     double *lam = t.lam ? t.lam : (double *)(ws + p.lam_off);
     const ColJob job = make_job(&t.ps, &t.k, 0, R, t.m);
     if (use_fused(t, p.dtype, p.refine)) {
-      int rc = run_fused(t, job, p.dtype, ws, status, st);
+      int rc = run_fused(t, job, p.dtype, p.refine, ws, status, st);
       if (rc) return rc;
       continue;
     }

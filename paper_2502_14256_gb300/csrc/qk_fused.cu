@@ -43,6 +43,7 @@ struct FTask {
   void *c;
   double *lam, *out, *grad;
   void *p, *pT, *yT, *gT;               // (R, n), (R, n), (R, nrhs, n), (R, nrhs, n)
+  void *yL;                             // (R, nrhs, n): low parts of the compensated y' (refinement)
   double *sp, *sy, *ld, *qg, *gr;       // partial sums
   uint32_t *status;
 };
@@ -122,11 +123,90 @@ __device__ __forceinline__ void kahan_add(T &s, T &c, T v) {
   s = t;
 }
 
+// Error-free sum: s + e == a + b exactly (Knuth's TwoSum; no ordering of |a|, |b| needed).
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
+  s = a + b;
+  const T bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated butterfly on (hi, lo) pairs: the rounding error of each hi sum is added
+// to the lo parts, so hi + lo carries the transform to about twice the precision of T.
+template <typename T>
+__device__ __forceinline__ void cbfly(T &ah, T &al, T &bh, T &bl) {
+  T s, e1, d, e2;
+  two_sum(ah, bh, s, e1);
+  two_sum(ah, -bh, d, e2);
+  const T sl = (al + bl) + e1, dl = (al - bl) + e2;
+  ah = s, al = sl, bh = d, bl = dl;
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void smem_round2(T *sh, T *sl, int b) {
+  constexpr int G = (1 << FCfg<T>::LOGT) >> R;
+  for (int g = threadIdx.x; g < G; g += kFNT) {
+    const int e0 = (g & ((1 << b) - 1)) | ((g >> b) << (b + R));
+    T vh[1 << R], vl[1 << R];
+#pragma unroll
+    for (int q = 0; q < (1 << R); ++q) {
+      vh[q] = sh[fpad<T>(e0 | (q << b))];
+      vl[q] = sl[fpad<T>(e0 | (q << b))];
+    }
+#pragma unroll
+    for (int h = 0; h < R; ++h)
+#pragma unroll
+      for (int q = 0; q < (1 << R); ++q)
+        if (!(q & (1 << h))) cbfly(vh[q], vl[q], vh[q | (1 << h)], vl[q | (1 << h)]);
+#pragma unroll
+    for (int q = 0; q < (1 << R); ++q) {
+      sh[fpad<T>(e0 | (q << b))] = vh[q];
+      sl[fpad<T>(e0 | (q << b))] = vl[q];
+    }
+  }
+}
+
+// tile_wht on compensated pairs (hi, lo); shl: a second padded tile for the lo parts.
+template <typename T>
+__device__ __forceinline__ void tile_wht2(T (&vh)[FCfg<T>::L], T (&vl)[FCfg<T>::L], T *sh, T *shl, int c) {
+  constexpr int L = FCfg<T>::L, LOGL = FCfg<T>::LOGL;
+#pragma unroll
+  for (int h = 0; h < LOGL; ++h) {
+    if (kLOGNT + h >= c) {
+#pragma unroll
+      for (int q = 0; q < L; ++q)
+        if (!(q & (1 << h))) cbfly(vh[q], vl[q], vh[q | (1 << h)], vl[q | (1 << h)]);
+    }
+  }
+  if (c < kLOGNT) {
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      sh[fpad<T>(threadIdx.x + (l << kLOGNT))] = vh[l];
+      shl[fpad<T>(threadIdx.x + (l << kLOGNT))] = vl[l];
+    }
+    __syncthreads();
+    for (int b = c; b < kLOGNT; b += 4) {
+      const int r = (kLOGNT - b) < 4 ? (kLOGNT - b) : 4;
+      if (r == 4) smem_round2<T, 4>(sh, shl, b);
+      else if (r == 3) smem_round2<T, 3>(sh, shl, b);
+      else if (r == 2) smem_round2<T, 2>(sh, shl, b);
+      else smem_round2<T, 1>(sh, shl, b);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      vh[l] = sh[fpad<T>(threadIdx.x + (l << kLOGNT))];
+      vl[l] = shl[fpad<T>(threadIdx.x + (l << kLOGNT))];
+    }
+    __syncthreads();
+  }
+}
+
 __device__ __forceinline__ float fused_log(float v) { return logf(v); }
 __device__ __forceinline__ double fused_log(double v) { return log(v); }
 
 // ------------------------------------------------------------------ phase A
-template <typename T, int FAM, int ALPHA>
+template <typename T, int FAM, int ALPHA, bool COMP>
 __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -137,7 +217,8 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
   carve_tables<L>(smem, d, &wd, tb);
   T *wT = reinterpret_cast<T *>(wd);
   T *sm = reinterpret_cast<T *>(smem + align256(col_smem_bytes<L>(d)));
-  double *red = reinterpret_cast<double *>(smem + align256(col_smem_bytes<L>(d)) + tile_smem_bytes<T>());
+  double *red = reinterpret_cast<double *>(smem + align256(col_smem_bytes<L>(d)) +
+                                           (COMP ? 2 : 1) * tile_smem_bytes<T>());
   const uint32_t r = blockIdx.y, tile = blockIdx.x;
   const uint64_t n = 1ull << job.m, base = (uint64_t)tile << LOGT;
   const int t = threadIdx.x;
@@ -174,20 +255,33 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
     }
     const double sys = block_sum((double)ys - (double)yc, red);
     if (t == 0) ft.sy[v * ft.tiles + tile] = sys;
-    tile_wht<T>(yv, sm, 0);
     T *YT = reinterpret_cast<T *>(ft.yT) + v * n + base;
+    if constexpr (COMP) {
+      T yl[L];
 #pragma unroll
-    for (int l = 0; l < L; ++l) YT[t + (l << kLOGNT)] = yv[l];
+      for (int l = 0; l < L; ++l) yl[l] = T(0);
+      tile_wht2<T>(yv, yl, sm, sm + tile_smem_bytes<T>() / sizeof(T), 0);
+      T *YL = reinterpret_cast<T *>(ft.yL) + v * n + base;
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        YT[t + (l << kLOGNT)] = yv[l];
+        YL[t + (l << kLOGNT)] = yl[l];
+      }
+    } else {
+      tile_wht<T>(yv, sm, 0);
+#pragma unroll
+      for (int l = 0; l < L; ++l) YT[t + (l << kLOGNT)] = yv[l];
+    }
   }
 }
 
 // ------------------------------------------------------------------ phase B
-template <typename T>
+template <typename T, bool COMP>
 __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
   extern __shared__ __align__(16) unsigned char smem[];
   T *sm = reinterpret_cast<T *>(smem);
-  T *ilv = reinterpret_cast<T *>(smem + tile_smem_bytes<T>());      // 1 / lambda, tile layout
+  T *lmv = reinterpret_cast<T *>(smem + tile_smem_bytes<T>());      // lambda, tile layout
   T *gst = reinterpret_cast<T *>(smem + 2 * tile_smem_bytes<T>());  // g before its transform
   double *red = reinterpret_cast<double *>(smem + 3 * tile_smem_bytes<T>());
   const uint32_t r = blockIdx.y, tau = blockIdx.x;
@@ -216,7 +310,7 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
     bad |= !(v > T(0));
     lds += fused_log(v);
     if (LAM) LAM[wl] = (double)v;
-    ilv[fpad<T>(t + (l << kLOGNT))] = T(1) / v;  // each thread reads back only its own entries
+    lmv[fpad<T>(t + (l << kLOGNT))] = v;  // each thread reads back only its own entries
   }
   if (bad && ft.status) atomicOr(ft.status, (uint32_t)QK_STATUS_NOTPD);
   const double ldsum = block_sum((double)lds, red);
@@ -229,17 +323,36 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
     T y[L];
 #pragma unroll
     for (int l = 0; l < L; ++l) y[l] = YT[widx(l)];
-    tile_wht<T>(y, sm, c);
+    T ylo[COMP ? L : 1];
+    if constexpr (COMP) {
+      const T *YL = reinterpret_cast<const T *>(ft.yL) + v * n;
+#pragma unroll
+      for (int l = 0; l < L; ++l) ylo[l] = YL[widx(l)];
+      tile_wht2<T>(y, ylo, sm, gst, c);  // gst doubles as the lo tile here
+    } else {
+      tile_wht<T>(y, sm, c);
+    }
     T quad = T(0), gs = T(0);
 #pragma unroll
     for (int l = 0; l < L; ++l) {
       const int e = fpad<T>(t + (l << kLOGNT));  // this thread's own entries only
-      const T il = ilv[e];
-      const T ch = y[l] * inv_n * il;  // c^_w = Y_w / (n lambda_w)
-      const T a = ch * y[l];           // Y_w^2 / (n lambda_w)
+      const T lw = lmv[e];
+      const T il = T(1) / lw;
+      const T sc = inv_n * il;          // 1 / (n lambda_w)
+      T ch = y[l] * sc;                 // c^_w = Y_w / (n lambda_w)
+      const T a = ch * y[l];            // Y_w^2 / (n lambda_w)
       quad += a;
       const T gg = T(0.5) * (a - T(1)) * il;
       gs += gg;
+      if constexpr (COMP) {
+        // refinement: the exact residual of the division plus the forward transform's
+        // own rounding error (the lo part), divided once more, corrects c^ before the
+        // inverse transform: the solve then equals one step of iterative refinement
+        // with an exact residual, up to the rounding of the inverse transform.
+        const T nl = (T)n * lw;                       // exact: n is a power of two
+        const T rho = fmadd(-ch, nl, y[l]);           // Y_hi - c^ n lambda_w
+        ch = fmadd(rho + ylo[l], sc, ch);
+      }
       y[l] = ch;
       gst[e] = gg;
     }
@@ -381,31 +494,33 @@ bool fused_supported(const qk_task &t, int dtype) {
 
 static size_t fused_elem(int dtype) { return dtype == QK_F64 ? 8 : 4; }
 
-size_t fused_ws_bytes(const qk_task &t, int dtype) {
+size_t fused_ws_bytes(const qk_task &t, int dtype, int refine) {
   const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
   const uint64_t R = t.ps.R, n = 1ull << t.m, tiles = n >> LOGT, nv = R * t.nrhs;
   const size_t e = fused_elem(dtype);
   size_t s = 2 * align256(e * R * n) + 2 * align256(e * nv * n);
   s += 2 * align256(8 * R * tiles) + align256(8 * nv * tiles) + align256(16 * nv * tiles);
   s += align256(8 * nv * tiles * 2 * (uint64_t)t.ps.d);
+  if (refine > 0 && dtype == QK_F32) s += align256(e * nv * n);  // lo parts of y'
   return s;
 }
 
-template <typename T, int FAM, int ALPHA>
+template <typename T, int FAM, int ALPHA, bool COMP>
 static int launch_fused_t(const FTask &ft, cudaStream_t st) {
   constexpr int L = FCfg<T>::L;
   const uint32_t R = ft.job.nr, d = ft.job.d;
   const size_t colb = align256(col_smem_bytes<L>(d));
-  const size_t smA = colb + tile_smem_bytes<T>() + 32 * sizeof(double);
+  // phase A keeps a second tile for the lo parts when compensating
+  const size_t smA = colb + (COMP ? 2 : 1) * tile_smem_bytes<T>() + 32 * sizeof(double);
   const size_t smB = 3 * tile_smem_bytes<T>() + 32 * sizeof(double);
   const size_t smC = colb + tile_smem_bytes<T>() + (size_t)(kFNT / 32) * 2 * d * sizeof(double);
-  smem_optin<k_fused_A<T, FAM, ALPHA>>(smA);
-  smem_optin<k_fused_B<T>>(smB);
+  smem_optin<k_fused_A<T, FAM, ALPHA, COMP>>(smA);
+  smem_optin<k_fused_B<T, COMP>>(smB);
   smem_optin<k_fused_C<T, FAM, ALPHA>>(smC);
-  k_fused_A<T, FAM, ALPHA><<<dim3(ft.tiles, R), kFNT, smA, st>>>(ft);
+  k_fused_A<T, FAM, ALPHA, COMP><<<dim3(ft.tiles, R), kFNT, smA, st>>>(ft);
   int rc = check_launch("fused A");
   if (rc) return rc;
-  k_fused_B<T><<<dim3(ft.tiles, R), kFNT, smB, st>>>(ft);
+  k_fused_B<T, COMP><<<dim3(ft.tiles, R), kFNT, smB, st>>>(ft);
   if ((rc = check_launch("fused B"))) return rc;
   if (ft.c || ft.grad) {
     k_fused_C<T, FAM, ALPHA><<<dim3(ft.tiles, R * ft.nrhs), kFNT, smC, st>>>(ft);
@@ -415,18 +530,19 @@ static int launch_fused_t(const FTask &ft, cudaStream_t st) {
   return check_launch("fused final");
 }
 
-template <typename T>
+template <typename T, bool COMP>
 static int dispatch_fused(const FTask &ft, cudaStream_t st) {
   switch (ft.job.alpha) {
-    case 1: return launch_fused_t<T, 0, 1>(ft, st);
-    case 2: return launch_fused_t<T, 0, 2>(ft, st);
-    case 3: return launch_fused_t<T, 0, 3>(ft, st);
-    case 4: return launch_fused_t<T, 0, 4>(ft, st);
+    case 1: return launch_fused_t<T, 0, 1, COMP>(ft, st);
+    case 2: return launch_fused_t<T, 0, 2, COMP>(ft, st);
+    case 3: return launch_fused_t<T, 0, 3, COMP>(ft, st);
+    case 4: return launch_fused_t<T, 0, 4, COMP>(ft, st);
     default: return fail(QK_EINVAL, "DSI order must be 1..4");
   }
 }
 
-int run_fused(const qk_task &t, const ColJob &job, int dtype, void *ws, uint32_t *status, cudaStream_t st) {
+int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *ws, uint32_t *status,
+              cudaStream_t st) {
   const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
   const uint64_t R = t.ps.R, n = 1ull << t.m, tiles = n >> LOGT, nv = R * t.nrhs;
   const size_t e = fused_elem(dtype);
@@ -452,7 +568,16 @@ int run_fused(const qk_task &t, const ColJob &job, int dtype, void *ws, uint32_t
   ft.sy = (double *)p, p += align256(8 * nv * tiles);
   ft.qg = (double *)p, p += align256(16 * nv * tiles);
   ft.gr = (double *)p;
-  return dtype == QK_F64 ? dispatch_fused<double>(ft, st) : dispatch_fused<float>(ft, st);
+  p += align256(8 * nv * tiles * 2 * (uint64_t)t.ps.d);
+  ft.yL = nullptr;
+  // FP64 needs no refinement; FP32 with refine >= 1 runs the compensated variant
+  // (one exact-residual step; further steps change nothing at FP32 resolution)
+  if (dtype == QK_F64) return dispatch_fused<double, false>(ft, st);
+  if (refine > 0) {
+    ft.yL = p;
+    return dispatch_fused<float, true>(ft, st);
+  }
+  return dispatch_fused<float, false>(ft, st);
 }
 
 }  // namespace qk

@@ -36,8 +36,9 @@ int launch_lms(uint32_t d, uint32_t R, const uint32_t *C, const uint32_t *S, uin
                cudaStream_t st);
 
 bool fused_supported(const qk_task &t, int dtype);
-size_t fused_ws_bytes(const qk_task &t, int dtype);
-int run_fused(const qk_task &t, const ColJob &job, int dtype, void *ws, uint32_t *status, cudaStream_t st);
+size_t fused_ws_bytes(const qk_task &t, int dtype, int refine);
+int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *ws, uint32_t *status,
+              cudaStream_t st);
 }  // namespace qk
 
 namespace qk {

@@ -454,3 +454,28 @@ def test_fused_schedule_matches_oracle(qk, dt, m, alpha, order, nrhs):
                 scale = abs(case.zeta * float(np.sum(y)) / lam0 ** 2) * absum
                 bound = 2e-4 * np.abs(gr["dmean_dc"]) + 8 * math.sqrt(32) * qc.EPS32 * scale
                 assert np.all(np.abs(g_[d + 1:2 * d + 1] - gr["dmean_dc"]) < bound)
+
+
+@pytest.mark.parametrize("m,alpha,eta", [(15, 2, 1e-4), (18, 1, 1e-5), (20, 4, 1e-4)])
+def test_fused_refinement_solves_the_fp32_operator(qk, m, alpha, eta):
+    """One refinement step (refine_steps = 1) with the residual carried exactly
+    (compensated forward transform and exact division residual): the FP32 solve then
+    matches the exact solution of K^ c = y, K^ built from the same FP32 eigenvalues,
+    to the rounding of the inverse transform; the unrefined solve does not."""
+    d, R, nrhs = 5, 1, 2
+    case = qc.make_case("net", "dsi", alpha, d, R, seed=3000 + m, c=0.9 ** np.arange(1, d + 1))
+    n = 1 << m
+    k1, X = case.k1_ref(0, m)
+    rng = np.random.default_rng(m)
+    y_h = np.stack([np.exp(X[:, 0] / 2 ** 32) + 0.1 * rng.standard_normal(n) for _ in range(nrhs)])[None]
+    y32 = y_h.astype(np.float32).astype(np.float64)
+    ref = _batch_outputs(qk, case, m, nrhs, F32, y_h, eta, refine=1)
+    raw = _batch_outputs(qk, case, m, nrhs, F32, y_h, eta, refine=0)
+    lam_hat = ref["lam"][0]
+    assert np.array_equal(lam_hat, raw["lam"][0])
+    for q in range(nrhs):
+        c_exact = o.spectral_solve("dsi", lam_hat, y32[0, q])
+        e1 = qc.rel_err(ref["c"][0, q], c_exact)
+        e0 = qc.rel_err(raw["c"][0, q], c_exact)
+        assert e1 < 8 * math.sqrt(m) * qc.EPS32, (e1, e0)
+        assert e1 < e0, (e1, e0)
