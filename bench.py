@@ -249,9 +249,12 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = qk.launch_count()
+    qk.batch_timing(P32.ws, args.steps)  # CUDA events around each kernel of the timed steps
     ms = time_steps(torch, P32.step, args.steps, 0, stream)
     launches = qk.launch_count() - launches0
     clocks = sampler.stop()
+    kernel_ms = qk.batch_kernel_ms(P32.ws)
+    qk.batch_timing(P32.ws, 0)
     if world > 1:
         dist.barrier()
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
@@ -316,6 +319,25 @@ def main():
             "grad_dc": rel(P32.grad[..., :d], P64.grad[..., :d])}
         del P64
 
+    # ---- roofline of the dominant kernel of the timed step
+    R_, n_, d_ = W["R"], W["n"], W["d"]
+    top = max(kernel_ms.items(), key=lambda kv: kv[1][1])
+    top_name, (top_launches, top_ms_total) = top
+    top_ms = top_ms_total / max(1, top_launches)
+    # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    # algorithmic work per launch (per point and right-hand side, DSI order 2):
+    #   gradient sweep 10 flops per dimension (K, f = 1 + c K, K/f, two accumulations),
+    #   column sweep 8 flops per dimension (K, a = c K, p update),
+    #   13-bit tile transforms 13 adds per vector.
+    flops_per_point = {"k_fused_C": 10 * d_ + 2 * 13 + 3, "k_fused_A": 8 * d_ + 2 * 13 + 2}
+    roof = None
+    if top_name in flops_per_point:
+        work = flops_per_point[top_name] * R_ * n_
+        ach = work / (top_ms * 1e-3) / 1e12
+        roof = {"kernel": top_name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None, "ms_per_launch": top_ms,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
@@ -344,11 +366,11 @@ def main():
             "gpu_launches_per_step": launches / max(1, args.steps),
             "fp64_plain": fp64,
             "stages_ms": stage,
+            "kernels_ms_per_step": {k: v[1] / max(1, args.steps) for k, v in kernel_ms.items()},
             "fwht": {"gbs": fw_gbs, "ms": fw_ms, "frac_of_hbm": fw_gbs / hbm_peak, "bytes": fw_bytes,
-                     "shape": f"{R} x 2^{m} fp32, in place"},
-            "roofline": {"kernel": "k_transform_pass<WHT,float> (batched FWHT, 2 passes)", "bound": "hbm",
-                         "achieved": fw_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": fw_gbs / hbm_peak,
-                         "traffic": None, "peak_source": peak_src},
+                     "peak": hbm_peak, "peak_source": peak_src,
+                     "shape": f"{R} x 2^{m} fp32, in place, two tile passes per L2-sized chunk"},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks,
         }

@@ -4,7 +4,9 @@
 // only (no allocation, no host synchronisation), so it can be captured into a
 // CUDA graph and replayed.
 #include <cstring>
+#include <memory>
 #include <mutex>
+#include <string>
 #include <unordered_map>
 #include <vector>
 
@@ -17,6 +19,34 @@ int check_pointset(const qk_pointset *ps, uint32_t r0, uint32_t nr);
 int check_kernel(const qk_kernel *k, const qk_pointset *ps);
 ColJob make_job(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr, uint32_t m);
 
+// Event pairs recorded around launches when timing is on (qk_batch_timing).
+struct EventTimer : LaunchTimer {
+  struct Rec {
+    std::string name;
+    cudaEvent_t a = nullptr, b = nullptr;
+  };
+  std::vector<Rec> recs;
+  uint32_t runs_left = 0;
+  bool active = false;
+  void begin(const char *name, cudaStream_t st) override {
+    Rec r;
+    r.name = name;
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    cudaEventRecord(r.a, st);
+    recs.push_back(r);
+  }
+  void end(cudaStream_t st) override { cudaEventRecord(recs.back().b, st); }
+  void clear() {
+    for (Rec &r : recs) {
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    recs.clear();
+  }
+  ~EventTimer() override { clear(); }
+};
+
 struct Plan {
   std::vector<qk_task> tasks;
   int32_t dtype = QK_F64;
@@ -24,6 +54,7 @@ struct Plan {
   size_t scratch = 0;   // bytes of the shared scratch region
   size_t lam_off = 0;   // offset of the eigenvalue buffer
   size_t total = 0;
+  std::shared_ptr<EventTimer> timer;
 };
 
 static std::mutex g_mu;
@@ -78,7 +109,19 @@ static int make_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, int32
   return QK_OK;
 }
 
-static int run_plan(const Plan &p, unsigned char *ws, uint32_t *status, cudaStream_t st) {
+// Brackets one standalone op of the unfused path when timing is on.
+struct OpScope {
+  LaunchTimer *tm;
+  cudaStream_t st;
+  OpScope(LaunchTimer *t, const char *name, cudaStream_t s) : tm(t), st(s) {
+    if (tm) tm->begin(name, st);
+  }
+  ~OpScope() {
+    if (tm) tm->end(st);
+  }
+};
+
+static int run_plan(const Plan &p, unsigned char *ws, uint32_t *status, cudaStream_t st, LaunchTimer *tm) {
   for (const qk_task &t : p.tasks) {
     const uint32_t R = t.ps.R;
     const size_t tb = p.dtype == QK_F64 ? 8 : 4;
@@ -87,15 +130,27 @@ static int run_plan(const Plan &p, unsigned char *ws, uint32_t *status, cudaStre
     double *lam = t.lam ? t.lam : (double *)(ws + p.lam_off);
     const ColJob job = make_job(&t.ps, &t.k, 0, R, t.m);
     if (use_fused(t, p.dtype, p.refine)) {
-      int rc = run_fused(t, job, p.dtype, p.refine, ws, status, st);
+      int rc = run_fused(t, job, p.dtype, p.refine, ws, status, st, tm);
       if (rc) return rc;
       continue;
     }
-    int rc = launch_kernel_col(job, p.dtype, QK_COL_P, col, st);
-    if (rc) return rc;
-    if ((rc = op_eigs(t.k.family, t.m, R, p.dtype, QK_COL_P, col, t.k.zeta, t.eta, lam, scr, status, st))) return rc;
-    if ((rc = op_mll(job, t.nrhs, p.dtype, lam, t.y, t.out, t.grad, scr, st))) return rc;
-    if (t.c && (rc = op_solve(t.k.family, t.m, R, t.nrhs, p.dtype, lam, t.y, t.c, p.refine, scr, st))) return rc;
+    int rc;
+    {
+      OpScope s(tm, "op_kernel_col", st);
+      if ((rc = launch_kernel_col(job, p.dtype, QK_COL_P, col, st))) return rc;
+    }
+    {
+      OpScope s(tm, "op_eigs", st);
+      if ((rc = op_eigs(t.k.family, t.m, R, p.dtype, QK_COL_P, col, t.k.zeta, t.eta, lam, scr, status, st))) return rc;
+    }
+    {
+      OpScope s(tm, "op_mll", st);
+      if ((rc = op_mll(job, t.nrhs, p.dtype, lam, t.y, t.out, t.grad, scr, st))) return rc;
+    }
+    if (t.c) {
+      OpScope s(tm, "op_solve", st);
+      if ((rc = op_solve(t.k.family, t.m, R, t.nrhs, p.dtype, lam, t.y, t.c, p.refine, scr, st))) return rc;
+    }
   }
   return QK_OK;
 }
@@ -134,14 +189,66 @@ int qk_batch_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, int32_t 
 
 int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream stream) {
   Plan p;
+  LaunchTimer *tm = nullptr;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     auto it = g_plans.find(ws);
     if (it == g_plans.end()) return fail(QK_EINVAL, "no plan recorded for this workspace (call qk_batch_plan)");
     p = it->second;
+    if (p.timer && p.timer->runs_left > 0) {
+      --p.timer->runs_left;
+      tm = p.timer.get();
+    }
   }
   if (ws_bytes < p.total) return fail(QK_EWORKSPACE, "batch workspace has %zu bytes, %zu needed", ws_bytes, p.total);
-  return run_plan(p, (unsigned char *)ws, status, (cudaStream_t)stream);
+  return run_plan(p, (unsigned char *)ws, status, (cudaStream_t)stream, tm);
+}
+
+int qk_batch_timing(void *ws, uint32_t runs) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_plans.find(ws);
+  if (it == g_plans.end()) return fail(QK_EINVAL, "no plan recorded for this workspace (call qk_batch_plan)");
+  if (!it->second.timer) it->second.timer = std::make_shared<EventTimer>();
+  it->second.timer->clear();
+  it->second.timer->runs_left = runs;
+  return QK_OK;
+}
+
+int qk_batch_kernel_ms(void *ws, uint32_t idx, char *name, size_t name_len, uint32_t *launches, double *ms) {
+  std::shared_ptr<EventTimer> tm;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_plans.find(ws);
+    if (it == g_plans.end()) return fail(QK_EINVAL, "no plan recorded for this workspace (call qk_batch_plan)");
+    tm = it->second.timer;
+  }
+  if (!tm) return fail(QK_EINVAL, "timing was not enabled (call qk_batch_timing)");
+  std::vector<std::string> names;
+  for (const auto &r : tm->recs) {
+    bool seen = false;
+    for (const auto &nm : names) seen |= nm == r.name;
+    if (!seen) names.push_back(r.name);
+  }
+  if (idx >= names.size()) return fail(QK_EINVAL, "kernel index %u beyond %zu recorded names", idx, names.size());
+  uint32_t cnt = 0;
+  double tot = 0.0;
+  for (const auto &r : tm->recs) {
+    if (r.name != names[idx]) continue;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "qk_batch_kernel_ms");
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess) return cuda_fail(e, "qk_batch_kernel_ms");
+    ++cnt;
+    tot += t;
+  }
+  if (name && name_len) {
+    strncpy(name, names[idx].c_str(), name_len - 1);
+    name[name_len - 1] = 0;
+  }
+  if (launches) *launches = cnt;
+  if (ms) *ms = tot;
+  return QK_OK;
 }
 
 }  // extern "C"

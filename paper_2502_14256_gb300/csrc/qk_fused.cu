@@ -20,6 +20,7 @@
 // tile bits carried by l (the top log2 L bits) are transformed in registers, the
 // low 8 bits in padded shared memory in radix-16 rounds.
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "qk_column.cuh"
@@ -202,6 +203,176 @@ __device__ __forceinline__ void tile_wht2(T (&vh)[FCfg<T>::L], T (&vl)[FCfg<T>::
   }
 }
 
+// ---------------------------------------------------------- register-tiled WHT
+// Three thread layouts of a 2^LOGT-element tile (L = 2^LOGL elements per thread,
+// 256 threads):
+//   L0: e = t + 256 l                                   (l carries bits [8, LOGT))
+//   L1: e = L t + l                                     (l carries bits [0, LOGL))
+//   L2: e = (t mod L) + L l + L^2 (t div L)             (l carries bits [LOGL, 2 LOGL))
+// L0 and L2 give coalesced global accesses.  Every transformed bit is butterflied in
+// exactly one layout: [c, LOGL) in L1, [max(c, LOGL), 8) in L2, [max(c, 8), LOGT) in
+// L0, with conflict-free transposes through a tile padded by 4 words per L elements
+// (L1 side in 128-bit vectors).
+template <typename T> struct Lay {
+  static constexpr int L = FCfg<T>::L, LOGL = FCfg<T>::LOGL, LOGT = FCfg<T>::LOGT;
+  static constexpr int PADE = 16 / sizeof(T);  // 4 words per row of L elements
+  static constexpr int VEC = 16 / sizeof(T);   // elements per 128-bit access
+};
+template <typename T>
+__host__ __device__ constexpr size_t xtile_bytes() {
+  return (size_t)((1 << FCfg<T>::LOGT) + Lay<T>::PADE * ((1 << FCfg<T>::LOGT) >> FCfg<T>::LOGL)) * sizeof(T);
+}
+template <typename T>
+__device__ __forceinline__ int xpad(int e) { return e + Lay<T>::PADE * (e >> Lay<T>::LOGL); }
+template <typename T>
+__device__ __forceinline__ int e_of(int lay, int t, int l) {
+  constexpr int LOGL = Lay<T>::LOGL, L = Lay<T>::L;
+  if (lay == 0) return t + (l << 8);
+  if (lay == 1) return (t << LOGL) + l;
+  return (t & (L - 1)) + (l << LOGL) + ((t >> LOGL) << (2 * LOGL));
+}
+
+// Butterflies on the register bits h whose tile bit (bit0 + h) lies in [lo, hi).
+template <typename T>
+__device__ __forceinline__ void reg_stages(T (&v)[FCfg<T>::L], int bit0, int lo, int hi) {
+  constexpr int L = FCfg<T>::L, LOGL = FCfg<T>::LOGL;
+#pragma unroll
+  for (int h = 0; h < LOGL; ++h) {
+    if (bit0 + h >= lo && bit0 + h < hi) {
+#pragma unroll
+      for (int q = 0; q < L; ++q)
+        if (!(q & (1 << h))) {
+          const T a = v[q], b = v[q | (1 << h)];
+          v[q] = a + b;
+          v[q | (1 << h)] = a - b;
+        }
+    }
+  }
+}
+
+// Padded tile index of element (t, l) of a layout = base(t) + stride * l.
+template <typename T>
+__device__ __forceinline__ int xbase(int lay, int t) {
+  constexpr int LOGL = Lay<T>::LOGL, L = Lay<T>::L, P = Lay<T>::PADE;
+  if (lay == 0) return t + P * (t >> LOGL);
+  if (lay == 1) return (t << LOGL) + P * t;
+  return (t & (L - 1)) + ((t >> LOGL) << (2 * LOGL)) + P * ((t >> LOGL) << LOGL);
+}
+template <typename T>
+__host__ __device__ constexpr int xstride(int lay) {
+  return lay == 0 ? 256 + Lay<T>::PADE * (256 >> Lay<T>::LOGL) : (lay == 1 ? 1 : Lay<T>::L + Lay<T>::PADE);
+}
+
+// v (layout `from`) -> v (layout `to`) through the padded tile.
+template <typename T>
+__device__ __forceinline__ void xpose(T (&v)[FCfg<T>::L], T *sm, int from, int to) {
+  constexpr int L = FCfg<T>::L, V = Lay<T>::VEC;
+  using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  const int t = threadIdx.x;
+  T *w = sm + xbase<T>(from, t);
+  if (from == 1) {
+#pragma unroll
+    for (int l = 0; l < L; l += V) *reinterpret_cast<V4 *>(w + l) = *reinterpret_cast<V4 *>(&v[l]);
+  } else if (from == 0) {
+#pragma unroll
+    for (int l = 0; l < L; ++l) w[l * xstride<T>(0)] = v[l];
+  } else {
+#pragma unroll
+    for (int l = 0; l < L; ++l) w[l * xstride<T>(2)] = v[l];
+  }
+  __syncthreads();
+  const T *rd = sm + xbase<T>(to, t);
+  if (to == 1) {
+#pragma unroll
+    for (int l = 0; l < L; l += V) *reinterpret_cast<V4 *>(&v[l]) = *reinterpret_cast<const V4 *>(rd + l);
+  } else if (to == 0) {
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = rd[l * xstride<T>(0)];
+  } else {
+#pragma unroll
+    for (int l = 0; l < L; ++l) v[l] = rd[l * xstride<T>(2)];
+  }
+  __syncthreads();
+}
+
+// Full tile WHT (bits [0, LOGT)): from L0 to L2 (dir 0) or from L2 to L0 (dir 1).
+template <typename T>
+__device__ __forceinline__ void xwht_full(T (&v)[FCfg<T>::L], T *sm, int dir) {
+  constexpr int LOGL = Lay<T>::LOGL, LOGT = Lay<T>::LOGT;
+  if (dir == 0) {
+    reg_stages<T>(v, 8, 8, LOGT);
+    xpose<T>(v, sm, 0, 1);
+    reg_stages<T>(v, 0, 0, LOGL);
+    xpose<T>(v, sm, 1, 2);
+    reg_stages<T>(v, LOGL, LOGL, 8);
+  } else {
+    reg_stages<T>(v, LOGL, LOGL, 8);
+    xpose<T>(v, sm, 2, 1);
+    reg_stages<T>(v, 0, 0, LOGL);
+    xpose<T>(v, sm, 1, 0);
+    reg_stages<T>(v, 8, 8, LOGT);
+  }
+}
+
+// Column-tile WHT on bits [c, LOGT), c >= LOGL: from L0 to L2 (dir 0) or L2 to L0 (dir 1).
+template <typename T>
+__device__ __forceinline__ void xwht_col(T (&v)[FCfg<T>::L], T *sm, int c, int dir) {
+  constexpr int LOGL = Lay<T>::LOGL, LOGT = Lay<T>::LOGT;
+  if (dir == 0) {
+    reg_stages<T>(v, 8, c, LOGT);
+    xpose<T>(v, sm, 0, 2);
+    reg_stages<T>(v, LOGL, c, 8);
+  } else {
+    reg_stages<T>(v, LOGL, c, 8);
+    xpose<T>(v, sm, 2, 0);
+    reg_stages<T>(v, 8, c, LOGT);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void reg_stages2(T (&vh)[FCfg<T>::L], T (&vl)[FCfg<T>::L], int bit0, int lo, int hi) {
+  constexpr int L = FCfg<T>::L, LOGL = FCfg<T>::LOGL;
+#pragma unroll
+  for (int h = 0; h < LOGL; ++h) {
+    if (bit0 + h >= lo && bit0 + h < hi) {
+#pragma unroll
+      for (int q = 0; q < L; ++q)
+        if (!(q & (1 << h))) cbfly(vh[q], vl[q], vh[q | (1 << h)], vl[q | (1 << h)]);
+    }
+  }
+}
+
+// Compensated (hi, lo) versions of xwht_full / xwht_col; sml: a second padded tile.
+template <typename T>
+__device__ __forceinline__ void xwht_full2(T (&vh)[FCfg<T>::L], T (&vl)[FCfg<T>::L], T *sm, T *sml, int dir) {
+  constexpr int LOGL = Lay<T>::LOGL, LOGT = Lay<T>::LOGT;
+  const int a = dir == 0 ? 0 : 2, b = dir == 0 ? 2 : 0;
+  const int a0 = dir == 0 ? 8 : LOGL, a1 = dir == 0 ? LOGT : 8, b0 = dir == 0 ? LOGL : 8, b1 = dir == 0 ? 8 : LOGT;
+  reg_stages2<T>(vh, vl, a0, a0, a1);
+  xpose<T>(vh, sm, a, 1);
+  xpose<T>(vl, sml, a, 1);
+  reg_stages2<T>(vh, vl, 0, 0, LOGL);
+  xpose<T>(vh, sm, 1, b);
+  xpose<T>(vl, sml, 1, b);
+  reg_stages2<T>(vh, vl, b0, b0, b1);
+}
+
+template <typename T>
+__device__ __forceinline__ void xwht_col2(T (&vh)[FCfg<T>::L], T (&vl)[FCfg<T>::L], T *sm, T *sml, int c, int dir) {
+  constexpr int LOGL = Lay<T>::LOGL, LOGT = Lay<T>::LOGT;
+  if (dir == 0) {
+    reg_stages2<T>(vh, vl, 8, c, LOGT);
+    xpose<T>(vh, sm, 0, 2);
+    xpose<T>(vl, sml, 0, 2);
+    reg_stages2<T>(vh, vl, LOGL, c, 8);
+  } else {
+    reg_stages2<T>(vh, vl, LOGL, c, 8);
+    xpose<T>(vh, sm, 2, 0);
+    xpose<T>(vl, sml, 2, 0);
+    reg_stages2<T>(vh, vl, 8, c, LOGT);
+  }
+}
+
 __device__ __forceinline__ float fused_log(float v) { return logf(v); }
 __device__ __forceinline__ double fused_log(double v) { return log(v); }
 
@@ -217,8 +388,9 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
   carve_tables<L>(smem, d, &wd, tb);
   T *wT = reinterpret_cast<T *>(wd);
   T *sm = reinterpret_cast<T *>(smem + align256(col_smem_bytes<L>(d)));
+  T *sml = reinterpret_cast<T *>(smem + align256(col_smem_bytes<L>(d)) + xtile_bytes<T>());
   double *red = reinterpret_cast<double *>(smem + align256(col_smem_bytes<L>(d)) +
-                                           (COMP ? 2 : 1) * tile_smem_bytes<T>());
+                                           (COMP ? 2 : 1) * xtile_bytes<T>());
   const uint32_t r = blockIdx.y, tile = blockIdx.x;
   const uint64_t n = 1ull << job.m, base = (uint64_t)tile << LOGT;
   const int t = threadIdx.x;
@@ -239,10 +411,10 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
   }
   const double sps = block_sum((double)ps - (double)pc, red);
   if (t == 0) ft.sp[(uint64_t)r * ft.tiles + tile] = sps;
-  tile_wht<T>(p, sm, 0);
+  xwht_full<T>(p, sm, 0);  // L0 -> L2
   T *PT = reinterpret_cast<T *>(ft.pT) + (uint64_t)r * n + base;
 #pragma unroll
-  for (int l = 0; l < L; ++l) PT[t + (l << kLOGNT)] = p[l];
+  for (int l = 0; l < L; ++l) PT[e_of<T>(2, t, l)] = p[l];
   for (uint32_t q = 0; q < ft.nrhs; ++q) {
     const uint64_t v = (uint64_t)r * ft.nrhs + q;
     const T *Y = reinterpret_cast<const T *>(ft.y) + v * n + base;
@@ -260,17 +432,17 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
       T yl[L];
 #pragma unroll
       for (int l = 0; l < L; ++l) yl[l] = T(0);
-      tile_wht2<T>(yv, yl, sm, sm + tile_smem_bytes<T>() / sizeof(T), 0);
+      xwht_full2<T>(yv, yl, sm, sml, 0);
       T *YL = reinterpret_cast<T *>(ft.yL) + v * n + base;
 #pragma unroll
       for (int l = 0; l < L; ++l) {
-        YT[t + (l << kLOGNT)] = yv[l];
-        YL[t + (l << kLOGNT)] = yl[l];
+        YT[e_of<T>(2, t, l)] = yv[l];
+        YL[e_of<T>(2, t, l)] = yl[l];
       }
     } else {
-      tile_wht<T>(yv, sm, 0);
+      xwht_full<T>(yv, sm, 0);
 #pragma unroll
-      for (int l = 0; l < L; ++l) YT[t + (l << kLOGNT)] = yv[l];
+      for (int l = 0; l < L; ++l) YT[e_of<T>(2, t, l)] = yv[l];
     }
   }
 }
@@ -281,36 +453,38 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
   extern __shared__ __align__(16) unsigned char smem[];
   T *sm = reinterpret_cast<T *>(smem);
-  T *lmv = reinterpret_cast<T *>(smem + tile_smem_bytes<T>());      // lambda, tile layout
-  T *gst = reinterpret_cast<T *>(smem + 2 * tile_smem_bytes<T>());  // g before its transform
-  double *red = reinterpret_cast<double *>(smem + 3 * tile_smem_bytes<T>());
+  T *lmv = reinterpret_cast<T *>(smem + xtile_bytes<T>());      // lambda (own entries)
+  T *gst = reinterpret_cast<T *>(smem + 2 * xtile_bytes<T>());  // g (own entries) / lo tile
+  double *red = reinterpret_cast<double *>(smem + 3 * xtile_bytes<T>());
   const uint32_t r = blockIdx.y, tau = blockIdx.x;
   const int c = ft.cB, t = threadIdx.x;
   const uint64_t n = 1ull << ft.job.m;
   // element (t, l) of the tile is w = (row << LOGT) | (tau << c) | col, e = t + 256 l
   const uint32_t tcol = tau << c;  // fused sizes keep n <= 2^(2 LOGT - 5) < 2^32
-  auto widx = [&](int l) -> uint32_t {
-    const uint32_t e = t + (l << kLOGNT);
-    return ((e >> c) << LOGT) | tcol | (e & ((1u << c) - 1));
-  };
+  // tile element e -> index in the vector; wi0 / wi2: the elements (t, l) of layouts L0 / L2
+  auto widx = [&](uint32_t e) -> uint32_t { return ((e >> c) << LOGT) | tcol | (e & ((1u << c) - 1)); };
+  // L0 element (t, l) has e = t + 256 l; for c <= 8 its index is w0 + l * S0
+  const bool lin = c <= kLOGNT;
+  const uint32_t w0 = widx((uint32_t)t), S0 = 1u << (LOGT + kLOGNT - c);
+  auto wi0 = [&](int l) -> uint32_t { return lin ? w0 + (uint32_t)l * S0 : widx(e_of<T>(0, t, l)); };
+  auto wi2 = [&](int l) -> uint32_t { return widx(e_of<T>(2, t, l)); };
   const T *PT = reinterpret_cast<const T *>(ft.pT) + (uint64_t)r * n;
   T lam[L];
 #pragma unroll
-  for (int l = 0; l < L; ++l) lam[l] = PT[widx(l)];
-  tile_wht<T>(lam, sm, c);
+  for (int l = 0; l < L; ++l) lam[l] = PT[wi0(l)];
+  xwht_col<T>(lam, sm, c, 0);  // L0 -> L2
   const T zeta = (T)ft.job.zeta, eta = (T)ft.eta, zn = (T)(ft.job.zeta * (double)n);
   bool bad = false;
   T lds = T(0);
   double *LAM = ft.lam ? ft.lam + (uint64_t)r * n : nullptr;
 #pragma unroll
   for (int l = 0; l < L; ++l) {
-    const uint32_t wl = widx(l);
     T v = fmadd(zeta, lam[l], eta);
-    if (wl == 0) v += zn;
+    if (l == 0 && t == 0 && tau == 0) v += zn;  // w = 0 (e = 0 in every layout)
     bad |= !(v > T(0));
     lds += fused_log(v);
-    if (LAM) LAM[wl] = (double)v;
-    lmv[fpad<T>(t + (l << kLOGNT))] = v;  // each thread reads back only its own entries
+    if (LAM) LAM[wi2(l)] = (double)v;
+    lmv[t + (l << kLOGNT)] = v;  // each thread reads back only its own entries
   }
   if (bad && ft.status) atomicOr(ft.status, (uint32_t)QK_STATUS_NOTPD);
   const double ldsum = block_sum((double)lds, red);
@@ -322,20 +496,20 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
     T *GT = reinterpret_cast<T *>(ft.gT) + v * n;
     T y[L];
 #pragma unroll
-    for (int l = 0; l < L; ++l) y[l] = YT[widx(l)];
+    for (int l = 0; l < L; ++l) y[l] = YT[wi0(l)];
     T ylo[COMP ? L : 1];
     if constexpr (COMP) {
       const T *YL = reinterpret_cast<const T *>(ft.yL) + v * n;
 #pragma unroll
-      for (int l = 0; l < L; ++l) ylo[l] = YL[widx(l)];
-      tile_wht2<T>(y, ylo, sm, gst, c);  // gst doubles as the lo tile here
+      for (int l = 0; l < L; ++l) ylo[l] = YL[wi0(l)];
+      xwht_col2<T>(y, ylo, sm, gst, c, 0);  // gst doubles as the lo tile here
     } else {
-      tile_wht<T>(y, sm, c);
+      xwht_col<T>(y, sm, c, 0);
     }
     T quad = T(0), gs = T(0);
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-      const int e = fpad<T>(t + (l << kLOGNT));  // this thread's own entries only
+      const int e = t + (l << kLOGNT);  // this thread's own entries only
       const T lw = lmv[e];
       const T il = T(1) / lw;
       const T sc = inv_n * il;          // 1 / (n lambda_w)
@@ -356,14 +530,14 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
       y[l] = ch;
       gst[e] = gg;
     }
-    tile_wht<T>(y, sm, c);
+    xwht_col<T>(y, sm, c, 1);  // L2 -> L0
 #pragma unroll
-    for (int l = 0; l < L; ++l) YT[widx(l)] = y[l];
+    for (int l = 0; l < L; ++l) YT[wi0(l)] = y[l];
 #pragma unroll
-    for (int l = 0; l < L; ++l) y[l] = gst[fpad<T>(t + (l << kLOGNT))];
-    tile_wht<T>(y, sm, c);
+    for (int l = 0; l < L; ++l) y[l] = gst[t + (l << kLOGNT)];
+    xwht_col<T>(y, sm, c, 1);
 #pragma unroll
-    for (int l = 0; l < L; ++l) GT[widx(l)] = y[l];
+    for (int l = 0; l < L; ++l) GT[wi0(l)] = y[l];
     const double sq = block_sum((double)quad, red);
     const double sg = block_sum((double)gs, red);
     if (t == 0) {
@@ -385,7 +559,7 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
   carve_tables<L>(smem, d, &wd, tb);
   T *wT = reinterpret_cast<T *>(wd);
   T *sm = reinterpret_cast<T *>(smem + align256(col_smem_bytes<L>(d)));
-  double *red = reinterpret_cast<double *>(smem + align256(col_smem_bytes<L>(d)) + tile_smem_bytes<T>());
+  double *red = reinterpret_cast<double *>(smem + align256(col_smem_bytes<L>(d)) + xtile_bytes<T>());
   const uint32_t v = blockIdx.y, r = v / ft.nrhs, tile = blockIdx.x;
   const uint64_t n = 1ull << job.m, base = (uint64_t)tile << LOGT;
   const int t = threadIdx.x;
@@ -393,8 +567,8 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
   const T *GT = reinterpret_cast<const T *>(ft.gT) + (uint64_t)v * n + base;
   T cc[L], uu[L];
 #pragma unroll
-  for (int l = 0; l < L; ++l) cc[l] = YT[t + (l << kLOGNT)];
-  tile_wht<T>(cc, sm, 0);
+  for (int l = 0; l < L; ++l) cc[l] = YT[e_of<T>(2, t, l)];
+  xwht_full<T>(cc, sm, 1);  // L2 -> L0: the thread's own points
   if (ft.c) {
     T *Cv = reinterpret_cast<T *>(ft.c) + (uint64_t)v * n + base;
 #pragma unroll
@@ -402,8 +576,10 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
   }
   if (!ft.grad) return;
 #pragma unroll
-  for (int l = 0; l < L; ++l) uu[l] = GT[t + (l << kLOGNT)];
-  tile_wht<T>(uu, sm, 0);
+  for (int l = 0; l < L; ++l) uu[l] = GT[e_of<T>(2, t, l)];
+  xwht_full<T>(uu, sm, 1);
+#pragma unroll
+  for (int l = 0; l < L; ++l) sm[t + (l << kLOGNT)] = uu[l];  // own entries, for the rare fallback
   for (uint32_t q = t; q < d; q += kFNT) wT[q] = (T)job.w[q];
   build_all<T, FAM, ALPHA, L>(job, job.Ct + (size_t)r * d * 32, job.g, base, tb);
   const T *P = reinterpret_cast<const T *>(ft.p) + (uint64_t)r * n + base;
@@ -421,7 +597,7 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
   __syncthreads();
   // u itself stays in the transform tile (sm) after tile_wht; each thread reads its own
   gradient_sweep<T, FAM, ALPHA, L>(job, tb, wT, bi, k1, uu, ok,
-                                   [&](int l) { return sm[fpad<T>(t + (l << kLOGNT))]; }, red);
+                                   [&](int l) { return sm[t + (l << kLOGNT)]; }, red);
   __syncthreads();
   double *dst = ft.gr + ((uint64_t)v * ft.tiles + tile) * 2 * d;
   for (uint32_t q = t; q < 2 * d; q += kFNT) {
@@ -485,6 +661,76 @@ __global__ void __launch_bounds__(256) k_fused_final(FTask ft) {
   }
 }
 
+// ------------------------------------------------- standalone batched WHT
+// x <- H x * scale for vectors of n = 2^m with LOGT < m <= 2 LOGT - 5, in place, in two
+// tile passes: low LOGT bits on contiguous tiles, the high bits on column tiles.
+template <typename T>
+__global__ void __launch_bounds__(kFNT) k_wht_low(T *__restrict__ x, int m) {
+  constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sm = reinterpret_cast<T *>(smem);
+  T *xb = x + ((uint64_t)blockIdx.x << LOGT);  // tiles of all vectors, contiguous
+  const int t = threadIdx.x;
+  T v[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) v[l] = xb[e_of<T>(0, t, l)];
+  xwht_full<T>(v, sm, 0);
+#pragma unroll
+  for (int l = 0; l < L; ++l) xb[e_of<T>(2, t, l)] = v[l];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFNT) k_wht_high(T *__restrict__ x, int m, T scale) {
+  constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T *sm = reinterpret_cast<T *>(smem);
+  const int c = 2 * LOGT - m, t = threadIdx.x;
+  const uint32_t tiles = 1u << (m - LOGT);
+  const uint32_t tau = blockIdx.x & (tiles - 1);
+  T *xv = x + ((uint64_t)(blockIdx.x >> (m - LOGT)) << m);
+  const uint32_t tcol = tau << c;
+  auto widx = [&](uint32_t e) -> uint32_t { return ((e >> c) << LOGT) | tcol | (e & ((1u << c) - 1)); };
+  T v[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) v[l] = xv[widx(e_of<T>(0, t, l))];
+  xwht_col<T>(v, sm, c, 0);
+#pragma unroll
+  for (int l = 0; l < L; ++l) xv[widx(e_of<T>(2, t, l))] = v[l] * scale;
+}
+
+bool tiled_wht_supported(uint32_t m, int dtype) {
+  const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
+  return (int)m > LOGT && (int)m <= 2 * LOGT - 5;
+}
+
+// Vectors may be processed in chunks (chunk_bytes) so that the second pass could find
+// the first pass's output in L2; on GB300 a sweep of 8 MB .. unchunked (64 x 2^20 FP32)
+// measured 1.17 .. 2.96 TB/s algorithmic, best unchunked (each pass then streams at
+// ~87% of the measured copy bandwidth), so the default is one launch per pass.
+template <typename T>
+static int tiled_wht_t(T *x, uint32_t m, uint64_t nvec, double scale, cudaStream_t st, size_t chunk_bytes) {
+  constexpr int LOGT = FCfg<T>::LOGT;
+  const size_t sm = xtile_bytes<T>();
+  const uint64_t n = 1ull << m;
+  uint64_t chunk = chunk_bytes / (n * sizeof(T));
+  if (chunk < 1) chunk = 1;
+  for (uint64_t v0 = 0; v0 < nvec; v0 += chunk) {
+    const uint64_t nv = (nvec - v0) < chunk ? (nvec - v0) : chunk;
+    const uint64_t blocks = nv << (m - LOGT);
+    k_wht_low<T><<<(unsigned)blocks, kFNT, sm, st>>>(x + v0 * n, (int)m);
+    int rc = check_launch("wht low");
+    if (rc) return rc;
+    k_wht_high<T><<<(unsigned)blocks, kFNT, sm, st>>>(x + v0 * n, (int)m, (T)scale);
+    if ((rc = check_launch("wht high"))) return rc;
+  }
+  return QK_OK;
+}
+
+int tiled_wht(void *x, uint32_t m, uint64_t nvec, int dtype, double scale, cudaStream_t st, size_t chunk_bytes) {
+  return dtype == QK_F64 ? tiled_wht_t<double>((double *)x, m, nvec, scale, st, chunk_bytes)
+                         : tiled_wht_t<float>((float *)x, m, nvec, scale, st, chunk_bytes);
+}
+
 // ------------------------------------------------------------------ host side
 bool fused_supported(const qk_task &t, int dtype) {
   if (t.k.family != QK_DSI || t.ps.kind != QK_NET_B2) return false;
@@ -506,43 +752,51 @@ size_t fused_ws_bytes(const qk_task &t, int dtype, int refine) {
 }
 
 template <typename T, int FAM, int ALPHA, bool COMP>
-static int launch_fused_t(const FTask &ft, cudaStream_t st) {
+static int launch_fused_t(const FTask &ft, cudaStream_t st, LaunchTimer *tm) {
   constexpr int L = FCfg<T>::L;
   const uint32_t R = ft.job.nr, d = ft.job.d;
   const size_t colb = align256(col_smem_bytes<L>(d));
   // phase A keeps a second tile for the lo parts when compensating
-  const size_t smA = colb + (COMP ? 2 : 1) * tile_smem_bytes<T>() + 32 * sizeof(double);
-  const size_t smB = 3 * tile_smem_bytes<T>() + 32 * sizeof(double);
-  const size_t smC = colb + tile_smem_bytes<T>() + (size_t)(kFNT / 32) * 2 * d * sizeof(double);
+  const size_t smA = colb + (COMP ? 2 : 1) * xtile_bytes<T>() + 32 * sizeof(double);
+  const size_t smB = 3 * xtile_bytes<T>() + 32 * sizeof(double);
+  const size_t smC = colb + xtile_bytes<T>() + (size_t)(kFNT / 32) * 2 * d * sizeof(double);
   smem_optin<k_fused_A<T, FAM, ALPHA, COMP>>(smA);
   smem_optin<k_fused_B<T, COMP>>(smB);
   smem_optin<k_fused_C<T, FAM, ALPHA>>(smC);
+  if (tm) tm->begin("k_fused_A", st);
   k_fused_A<T, FAM, ALPHA, COMP><<<dim3(ft.tiles, R), kFNT, smA, st>>>(ft);
+  if (tm) tm->end(st);
   int rc = check_launch("fused A");
   if (rc) return rc;
+  if (tm) tm->begin("k_fused_B", st);
   k_fused_B<T, COMP><<<dim3(ft.tiles, R), kFNT, smB, st>>>(ft);
+  if (tm) tm->end(st);
   if ((rc = check_launch("fused B"))) return rc;
   if (ft.c || ft.grad) {
+    if (tm) tm->begin("k_fused_C", st);
     k_fused_C<T, FAM, ALPHA><<<dim3(ft.tiles, R * ft.nrhs), kFNT, smC, st>>>(ft);
+    if (tm) tm->end(st);
     if ((rc = check_launch("fused C"))) return rc;
   }
+  if (tm) tm->begin("k_fused_final", st);
   k_fused_final<<<R * ft.nrhs, 256, 0, st>>>(ft);
+  if (tm) tm->end(st);
   return check_launch("fused final");
 }
 
 template <typename T, bool COMP>
-static int dispatch_fused(const FTask &ft, cudaStream_t st) {
+static int dispatch_fused(const FTask &ft, cudaStream_t st, LaunchTimer *tm) {
   switch (ft.job.alpha) {
-    case 1: return launch_fused_t<T, 0, 1, COMP>(ft, st);
-    case 2: return launch_fused_t<T, 0, 2, COMP>(ft, st);
-    case 3: return launch_fused_t<T, 0, 3, COMP>(ft, st);
-    case 4: return launch_fused_t<T, 0, 4, COMP>(ft, st);
+    case 1: return launch_fused_t<T, 0, 1, COMP>(ft, st, tm);
+    case 2: return launch_fused_t<T, 0, 2, COMP>(ft, st, tm);
+    case 3: return launch_fused_t<T, 0, 3, COMP>(ft, st, tm);
+    case 4: return launch_fused_t<T, 0, 4, COMP>(ft, st, tm);
     default: return fail(QK_EINVAL, "DSI order must be 1..4");
   }
 }
 
 int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *ws, uint32_t *status,
-              cudaStream_t st) {
+              cudaStream_t st, LaunchTimer *tm) {
   const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
   const uint64_t R = t.ps.R, n = 1ull << t.m, tiles = n >> LOGT, nv = R * t.nrhs;
   const size_t e = fused_elem(dtype);
@@ -572,12 +826,12 @@ int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *
   ft.yL = nullptr;
   // FP64 needs no refinement; FP32 with refine >= 1 runs the compensated variant
   // (one exact-residual step; further steps change nothing at FP32 resolution)
-  if (dtype == QK_F64) return dispatch_fused<double, false>(ft, st);
+  if (dtype == QK_F64) return dispatch_fused<double, false>(ft, st, tm);
   if (refine > 0) {
     ft.yL = p;
-    return dispatch_fused<float, true>(ft, st);
+    return dispatch_fused<float, true>(ft, st, tm);
   }
-  return dispatch_fused<float, false>(ft, st);
+  return dispatch_fused<float, false>(ft, st, tm);
 }
 
 }  // namespace qk

@@ -8,6 +8,13 @@
 
 namespace qk {
 
+// Optional per-launch event recorder (qk_batch_timing); begin/end bracket one launch.
+struct LaunchTimer {
+  virtual void begin(const char *name, cudaStream_t st) = 0;
+  virtual void end(cudaStream_t st) = 0;
+  virtual ~LaunchTimer() {}
+};
+
 // Point-set description resolved for one randomization range.
 struct ColJob {
   int32_t kind, order;
@@ -36,9 +43,12 @@ int launch_lms(uint32_t d, uint32_t R, const uint32_t *C, const uint32_t *S, uin
                cudaStream_t st);
 
 bool fused_supported(const qk_task &t, int dtype);
+bool tiled_wht_supported(uint32_t m, int dtype);
+int tiled_wht(void *x, uint32_t m, uint64_t nvec, int dtype, double scale, cudaStream_t st,
+              size_t chunk_bytes = ~(size_t)0);
 size_t fused_ws_bytes(const qk_task &t, int dtype, int refine);
 int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *ws, uint32_t *status,
-              cudaStream_t st);
+              cudaStream_t st, LaunchTimer *tm = nullptr);
 }  // namespace qk
 
 namespace qk {

@@ -428,6 +428,7 @@ int op_mll(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const
 
 int op_transform(int kind, uint32_t m, uint64_t nvec, int dtype, void *x, cudaStream_t st) {
   const double scale = 1.0 / std::sqrt((double)(1ull << m));
+  if (kind == XF_WHT && tiled_wht_supported(m, dtype)) return tiled_wht(x, m, nvec, dtype, scale, st);
   if (kind == XF_WHT)
     return dtype == QK_F64 ? xform<double, XF_WHT>((double *)x, (int)m, nvec, scale, st)
                            : xform<float, XF_WHT>((float *)x, (int)m, nvec, scale, st);

@@ -30,7 +30,7 @@ OP_EIGS, OP_SOLVE, OP_MATVEC, OP_MLL = 0, 1, 2, 3
 EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_solve", "qk_matvec", "qk_mll",
             "qk_batch_workspace_bytes", "qk_batch_plan", "qk_batch_run", "qk_workspace_bytes",
             "qk_read_status", "qk_last_error", "qk_version", "qk_fwht", "qk_fftbr", "qk_ifftbr",
-            "qk_launch_count", "qk_eigs_static"]
+            "qk_launch_count", "qk_eigs_static", "qk_batch_timing", "qk_batch_kernel_ms"]
 
 
 class QKError(RuntimeError):
@@ -80,6 +80,8 @@ def _load():
         "qk_ifftbr": [u32, u64, i32, P, P],
         "qk_launch_count": [],
         "qk_eigs_static": [i32, u32, u32, i32, i32, P, dbl, dbl, P, P, P],
+        "qk_batch_timing": [P, u32],
+        "qk_batch_kernel_ms": [P, u32, C.c_char_p, sz, C.POINTER(u32), C.POINTER(dbl)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -268,3 +270,23 @@ def batch_plan(tasks, dtype: torch.dtype, refine_steps: int, ws, stream=None):
 
 def batch_run(ws, status=None, stream=None):
     _check(LIB.qk_batch_run(_ptr(ws), ws.numel(), _ptr(status), _stream(stream)))
+
+
+def batch_timing(ws, runs: int):
+    """Record CUDA events around each kernel of the next `runs` batch_run calls."""
+    _check(LIB.qk_batch_timing(_ptr(ws), runs))
+
+
+def batch_kernel_ms(ws):
+    """{kernel name: (launches, summed ms)} of the recorded runs."""
+    out, idx = {}, 0
+    while True:
+        name = C.create_string_buffer(64)
+        cnt = C.c_uint32(0)
+        ms = C.c_double(0.0)
+        rc = LIB.qk_batch_kernel_ms(_ptr(ws), idx, name, 64, C.byref(cnt), C.byref(ms))
+        if rc != QK_OK:
+            break
+        out[name.value.decode()] = (cnt.value, ms.value)
+        idx += 1
+    return out
