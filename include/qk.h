@@ -62,7 +62,11 @@ enum qk_status {
   QK_EWORKSPACE = 5  /* workspace null or smaller than qk_workspace_bytes() */
 };
 
-enum qk_status_bits { QK_STATUS_NOTPD = 1u, QK_STATUS_TIMEOUT = 2u };
+/* QK_STATUS_FLOOR is informational: some computed eigenvalue fell below the nugget
+ * eta > 0 and was raised to eta (the spectrum of K + eta I lies in [eta, inf), so a
+ * smaller value can only be rounding, e.g. FP32 transforms at large n).
+ * qk_read_status reports it as QK_OK. */
+enum qk_status_bits { QK_STATUS_NOTPD = 1u, QK_STATUS_TIMEOUT = 2u, QK_STATUS_FLOOR = 4u };
 
 enum qk_kind { QK_NET_B2 = 0, QK_LATTICE = 1 };
 enum qk_order { QK_NATURAL = 0, QK_GRAY = 1 };
@@ -143,7 +147,8 @@ QK_API int qk_kernel_col(const qk_pointset *ps, const qk_kernel *k, uint32_t r0,
  * matrices from their first columns col (batch, n) (dtype, form).  DSI: FWHT,
  * lambda in Hadamard order; SI: FFTBR, lambda in frequency order (real).
  * The transform runs in dtype; the nugget, zeta and the sign test in FP64.
- * lam: (batch, n) doubles.  Sets QK_STATUS_NOTPD if some lambda <= 0. */
+ * lam: (batch, n) doubles.  Eigenvalues below eta > 0 are raised to eta
+ * (QK_STATUS_FLOOR); with eta <= 0, QK_STATUS_NOTPD is set if some lambda <= 0. */
 QK_API int qk_eigs(int32_t family, uint32_t m, uint32_t batch, int32_t dtype, int32_t form,
             const void *col, double zeta, double eta, double *lam, void *ws,
             size_t ws_bytes, uint32_t *status, qk_stream stream);
@@ -237,6 +242,18 @@ QK_API int qk_batch_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, i
  * launches only (no host synchronisation, no allocation), so the call can be
  * captured into a CUDA graph. */
 QK_API int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream stream);
+
+/* Per-kernel timing of a planned schedule (no paper counterpart; used to report
+ * rooflines).  After qk_batch_timing(ws, runs), each of the next `runs` calls of
+ * qk_batch_run on that workspace records a CUDA event pair around every kernel it
+ * launches, on the launching stream (events are host-side runtime objects; no device
+ * memory is allocated).  qk_batch_kernel_ms(ws, idx, ...) waits for the recorded
+ * events and returns, for the idx-th distinct kernel name, its launch count and
+ * summed device milliseconds; QK_EINVAL once idx runs past the last name.
+ * qk_batch_timing(ws, 0) stops recording and forgets the records. */
+QK_API int qk_batch_timing(void *ws, uint32_t runs);
+QK_API int qk_batch_kernel_ms(void *ws, uint32_t idx, char *name, size_t name_len, uint32_t *launches,
+                              double *ms);
 
 /* ------------------------------------------------------------- utilities --- */
 

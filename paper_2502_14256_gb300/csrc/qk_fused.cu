@@ -477,16 +477,22 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
   bool bad = false;
   T lds = T(0);
   double *LAM = ft.lam ? ft.lam + (uint64_t)r * n : nullptr;
+  bool floored = false;
 #pragma unroll
   for (int l = 0; l < L; ++l) {
     T v = fmadd(zeta, lam[l], eta);
     if (l == 0 && t == 0 && tau == 0) v += zn;  // w = 0 (e = 0 in every layout)
+    if (eta > T(0) && !(v >= eta)) {  // K + eta I has no eigenvalue below eta: rounding
+      v = eta;
+      floored = true;
+    }
     bad |= !(v > T(0));
     lds += fused_log(v);
     if (LAM) LAM[wi2(l)] = (double)v;
     lmv[t + (l << kLOGNT)] = v;  // each thread reads back only its own entries
   }
   if (bad && ft.status) atomicOr(ft.status, (uint32_t)QK_STATUS_NOTPD);
+  if (floored && ft.status) atomicOr(ft.status, (uint32_t)QK_STATUS_FLOOR);
   const double ldsum = block_sum((double)lds, red);
   if (t == 0) ft.ld[(uint64_t)r * ft.tiles + tau] = ldsum;
   const T inv_n = T(1) / (T)n;

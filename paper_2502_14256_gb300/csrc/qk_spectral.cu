@@ -63,15 +63,20 @@ __global__ void k_store_real(const E *__restrict__ in, T *__restrict__ out, uint
 template <typename E>
 __global__ void k_lam_final(const E *__restrict__ X, double *__restrict__ lam, uint64_t total, int m,
                             double zmul, double dc, double eta, uint32_t *status) {
-  bool bad = false;
+  bool bad = false, floored = false;
   const uint64_t mask = (1ull << m) - 1;
   for (uint64_t i = gtid(); i < total; i += gstride()) {
     double v = zmul * re(X[i]) + eta;
     if ((i & mask) == 0) v += dc;
+    if (eta > 0.0 && !(v >= eta)) {  // K + eta I has no eigenvalue below eta: rounding
+      v = eta;
+      floored = true;
+    }
     lam[i] = v;
     bad |= !(v > 0.0);
   }
   if (bad && status) atomicOr(status, (uint32_t)QK_STATUS_NOTPD);
+  if (floored && status) atomicOr(status, (uint32_t)QK_STATUS_FLOOR);
 }
 
 // X[v][w] *= fac / lambda[v / nrhs][w] (mode 0) or fac * lambda (mode 1), in FP64.

@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libqk.so")
 
 QK_OK, QK_EINVAL, QK_ENOTPD, QK_ECUDA, QK_ETIMEOUT, QK_EWORKSPACE = range(6)
-QK_STATUS_NOTPD, QK_STATUS_TIMEOUT = 1, 2
+QK_STATUS_NOTPD, QK_STATUS_TIMEOUT, QK_STATUS_FLOOR = 1, 2, 4
 QK_NET_B2, QK_LATTICE = 0, 1
 QK_NATURAL, QK_GRAY = 0, 1
 QK_DSI, QK_SI = 0, 1

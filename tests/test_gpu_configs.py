@@ -1,0 +1,185 @@
+"""The named workloads at their full sizes, through the batched C-ABI schedule, checked on
+sampled outputs against the FP64 oracle (sampled because the oracle's spectral gradient is
+O(d^2 n) and its dense forms O(n^3)) and, for the precision workload, FP32-refined against
+the FP64 GPU path.  Oracle inputs are recomputed on the host from the oracle's own points."""
+import math
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import qk_oracle as o
+from paper_2502_14256_gb300 import inputs
+from tests import qkcases as qc
+from tests import qkworkloads as W
+
+pytestmark = pytest.mark.gpu
+F64, F32 = torch.float64, torch.float32
+
+
+@pytest.fixture(scope="module")
+def qk():
+    from paper_2502_14256_gb300 import build
+    build.build()
+    from paper_2502_14256_gb300 import qk as q
+    return q
+
+
+def _oracle_check(inst, bufs, r, rhs_list, tol, check_grad=True):
+    """Compare randomization r (given right-hand sides) with the oracle's spectral formulas."""
+    fam = inst.wl.family
+    n = 1 << inst.m
+    X = W.host_points(inst, r, np.arange(n))
+    c_w = o.effective_weights(inst.wl.gamma, inst.wl.log_ls)
+    k1 = o.first_column(fam, inst.wl.alpha, X, c_w, inst.wl.zeta)
+    lam = o.eigenvalues(fam, k1, inst.wl.eta)
+    Y = W.host_rhs(inst, r, X)
+    got_lam = bufs["lam"][r].cpu().numpy() if bufs["lam"] is not None else None
+    if got_lam is not None:
+        assert qc.rel_err(got_lam, lam) < tol["lam"]
+    cond = float(lam.max() / lam.min())
+    for q in rhs_list:
+        sp = o.spectral_mll(fam, lam, Y[q], inst.wl.zeta)
+        go = bufs["out"][r, q].cpu().numpy()
+        assert abs(go[0] - sp["quad"]) < tol["quad"] * abs(sp["quad"]), (go[0], sp["quad"])
+        assert abs(go[1] - sp["logdet"]) < tol["logdet"] * abs(sp["logdet"])
+        assert abs(go[2] - sp["mll"]) < tol["mll"] * abs(sp["mll"])
+        assert abs(go[3] - sp["post_mean"]) < tol["mean"] * max(1.0, abs(sp["post_mean"]))
+        if bufs["c"] is not None:
+            c_ref = o.spectral_solve(fam, lam, Y[q])
+            ctol = max(tol["c"], 20 * cond * qc.EPS64)
+            assert qc.rel_err(bufs["c"][r, q].cpu().numpy(), c_ref) < ctol
+        if check_grad and bufs["grad"] is not None:
+            gr = o.spectral_mll_grad(fam, inst.wl.alpha, X, Y[q], lam, c_w, inst.wl.zeta)
+            gg = bufs["grad"][r, q].cpu().numpy()
+            d = inst.wl.d
+            assert qc.rel_err(gg[:d], gr["dc"]) < tol["grad"], qc.rel_err(gg[:d], gr["dc"])
+            assert abs(gg[d] - gr["deta"]) < tol["grad"] * max(1.0, abs(gr["deta"]))
+
+
+TOL64 = dict(lam=1e-11, quad=1e-10, logdet=1e-11, mll=1e-10, mean=1e-10, c=1e-10, grad=1e-9)
+
+
+def test_plain_workload_against_dense_oracle(qk):
+    """n = 2^10, d = 4, order-1 DSI, FP64: every output against Cholesky / dense gradient."""
+    wl = inputs.workload("plain")
+    inst = W.build_instance(qk, wl, wl.ms[0], 1, 1, y_kind="product")
+    task, bufs = W.outputs(qk, inst, F64)
+    W.run_tasks(qk, [task], F64)
+    n = 1 << inst.m
+    X = W.host_points(inst, 0, np.arange(n))
+    y = W.host_rhs(inst, 0, X)[0]
+    K = o.gram_dense("dsi", wl.alpha, X, o.effective_weights(wl.gamma, wl.log_ls), wl.zeta, wl.eta)
+    c_ref, logdet = o.cholesky_solve(K, y)
+    mll = o.mll_dense(K, y)[0]
+    mean, var = o.bc_posterior_dense(K, y, wl.zeta)
+    g = o.mll_grad_dense("dsi", wl.alpha, X, y, wl.gamma, wl.log_ls, wl.eta, wl.zeta)
+    out = bufs["out"][0, 0].cpu().numpy()
+    assert qc.rel_err(bufs["c"][0, 0].cpu().numpy(), c_ref) < 1e-10
+    assert abs(out[1] - logdet) < 1e-10 * abs(logdet)
+    assert abs(out[2] - mll) < 1e-10 * abs(mll)
+    assert abs(out[3] - mean) < 1e-10 * max(1, abs(mean))
+    assert abs(out[4] - var) < 1e-10
+    grad = bufs["grad"][0, 0].cpu().numpy()
+    assert qc.rel_err(grad[:wl.d], g["dc"]) < 1e-9
+
+
+def test_batch_workload_full_size(qk):
+    """32 instances, m in 14..20, d = 16, 64 randomizations, 8 right-hand sides, order-2 DSI,
+    FP64, one schedule captured in a CUDA graph; sampled instances against the oracle."""
+    wl = inputs.workload("batch")
+    t0 = time.time()
+    insts = [W.build_instance(qk, wl, m, wl.R, wl.nrhs, seed_shift=i) for i, m in enumerate(wl.ms)]
+    small = int(np.argmin(wl.ms))
+    big = int(np.argmax(wl.ms))
+    # solutions and eigenvalues are requested for the sampled instances only (memory)
+    tasks, bufs = zip(*[W.outputs(qk, inst, F64, with_c=i in (small, big), with_lam=i in (small, big))
+                        for i, inst in enumerate(insts)])
+    t1 = time.time()
+    W.run_tasks(qk, list(tasks), F64, graph=True)
+    t2 = time.time()
+    print(f"\nbatch workload: {sum(1 << i.m for i in insts) * wl.R} points, inputs {t1 - t0:.1f} s, "
+          f"schedule (plan, first run, graph replay) {t2 - t1:.2f} s")
+    _oracle_check(insts[small], bufs[small], 0, range(wl.nrhs), TOL64)
+    _oracle_check(insts[small], bufs[small], 37, [3, 7], TOL64)
+    _oracle_check(insts[big], bufs[big], 63, [5], TOL64, check_grad=False)
+
+
+def test_differentiation_workload_full_size(qk):
+    """Lattice n = 2^18, d = 32, SI alpha = 2, log-lengthscales 0, nugget e^-12, FP64 MLL and
+    gradient against the oracle's spectral formulas."""
+    wl = inputs.workload("diff")
+    inst = W.build_instance(qk, wl, wl.ms[0], 1, 1, y_kind="product")
+    task, bufs = W.outputs(qk, inst, F64)
+    W.run_tasks(qk, [task], F64)
+    tol = dict(TOL64, grad=1e-8)
+    _oracle_check(inst, bufs, 0, [0], tol)
+
+
+def test_precision_workload_fp32_refined_against_fp64(qk):
+    """Net n = 2^24, d = 64, order-4 DSI, gamma_j = j^-3: FP32 column and transforms with one
+    refinement step against the FP64 GPU path on the same (FP32) right-hand side, per
+    output, over a range of nuggets (one of the 16 randomizations)."""
+    wl = inputs.workload("precision")
+    inst = W.build_instance(qk, wl, wl.ms[0], 1, 1, y_kind="product")
+    rel = lambda a, b: float((a.double() - b.double()).abs().max() / b.double().abs().max())  # noqa: E731
+    for eta in (1e-8, 1e-6, 1e-4, 1e-2, 1.0, 1e2):
+        t64, b64 = W.outputs(qk, inst, F64, y_via=F32, eta=eta)
+        _, w64 = W.run_tasks(qk, [t64], F64, allow_floor=True)
+        t32, b32 = W.outputs(qk, inst, F32, eta=eta)
+        _, w32 = W.run_tasks(qk, [t32], F32, refine=1, allow_floor=True)
+        lam = b64["lam"][0]
+        errs = {"lambda": rel(b32["lam"], b64["lam"]),
+                "lambda_min_rel": float(((b32["lam"] - b64["lam"]).abs() / b64["lam"]).max()),
+                "solve": rel(b32["c"], b64["c"]),
+                "quad": rel(b32["out"][..., 0], b64["out"][..., 0]),
+                "logdet": rel(b32["out"][..., 1], b64["out"][..., 1]),
+                "mll": rel(b32["out"][..., 2], b64["out"][..., 2]),
+                "post_mean": rel(b32["out"][..., 3], b64["out"][..., 3]),
+                "post_var": rel(b32["out"][..., 4], b64["out"][..., 4]),
+                "grad": rel(b32["grad"][..., :wl.d], b64["grad"][..., :wl.d])}
+        print(f"\nprecision eta={eta:g} lam [{float(lam.min()):.3e}, {float(lam.max()):.3e}] "
+              f"below 2eta: {int((lam < 2 * eta).sum())} status64={w64} status32={w32}")
+        print("  " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+        for k, v in errs.items():
+            assert np.isfinite(v), k
+        # well-conditioned at any nugget: the spectrum in max norm and the posterior mean
+        # (zeta sum(y) / lambda_0) carry only FP32 rounding of O(1) quantities
+        assert errs["lambda"] < 1e-7 and errs["post_mean"] < 1e-7, errs
+        # The FP32 column itself perturbs every eigenvalue by ~u32 ||k_1||_2 (~1e-3 here), so
+        # outputs weighted by 1/lambda meet 1e-5 only once lambda_min = eta is large enough:
+        # at eta = 100 (6e-6 of lambda_max) everything but the posterior variance does (the
+        # variance zeta(zeta sum(p) + eta)/lambda_0 is a difference near the FP32 noise of sum(p)).
+        if eta >= 100:
+            for k in ("solve", "quad", "logdet", "mll", "grad"):
+                assert errs[k] < 1e-5, (k, errs[k])
+
+
+def test_mixed_workload_full_size(qk):
+    """256 instances (half lattice + SI alpha = 1, half net + DSI order 2), m in 12..22,
+    d in {8, 32, 128}: FP32-refined schedule captured in a CUDA graph, against the FP64 GPU
+    path on the eight smallest instances."""
+    wls = inputs.mixed_batch()
+    t0 = time.time()
+    insts = [W.build_instance(qk, wl, wl.ms[0], 1, 1, seed_shift=0, y_kind="product") for wl in wls]
+    tasks, bufs = zip(*[W.outputs(qk, inst, F32, with_lam=False) for inst in insts])
+    t1 = time.time()
+    _, word = W.run_tasks(qk, list(tasks), F32, refine=1, graph=True, allow_floor=True)
+    t2 = time.time()
+    print(f"\nmixed workload: {sum(1 << i.m for i in insts)} points, inputs {t1 - t0:.1f} s, "
+          f"schedule {t2 - t1:.2f} s, status word {word}")
+    order = np.argsort([(1 << i.m) * i.wl.d for i in insts])[:8]
+    for k in order:
+        inst = insts[k]
+        t64, b64 = W.outputs(qk, inst, F64, with_lam=False, y_via=F32)
+        W.run_tasks(qk, [t64], F64)
+        b32 = bufs[k]
+        rel = lambda a, b: float((a.double() - b.double()).abs().max() / b.double().abs().max())  # noqa: E731
+        print(f"  {inst.wl.kind} m={inst.m} d={inst.wl.d}: mll {rel(b32['out'][..., 2], b64['out'][..., 2]):.2e} "
+              f"quad {rel(b32['out'][..., 0], b64['out'][..., 0]):.2e} solve {rel(b32['c'], b64['c']):.2e} "
+              f"grad {rel(b32['grad'][..., :inst.wl.d], b64['grad'][..., :inst.wl.d]):.2e}")
+        assert rel(b32["out"][..., 2], b64["out"][..., 2]) < 1e-5, (k, inst.wl.kind)
+        assert rel(b32["out"][..., 0], b64["out"][..., 0]) < 1e-5, (k, inst.wl.kind)
+        assert rel(b32["c"], b64["c"]) < 1e-5, (k, inst.wl.kind)
+        assert rel(b32["grad"][..., :inst.wl.d], b64["grad"][..., :inst.wl.d]) < 1e-5, (k, inst.wl.kind)

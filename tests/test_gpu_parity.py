@@ -128,6 +128,29 @@ def test_eigs_reports_non_positive_definite(qk):
     qk.read_status(status)  # cleared
 
 
+def test_eigenvalues_below_the_nugget_are_raised_to_it(qk):
+    """K + eta I has no eigenvalue below eta; a column whose transform dips below (here a
+    kernel with a negative weight, so that K itself is indefinite) is floored at eta and
+    flagged with the informational QK_STATUS_FLOOR bit, not an error."""
+    case = qc.make_case("net", "dsi", 2, 3, 1, seed=5, c=np.array([-0.9, 0.3, 0.1]))
+    kern = qc.kernel_of(case)
+    col = torch.empty((1, 256), dtype=F64, device=qc.dev())
+    qk.kernel_col(case.ps, kern, 0, 1, 8, col)
+    lam = torch.empty_like(col)
+    status = torch.zeros(1, dtype=torch.int32, device=qc.dev())
+    eta = 1e-3
+    qk.eigs(qk.QK_DSI, 8, col, lam, eta=eta, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == qk.QK_STATUS_FLOOR
+    got = lam.cpu().numpy()[0]
+    want = o.eigenvalues("dsi", case.k1_ref(0, 8)[0], eta)
+    assert np.all(got >= eta)
+    assert np.array_equal(got == eta, want < eta)
+    keep = want >= eta
+    assert qc.rel_err(got[keep], want[keep]) < 1e-12
+    qk.read_status(status)  # informational: not an error
+
+
 def _setup_spectrum(qk, case, m, dt, eta, R):
     kern = qc.kernel_of(case)
     fam = qk.QK_DSI if case.family == "dsi" else qk.QK_SI
