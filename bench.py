@@ -294,10 +294,13 @@ def main():
                                      3, 1, stream)
     # FWHT alone on the same data volume (in place, FP32): HBM roofline of the transform
     xf = torch.randn((R, n), dtype=torch.float32, device=dev)
-    fw_ms = time_steps(torch, lambda: q.fwht(m, xf), args.steps, 2, stream)
+    fw_ws = q.fwht_workspace(R, dev)
+    fw_plan = q.fwht_tune(m, xf, fw_ws)  # autotuned plan (xf is scratch here)
+    fw_ms = time_steps(torch, lambda: q.fwht_ws(m, xf, fw_ws), args.steps, 2, stream)
+    fw2_ms = time_steps(torch, lambda: q.fwht(m, xf), args.steps, 2, stream)
     fw_bytes = 2 * xf.numel() * 4  # one read + one write per element (the algorithmic minimum)
     fw_gbs = fw_bytes / (fw_ms * 1e-3) / 1e9
-    del xf
+    del xf, fw_ws
 
     # ---- plain FP64 pipeline beside it
     fp64 = None
@@ -369,7 +372,8 @@ def main():
             "kernels_ms_per_step": {k: v[1] / max(1, args.steps) for k, v in kernel_ms.items()},
             "fwht": {"gbs": fw_gbs, "ms": fw_ms, "frac_of_hbm": fw_gbs / hbm_peak, "bytes": fw_bytes,
                      "peak": hbm_peak, "peak_source": peak_src,
-                     "shape": f"{R} x 2^{m} fp32, in place, two tile passes per L2-sized chunk"},
+                     "shape": f"{R} x 2^{m} fp32, in place", "plan": fw_plan,
+                     "two_launch_ms": fw2_ms, "two_launch_gbs": fw_bytes / (fw2_ms * 1e-3) / 1e9},
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks,

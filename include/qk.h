@@ -211,6 +211,44 @@ QK_API int qk_fwht(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_stream 
 QK_API int qk_fftbr(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_stream stream);
 QK_API int qk_ifftbr(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_stream stream);
 
+/* qk_fwht with a workspace: the same transform (bit for bit: the same butterflies in the
+ * same order), for 2^13 < n <= 2^21 (FP32) or 2^12 < n <= 2^19 (FP64) run either as two
+ * launches (low bits on contiguous tiles, then high bits on column tiles) or as ONE
+ * persistent launch in which resident CTAs take tiles from a global ticket counter and a
+ * vector's column tiles are queued `lag` vectors after its low tiles, so that its
+ * first-pass output is still in L2 when read back.  Which one runs, with which lag and
+ * CTAs per SM, is the choice qk_fwht_tune recorded for (device, m, dtype, nvec), else the
+ * persistent launch with a lag from the grid size; a non-NULL `plan` (host) overrides
+ * both.  Other sizes run qk_fwht's transform.
+ * ws: (1 + nvec) 32-bit counters, 256-byte aligned (qk_workspace_bytes op 4; reset by the
+ * call itself).  A column tile waits for its vector's low tiles with a bounded wait
+ * (about 1 s); past it the tile is skipped and QK_STATUS_TIMEOUT is set in `status`
+ * (nullable).  Graph-capturable. */
+typedef struct {
+  int32_t mode;          /* QK_FWHT_TWO_PASS or QK_FWHT_PERSISTENT */
+  uint32_t lag;          /* persistent: vectors between low and column tiles (0 = automatic) */
+  uint32_t ctas_per_sm;  /* persistent: resident CTAs per SM (0 = the occupancy limit) */
+  float ms;              /* tuner: measured milliseconds per transform of the batch */
+} qk_fwht_plan;
+#define QK_FWHT_TWO_PASS 0
+#define QK_FWHT_PERSISTENT 1
+QK_API int qk_fwht_ws(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes,
+                      const qk_fwht_plan *plan, uint32_t *status, qk_stream stream);
+
+/* Autotuner for qk_fwht_ws (the paper has no counterpart): times the two-launch form and
+ * the persistent launch over CTAs per SM x lag on the caller's buffer x (its contents are
+ * overwritten: used as scratch), records the fastest for (current device, m, dtype, nvec)
+ * and returns it in *best (nullable).  Synchronises the stream; not capturable. */
+QK_API int qk_fwht_tune(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes,
+                        qk_fwht_plan *best, qk_stream stream);
+
+/* Test of the persistent launch's bounded wait (no counterpart in the paper): runs only
+ * the column tiles of qk_fwht_ws with no low tile published, so that every wait runs
+ * out after spin_limit sleeps of ~128 ns (1 .. 2^23); each tile is then skipped (x is
+ * left unchanged) and QK_STATUS_TIMEOUT is set in `status` (required). */
+QK_API int qk_fwht_wait_selftest(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes,
+                                 uint32_t spin_limit, uint32_t *status, qk_stream stream);
+
 /* --------------------------------------------------------------- batching --- */
 
 /* One task of a batched schedule: R randomizations of one point set and kernel,
@@ -257,8 +295,8 @@ QK_API int qk_batch_kernel_ms(void *ws, uint32_t idx, char *name, size_t name_le
 
 /* ------------------------------------------------------------- utilities --- */
 
-/* Workspace bytes needed by qk_eigs / qk_solve / qk_matvec / qk_mll with these
- * sizes (op: 0 eigs, 1 solve, 2 matvec, 3 mll). */
+/* Workspace bytes needed by qk_eigs / qk_solve / qk_matvec / qk_mll / qk_fwht_ws with
+ * these sizes (op: 0 eigs, 1 solve, 2 matvec, 3 mll, 4 fwht_ws with batch = nvec). */
 QK_API int qk_workspace_bytes(int32_t op, int32_t family, uint32_t m, uint32_t batch, uint32_t nrhs,
                        int32_t dtype, uint32_t d, size_t *bytes);
 

@@ -183,6 +183,7 @@ int qk_workspace_bytes(int32_t op, int32_t family, uint32_t m, uint32_t batch, u
     case 1: *bytes = ws_solve(family, m, batch, nrhs, dtype); break;
     case 2: *bytes = align256(elem_bytes(family, dtype) * (((uint64_t)batch * nrhs) << m)); break;
     case 3: *bytes = ws_mll(family, m, batch, nrhs, dtype, d); break;
+    case 4: *bytes = persist_wht_ws_bytes(batch); break;
     default: return fail(QK_EINVAL, "unknown op %d", op);
   }
   return QK_OK;

@@ -21,6 +21,7 @@
 // low 8 bits in padded shared memory in radix-16 rounds.
 #include <cmath>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "qk_column.cuh"
@@ -232,13 +233,34 @@ __device__ __forceinline__ int e_of(int lay, int t, int l) {
   return (t & (L - 1)) + (l << LOGL) + ((t >> LOGL) << (2 * LOGL));
 }
 
-// Butterflies on the register bits h whose tile bit (bit0 + h) lies in [lo, hi).
+// Two FP32 butterflies in one packed instruction pair: (a0, a1) +- (b0, b1) (sm_100+ f32x2).
+__device__ __forceinline__ void bfly_x2(float &a0, float &a1, float &b0, float &b1) {
+  unsigned long long A, B, S, D;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a0), "f"(a1));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b0), "f"(b1));
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(S) : "l"(A), "l"(B));
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(D) : "l"(A), "l"(B));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(S));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(b0), "=f"(b1) : "l"(D));
+}
+
+// Butterflies on the register bits h whose tile bit (bit0 + h) lies in [lo, hi).  FP32
+// stages on bits h >= 1 pair neighbouring registers into packed f32x2 adds (the same
+// roundings as scalar adds, half the instructions).
 template <typename T>
 __device__ __forceinline__ void reg_stages(T (&v)[FCfg<T>::L], int bit0, int lo, int hi) {
   constexpr int L = FCfg<T>::L, LOGL = FCfg<T>::LOGL;
 #pragma unroll
   for (int h = 0; h < LOGL; ++h) {
     if (bit0 + h >= lo && bit0 + h < hi) {
+      if constexpr (sizeof(T) == 4) {
+        if (h > 0) {
+#pragma unroll
+          for (int q = 0; q < L; q += 2)
+            if (!(q & (1 << h))) bfly_x2(v[q], v[q + 1], v[q | (1 << h)], v[(q | (1 << h)) + 1]);
+          continue;
+        }
+      }
 #pragma unroll
       for (int q = 0; q < L; ++q)
         if (!(q & (1 << h))) {
@@ -671,7 +693,7 @@ __global__ void __launch_bounds__(256) k_fused_final(FTask ft) {
 // x <- H x * scale for vectors of n = 2^m with LOGT < m <= 2 LOGT - 5, in place, in two
 // tile passes: low LOGT bits on contiguous tiles, the high bits on column tiles.
 template <typename T>
-__global__ void __launch_bounds__(kFNT) k_wht_low(T *__restrict__ x, int m) {
+__global__ void __launch_bounds__(kFNT) k_wht_low(T *__restrict__ x) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
   extern __shared__ __align__(16) unsigned char smem[];
   T *sm = reinterpret_cast<T *>(smem);
@@ -685,15 +707,16 @@ __global__ void __launch_bounds__(kFNT) k_wht_low(T *__restrict__ x, int m) {
   for (int l = 0; l < L; ++l) xb[e_of<T>(2, t, l)] = v[l];
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kFNT) k_wht_high(T *__restrict__ x, int m, T scale) {
+template <typename T, int M>
+__global__ void __launch_bounds__(kFNT) k_wht_high(T *__restrict__ x, T scale) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
   extern __shared__ __align__(16) unsigned char smem[];
   T *sm = reinterpret_cast<T *>(smem);
-  const int c = 2 * LOGT - m, t = threadIdx.x;
-  const uint32_t tiles = 1u << (m - LOGT);
+  constexpr int c = 2 * LOGT - M;
+  const int t = threadIdx.x;
+  constexpr uint32_t tiles = 1u << (M - LOGT);
   const uint32_t tau = blockIdx.x & (tiles - 1);
-  T *xv = x + ((uint64_t)(blockIdx.x >> (m - LOGT)) << m);
+  T *xv = x + ((uint64_t)(blockIdx.x >> (M - LOGT)) << M);
   const uint32_t tcol = tau << c;
   auto widx = [&](uint32_t e) -> uint32_t { return ((e >> c) << LOGT) | tcol | (e & ((1u << c) - 1)); };
   T v[L];
@@ -702,6 +725,124 @@ __global__ void __launch_bounds__(kFNT) k_wht_high(T *__restrict__ x, int m, T s
   xwht_col<T>(v, sm, c, 0);
 #pragma unroll
   for (int l = 0; l < L; ++l) xv[widx(e_of<T>(2, t, l))] = v[l] * scale;
+}
+
+// ------------------------------------------- persistent batched WHT (one launch)
+// Both tile passes of every vector in a single launch of resident CTAs that take work
+// items in ticket order from a global counter.  Step s of the item sequence holds the
+// low-pass tiles of vector s followed by the column tiles of vector s - lag, so a
+// vector's second pass runs while its first-pass output (written in place) is still in
+// L2 and HBM sees each element read once and written once.  A column tile of vector v
+// waits until every low tile of v has been published; those tiles hold smaller tickets,
+// were claimed by CTAs that are running, and wait on nothing, so the wait ends.  The
+// wait is bounded all the same: past the limit the item is skipped and
+// QK_STATUS_TIMEOUT is raised.
+struct WhtSched {
+  uint32_t nvec, lt, lag;  // lt = log2(tiles per vector); 1 <= lag <= nvec
+  __host__ __device__ uint32_t total() const { return (2u * nvec) << lt; }
+  __device__ void decode(uint32_t i, uint32_t &v, uint32_t &tile, bool &high) const {
+    const uint32_t T = 1u << lt, pre = lag << lt, mid = ((nvec - lag) << lt) * 2u;
+    if (i < pre) {
+      v = i >> lt, tile = i & (T - 1), high = false;
+    } else if (i - pre < mid) {
+      const uint32_t j = i - pre, s = j >> (lt + 1), k = j & (2 * T - 1);
+      high = k >= T;
+      v = high ? s : lag + s;
+      tile = k & (T - 1);
+    } else {
+      const uint32_t j = i - pre - mid;
+      v = (nvec - lag) + (j >> lt), tile = j & (T - 1), high = true;
+    }
+  }
+};
+
+__device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <typename T, int M>
+__global__ void __launch_bounds__(kFNT, 4) k_wht_persist(T *__restrict__ x, T scale, WhtSched sc,
+                                                         uint32_t *__restrict__ ctr, uint32_t *status,
+                                                         uint32_t spin_limit, uint32_t first_item) {
+  constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L, m = M, c = 2 * LOGT - M;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_item, s_ok;
+  T *sm = reinterpret_cast<T *>(smem);
+  uint32_t *ticket = ctr, *done = ctr + 1;
+  const int t = threadIdx.x;
+  const uint32_t total = sc.total(), T_ = 1u << sc.lt;
+  for (;;) {
+    if (t == 0) s_item = first_item + atomicAdd(ticket, 1u);
+    __syncthreads();
+    const uint32_t it = s_item;
+    if (it >= total) break;
+    uint32_t v, tile;
+    bool high;
+    sc.decode(it, v, tile, high);
+    T *xv = x + ((uint64_t)v << m);
+    T r[L];
+    if (!high) {
+      T *xb = xv + ((uint64_t)tile << LOGT);
+#pragma unroll
+      for (int l = 0; l < L; ++l) r[l] = xb[e_of<T>(0, t, l)];
+      xwht_full<T>(r, sm, 0);
+#pragma unroll
+      for (int l = 0; l < L; ++l) xb[e_of<T>(2, t, l)] = r[l];
+      __syncthreads();  // every thread's stores precede thread 0's release below
+      if (t == 0) red_release_add_u32(&done[v], 1u);
+    } else {
+      if (t == 0) {
+        uint32_t k = 0, ok = 1;
+        while (ld_acquire_u32(&done[v]) < T_) {
+          if (++k > spin_limit) {
+            ok = 0;
+            if (status) atomicOr(status, (uint32_t)QK_STATUS_TIMEOUT);
+            break;
+          }
+          __nanosleep(128);
+        }
+        s_ok = ok;
+      }
+      __syncthreads();
+      if (s_ok) {
+        const uint32_t tcol = tile << c;
+        auto widx = [&](uint32_t e) -> uint32_t { return ((e >> c) << LOGT) | tcol | (e & ((1u << c) - 1)); };
+#pragma unroll
+        for (int l = 0; l < L; ++l) r[l] = __ldcg(&xv[widx(e_of<T>(0, t, l))]);  // L2, never a stale L1 line
+        xwht_col<T>(r, sm, c, 0);
+#pragma unroll
+        for (int l = 0; l < L; ++l) xv[widx(e_of<T>(2, t, l))] = r[l] * scale;
+      }
+    }
+    __syncthreads();  // s_item and s_ok are rewritten next round
+  }
+}
+
+size_t persist_wht_ws_bytes(uint64_t nvec) { return align256(sizeof(uint32_t) * (1 + nvec)); }
+
+// Every m of the two-pass range gets its own instantiation: with the tile split known at
+// compile time, column-tile addressing folds into immediate offsets and the butterfly
+// stage selection into straight-line code.
+template <typename T> struct WhtKernels {
+  void (*low)(T *);  // the same for every m
+  void (*high)(T *, T);
+  void (*persist)(T *, T, WhtSched, uint32_t *, uint32_t *, uint32_t, uint32_t);
+};
+template <typename T, int M>
+static WhtKernels<T> wht_kernels_m() {
+  return WhtKernels<T>{k_wht_low<T>, k_wht_high<T, M>, k_wht_persist<T, M>};
+}
+template <typename T, int... I>
+static WhtKernels<T> wht_pick(int m, std::integer_sequence<int, I...>) {
+  constexpr int LO = FCfg<T>::LOGT + 1;
+  WhtKernels<T> out{nullptr, nullptr, nullptr};
+  ((m == LO + I ? (void)(out = wht_kernels_m<T, LO + I>()) : (void)0), ...);
+  return out;
+}
+template <typename T>
+static WhtKernels<T> wht_kernels(int m) {
+  constexpr int LOGT = FCfg<T>::LOGT;
+  return wht_pick<T>(m, std::make_integer_sequence<int, (2 * LOGT - 5) - LOGT>());
 }
 
 bool tiled_wht_supported(uint32_t m, int dtype) {
@@ -720,13 +861,14 @@ static int tiled_wht_t(T *x, uint32_t m, uint64_t nvec, double scale, cudaStream
   const uint64_t n = 1ull << m;
   uint64_t chunk = chunk_bytes / (n * sizeof(T));
   if (chunk < 1) chunk = 1;
+  const WhtKernels<T> K = wht_kernels<T>(m);
   for (uint64_t v0 = 0; v0 < nvec; v0 += chunk) {
     const uint64_t nv = (nvec - v0) < chunk ? (nvec - v0) : chunk;
     const uint64_t blocks = nv << (m - LOGT);
-    k_wht_low<T><<<(unsigned)blocks, kFNT, sm, st>>>(x + v0 * n, (int)m);
+    K.low<<<(unsigned)blocks, kFNT, sm, st>>>(x + v0 * n);
     int rc = check_launch("wht low");
     if (rc) return rc;
-    k_wht_high<T><<<(unsigned)blocks, kFNT, sm, st>>>(x + v0 * n, (int)m, (T)scale);
+    K.high<<<(unsigned)blocks, kFNT, sm, st>>>(x + v0 * n, (T)scale);
     if ((rc = check_launch("wht high"))) return rc;
   }
   return QK_OK;
@@ -735,6 +877,79 @@ static int tiled_wht_t(T *x, uint32_t m, uint64_t nvec, double scale, cudaStream
 int tiled_wht(void *x, uint32_t m, uint64_t nvec, int dtype, double scale, cudaStream_t st, size_t chunk_bytes) {
   return dtype == QK_F64 ? tiled_wht_t<double>((double *)x, m, nvec, scale, st, chunk_bytes)
                          : tiled_wht_t<float>((float *)x, m, nvec, scale, st, chunk_bytes);
+}
+
+template <typename T>
+static int persist_occupancy() {
+  static int occ = -1;
+  if (occ < 0) {
+    // every instantiation has the same launch bounds and shared memory; query one
+    constexpr int M = 2 * FCfg<T>::LOGT - 6;
+    const size_t sm = xtile_bytes<T>();
+    smem_optin<k_wht_persist<T, M>>(sm);
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_wht_persist<T, M>, kFNT, sm) != cudaSuccess) return -1;
+    occ = o;
+  }
+  return occ;
+}
+
+int persist_wht_max_ctas_per_sm(int dtype) {
+  return dtype == QK_F64 ? persist_occupancy<double>() : persist_occupancy<float>();
+}
+
+// Lag (in vectors) after which a vector's column tiles are queued: enough tickets between
+// a vector's last low tile and its first column tile that the low tile has finished when
+// the column tile is taken ((2 lag - 1) tiles >= resident CTAs), and at most 48 MB of
+// first-pass output waiting in L2.
+uint32_t persist_wht_default_lag(uint32_t m, uint64_t nvec, int dtype, uint32_t ctas) {
+  const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
+  const uint64_t T = 1ull << (m - LOGT), bytes = (dtype == QK_F64 ? 8ull : 4ull) << m;
+  uint64_t lag = (ctas / T + 2) / 2 + 1;
+  const uint64_t cap = (48ull << 20) / bytes;
+  if (lag > cap) lag = cap;
+  if (lag < 1) lag = 1;
+  if (lag > nvec) lag = nvec;
+  return (uint32_t)lag;
+}
+
+template <typename T>
+static int persist_wht_t(T *x, uint32_t m, uint64_t nvec, double scale, uint32_t *ctr, uint32_t *status,
+                         cudaStream_t st, uint32_t lag, uint32_t ctas_per_sm, uint32_t spin_limit,
+                         bool columns_only) {
+  constexpr int LOGT = FCfg<T>::LOGT;
+  const int occ = persist_occupancy<T>();
+  if (occ <= 0) return fail(QK_ECUDA, "persistent WHT: occupancy query failed");
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t cps = ctas_per_sm == 0 || (int)ctas_per_sm > occ ? (uint32_t)occ : ctas_per_sm;
+  const uint64_t items = (2ull * nvec) << (m - LOGT);
+  if (items >= (1ull << 31)) return fail(QK_EINVAL, "persistent WHT: %llu work items exceed 2^31",
+                                         (unsigned long long)items);
+  const uint32_t grid = (uint32_t)sms * cps;
+  if (lag == 0) lag = persist_wht_default_lag(m, nvec, sizeof(T) == 8 ? QK_F64 : QK_F32, grid);
+  if (lag > nvec) lag = (uint32_t)nvec;
+  WhtSched sc{(uint32_t)nvec, (uint32_t)(m - LOGT), lag};
+  cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * (1 + nvec), st);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent WHT: counter reset");
+  // columns_only starts the tickets at the first column tile with every vector's low
+  // tiles left unpublished: each column tile's wait must then run out (a test of the
+  // bounded wait; the data are left untouched).
+  if (columns_only) sc.lag = (uint32_t)nvec;
+  const uint32_t first = columns_only ? (uint32_t)(nvec << (m - LOGT)) : 0u;
+  wht_kernels<T>((int)m).persist<<<grid, kFNT, xtile_bytes<T>(), st>>>(x, (T)scale, sc, ctr, status, spin_limit,
+                                                                        first);
+  return check_launch("wht persistent");
+}
+
+int persist_wht(void *x, uint32_t m, uint64_t nvec, int dtype, double scale, void *ws, uint32_t *status,
+                cudaStream_t st, uint32_t lag, uint32_t ctas_per_sm, uint32_t spin_limit, bool columns_only) {
+  if (nvec == 0) return QK_OK;
+  return dtype == QK_F64 ? persist_wht_t<double>((double *)x, m, nvec, scale, (uint32_t *)ws, status, st, lag,
+                                                 ctas_per_sm, spin_limit, columns_only)
+                         : persist_wht_t<float>((float *)x, m, nvec, scale, (uint32_t *)ws, status, st, lag,
+                                                ctas_per_sm, spin_limit, columns_only);
 }
 
 // ------------------------------------------------------------------ host side

@@ -46,6 +46,14 @@ bool fused_supported(const qk_task &t, int dtype);
 bool tiled_wht_supported(uint32_t m, int dtype);
 int tiled_wht(void *x, uint32_t m, uint64_t nvec, int dtype, double scale, cudaStream_t st,
               size_t chunk_bytes = ~(size_t)0);
+// Persistent single-launch batched WHT (qk_fused.cu) and its tuner (qk_tune.cu).
+constexpr uint32_t kSpinLimit = 1u << 23;  // ~1 s of 128 ns sleeps
+size_t persist_wht_ws_bytes(uint64_t nvec);
+int persist_wht_max_ctas_per_sm(int dtype);
+uint32_t persist_wht_default_lag(uint32_t m, uint64_t nvec, int dtype, uint32_t ctas);
+int persist_wht(void *x, uint32_t m, uint64_t nvec, int dtype, double scale, void *ws, uint32_t *status,
+                cudaStream_t st, uint32_t lag, uint32_t ctas_per_sm, uint32_t spin_limit = kSpinLimit,
+                bool columns_only = false);
 size_t fused_ws_bytes(const qk_task &t, int dtype, int refine);
 int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *ws, uint32_t *status,
               cudaStream_t st, LaunchTimer *tm = nullptr);

@@ -24,13 +24,15 @@ QK_NATURAL, QK_GRAY = 0, 1
 QK_DSI, QK_SI = 0, 1
 QK_F64, QK_F32 = 0, 1
 QK_COL_K1, QK_COL_P = 0, 1
-QK_MLL_NOUT = 5
-OP_EIGS, OP_SOLVE, OP_MATVEC, OP_MLL = 0, 1, 2, 3
+QK_MLL_QUAD, QK_MLL_LOGDET, QK_MLL_MLL, QK_MLL_MEAN, QK_MLL_VAR, QK_MLL_NOUT = range(6)
+OP_EIGS, OP_SOLVE, OP_MATVEC, OP_MLL, OP_FWHT = 0, 1, 2, 3, 4
+QK_FWHT_TWO_PASS, QK_FWHT_PERSISTENT = 0, 1
 
 EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_solve", "qk_matvec", "qk_mll",
             "qk_batch_workspace_bytes", "qk_batch_plan", "qk_batch_run", "qk_workspace_bytes",
             "qk_read_status", "qk_last_error", "qk_version", "qk_fwht", "qk_fftbr", "qk_ifftbr",
-            "qk_launch_count", "qk_eigs_static", "qk_batch_timing", "qk_batch_kernel_ms"]
+            "qk_launch_count", "qk_eigs_static", "qk_batch_timing", "qk_batch_kernel_ms", "qk_fwht_ws",
+            "qk_fwht_tune", "qk_fwht_wait_selftest"]
 
 
 class QKError(RuntimeError):
@@ -47,6 +49,10 @@ class PointSet(C.Structure):
 class Kernel(C.Structure):
     _fields_ = [("family", C.c_int32), ("alpha", C.c_int32), ("d", C.c_uint32), ("weights", C.c_void_p),
                 ("zeta", C.c_double)]
+
+
+class FwhtPlan(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("lag", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("ms", C.c_float)]
 
 
 class Task(C.Structure):
@@ -82,6 +88,9 @@ def _load():
         "qk_eigs_static": [i32, u32, u32, i32, i32, P, dbl, dbl, P, P, P],
         "qk_batch_timing": [P, u32],
         "qk_batch_kernel_ms": [P, u32, C.c_char_p, sz, C.POINTER(u32), C.POINTER(dbl)],
+        "qk_fwht_ws": [u32, u64, i32, P, P, sz, C.POINTER(FwhtPlan), P, P],
+        "qk_fwht_tune": [u32, u64, i32, P, P, sz, C.POINTER(FwhtPlan), P],
+        "qk_fwht_wait_selftest": [u32, u64, i32, P, P, sz, u32, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -247,6 +256,44 @@ def fftbr(m: int, x, stream=None):
 def ifftbr(m: int, x, stream=None):
     _check(LIB.qk_ifftbr(m, _nvec_m(x, m, True), dtype_code(x.dtype), _ptr(x), _stream(stream)))
     return x
+
+
+def fwht_workspace(nvec: int, device="cuda"):
+    return workspace(workspace_bytes(OP_FWHT, QK_DSI, 0, nvec, 1, torch.float32), device)
+
+
+def fwht_ws(m: int, x, ws=None, plan=None, status=None, stream=None):
+    """qk_fwht with a workspace: the tuned (or the given) two-pass or persistent single-launch
+    form; plan = dict(mode=QK_FWHT_*, lag=.., ctas_per_sm=..) pins one."""
+    nvec = _nvec_m(x, m, False)
+    if ws is None:
+        ws = fwht_workspace(nvec, x.device)
+    pp = None
+    if plan is not None:
+        pp = C.byref(FwhtPlan(plan["mode"], plan.get("lag", 0), plan.get("ctas_per_sm", 0), 0.0))
+    _check(LIB.qk_fwht_ws(m, nvec, dtype_code(x.dtype), _ptr(x), _ptr(ws), ws.numel(), pp, _ptr(status),
+                          _stream(stream)))
+    return x
+
+
+def fwht_tune(m: int, x, ws=None, stream=None) -> dict:
+    """Autotune qk_fwht_ws for x's shape (x is overwritten); returns the chosen plan."""
+    nvec = _nvec_m(x, m, False)
+    if ws is None:
+        ws = fwht_workspace(nvec, x.device)
+    plan = FwhtPlan()
+    _check(LIB.qk_fwht_tune(m, nvec, dtype_code(x.dtype), _ptr(x), _ptr(ws), ws.numel(), C.byref(plan),
+                            _stream(stream)))
+    return {"mode": "persistent" if plan.mode == QK_FWHT_PERSISTENT else "two_pass", "lag": plan.lag,
+            "ctas_per_sm": plan.ctas_per_sm, "ms": plan.ms}
+
+
+def fwht_wait_selftest(m: int, x, spin_limit: int, status, ws=None, stream=None):
+    nvec = _nvec_m(x, m, False)
+    if ws is None:
+        ws = fwht_workspace(nvec, x.device)
+    _check(LIB.qk_fwht_wait_selftest(m, nvec, dtype_code(x.dtype), _ptr(x), _ptr(ws), ws.numel(), spin_limit,
+                                     _ptr(status), _stream(stream)))
 
 
 # ------------------------------------------------------------------ batching
