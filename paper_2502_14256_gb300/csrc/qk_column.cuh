@@ -79,51 +79,74 @@ __device__ __forceinline__ void carve_tables(unsigned char *smem, uint32_t d, do
   tb.gs = u;
 }
 
-// Fill the DSI coefficient rows (computed in FP64, stored as T).
+// DSI coefficient rows.  They depend only on beta and the order (the weights enter
+// later, as c_j K), so they are computed once, at compile time, in double precision
+// (the Theorem's beta-dependent coefficients, stored as T); every CTA copies them into
+// shared memory.  Rows of order 3 and 4 carry the rounding residuals of their constant
+// (and, for order 4, linear) coefficients, so that FP32 rows add no per-row bias.
+constexpr int kDsiTabLen = kTabRows * kTabNC + kOctRows;
+template <typename T> struct DsiTable { T v[kDsiTabLen]; };
+
+__host__ __device__ constexpr double pow2neg(int e) {
+  double r = 1.0;
+  for (int i = 0; i < e; ++i) r *= 0.5;
+  return r;
+}
+
 template <typename T, int ALPHA>
-__device__ void build_dsi_tab(T *tab) {
-  for (int q = threadIdx.x; q < kTabRows + kOctRows; q += kColNT) {
-    if (q < kTabRows) {
-      const int beta = q < 32 ? q + 1 : 0;
-      const double t1 = q < 32 ? exp2neg(0.0, beta) : 0.0, t2 = t1 * t1, t3 = t2 * t1;
-      const double b = (double)beta;
-      double A = 0, B = 0, C = 0, D = 0, E = 0;
-      if (ALPHA == 1) {
-        A = q < 32 ? 1.0 - 3.0 * t1 : 1.0;
-      } else if (ALPHA == 2) {
-        A = 1.5 - 2.5 * t1;
-        B = -b * 0x1p-32;
-      } else if (ALPHA == 3) {
-        A = -1.0 + (43.0 / 18.0) * (1.0 - t2);
-        B = -5.0 * (1.0 - t1) * 0x1p-32;
-        C = b * 0x1p-64;
-      } else {
-        A = -1.0 + (701.0 / 294.0) * (1.0 - t3);
-        B = -(43.0 / 9.0) * (1.0 - t2) * 0x1p-32;
-        C = 5.0 * (1.0 - t1) * 0x1p-64;
-        D = -(2.0 / 3.0) * b * 0x1p-96;
-        E = -b / 24.0;
-      }
-      // Rows of order 3 and 4 carry the rounding residuals of their constant (and, for
-      // order 4, linear) coefficients, so that FP32 rows add no per-row bias.
-      constexpr int S = tab_stride(ALPHA);
-      T *row = tab + q * S;
-      const double co[5] = {A, B, C, D, E};
-      for (int k = 0; k < S && k < 5; ++k) row[k] = (T)co[k];
-      for (int k = 5; k < S; ++k) row[k] = T(0);
-      if (ALPHA == 3) row[3] = (T)(A - (double)(T)A);
-      if (ALPHA == 4) {
-        row[5] = (T)(A - (double)(T)A);
-        row[6] = (T)(B - (double)(T)B);
-      }
+__host__ __device__ constexpr DsiTable<T> make_dsi_table() {
+  DsiTable<T> tab{};
+  constexpr int S = tab_stride(ALPHA);
+  for (int q = 0; q < kTabRows; ++q) {
+    const int beta = q < 32 ? q + 1 : 0;
+    const double t1 = q < 32 ? pow2neg(beta) : 0.0, t2 = t1 * t1, t3 = t2 * t1;
+    const double b = (double)beta;
+    double A = 0, B = 0, C = 0, D = 0, E = 0;
+    if (ALPHA == 1) {
+      A = q < 32 ? 1.0 - 3.0 * t1 : 1.0;
+    } else if (ALPHA == 2) {
+      A = 1.5 - 2.5 * t1;
+      B = -b * pow2neg(32);
+    } else if (ALPHA == 3) {
+      A = -1.0 + (43.0 / 18.0) * (1.0 - t2);
+      B = -5.0 * (1.0 - t1) * pow2neg(32);
+      C = b * pow2neg(64);
     } else {
-      const int byte = q - kTabRows;  // S' of the 8 digits of one byte (a = 0..7)
-      double s = 0.0;
-      for (int a = 0; a < 8; ++a)
-        if ((byte >> (7 - a)) & 1) s += exp2neg(0.0, 3 * a);
-      tab[kTabRows * kTabNC + byte] = (T)s;
+      A = -1.0 + (701.0 / 294.0) * (1.0 - t3);
+      B = -(43.0 / 9.0) * (1.0 - t2) * pow2neg(32);
+      C = 5.0 * (1.0 - t1) * pow2neg(64);
+      D = -(2.0 / 3.0) * b * pow2neg(96);
+      E = -b / 24.0;
+    }
+    const double co[5] = {A, B, C, D, E};
+    for (int k = 0; k < S && k < 5; ++k) tab.v[q * S + k] = (T)co[k];
+    if (ALPHA == 3) tab.v[q * S + 3] = (T)(A - (double)(T)A);
+    if (ALPHA == 4) {
+      tab.v[q * S + 5] = (T)(A - (double)(T)A);
+      tab.v[q * S + 6] = (T)(B - (double)(T)B);
     }
   }
+  for (int byte = 0; byte < kOctRows; ++byte) {  // S' of the 8 digits of one byte (a = 0..7)
+    double sum = 0.0;
+    for (int a = 0; a < 8; ++a)
+      if ((byte >> (7 - a)) & 1) sum += pow2neg(3 * a);
+    tab.v[kTabRows * kTabNC + byte] = (T)sum;
+  }
+  return tab;
+}
+
+static __device__ const DsiTable<float> g_dsi_f[4] = {make_dsi_table<float, 1>(), make_dsi_table<float, 2>(),
+                                                      make_dsi_table<float, 3>(), make_dsi_table<float, 4>()};
+static __device__ const DsiTable<double> g_dsi_d[4] = {make_dsi_table<double, 1>(), make_dsi_table<double, 2>(),
+                                                       make_dsi_table<double, 3>(), make_dsi_table<double, 4>()};
+
+// Copy the DSI coefficient rows of this order into shared memory.
+template <typename T, int ALPHA>
+__device__ void build_dsi_tab(T *tab) {
+  const T *src;
+  if constexpr (sizeof(T) == 4) src = g_dsi_f[ALPHA - 1].v;
+  else src = g_dsi_d[ALPHA - 1].v;
+  for (int q = threadIdx.x; q < kDsiTabLen; q += kColNT) tab[q] = src[q];
 }
 
 __device__ __forceinline__ float word_to(float, uint32_t Z) { return __uint2float_rn(Z); }
@@ -264,8 +287,9 @@ __device__ T dk_explicit(const ColJob &job, const DiffTables &tb, const T *wT, u
 __device__ __forceinline__ float ratio(float a, float b) { return __fdividef(a, b); }  // 2 ulp
 __device__ __forceinline__ double ratio(double a, double b) { return a / b; }
 
-// Gradient sweep: for each dimension j, warp-reduced FP64 sums over this warp's
-// points of u_i dk1_i/dc_j and dk1_i/dc_j, written to red[warp][2d], with
+// Gradient sweep: for each dimension j, warp-reduced sums over this warp's points of
+// u_i dk1_i/dc_j and dk1_i/dc_j (float-float pairs in FP32 sweeps, doubles in FP64
+// sweeps), written to red[warp][2d] and totalled by red_total, with
 // dk1_i/dc_j = k1_i K_ij / (1 + c_j K_ij).  wk[l] = u_l k1_l; uget(l) returns u_l and
 // is called only for the rare exact zero of 1 + c_j K_ij, handled after the loop by
 // the explicit product over the other dimensions.
@@ -306,16 +330,48 @@ __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTabl
         s1 += dk;
       }
     }
-    double du = (double)su, d1 = (double)s1;
+    if constexpr (sizeof(T) == 4) {
+      // float-float warp sums, kept as (hi, lo) pairs: no FP64 arithmetic per dimension
+      float ue = 0.f, oe = 0.f;
+      warp_sum_ff(su, ue);
+      warp_sum_ff(s1, oe);
+      if (lane == 0) {
+        float2 *r2 = reinterpret_cast<float2 *>(red);
+        r2[(size_t)warp * 2 * d + j] = make_float2(su, ue);
+        r2[(size_t)warp * 2 * d + d + j] = make_float2(s1, oe);
+      }
+    } else {
+      double du = su, d1 = s1;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      du += __shfl_xor_sync(0xffffffffu, du, o);
-      d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+      for (int o = 16; o > 0; o >>= 1) {
+        du += __shfl_xor_sync(0xffffffffu, du, o);
+        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+      }
+      if (lane == 0) {
+        red[(size_t)warp * 2 * d + j] = du;
+        red[(size_t)warp * 2 * d + d + j] = d1;
+      }
     }
-    if (lane == 0) {
-      red[(size_t)warp * 2 * d + j] = du;
-      red[(size_t)warp * 2 * d + d + j] = d1;
+  }
+}
+
+// Entry q of the per-warp gradient partials red[warp][nq] summed over the warps: FP32
+// sweeps leave float-float pairs (summed in float-float, converted once), FP64 sweeps
+// doubles.
+template <typename T>
+__device__ __forceinline__ double red_total(const double *red, int warps, uint32_t nq, uint32_t q) {
+  if constexpr (sizeof(T) == 4) {
+    const float2 *r2 = reinterpret_cast<const float2 *>(red);
+    float s = 0.f, e = 0.f;
+    for (int w = 0; w < warps; ++w) {
+      const float2 p = r2[(size_t)w * nq + q];
+      ff_merge(s, e, p.x, p.y);
     }
+    return (double)s + (double)e;
+  } else {
+    double s = 0.0;
+    for (int w = 0; w < warps; ++w) s += red[(size_t)w * nq + q];
+    return s;
   }
 }
 

@@ -77,6 +77,65 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
   return s;
 }
 
+// Error-free sum: s + e == a + b exactly (Knuth's TwoSum; no ordering of |a|, |b| needed).
+template <typename T>
+__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
+  s = a + b;
+  const T bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Float-float ("compensated") sums.  On GB300 an FP64 add costs about 40 FP32 adds, so
+// FP32 reductions keep their partial sums as unevaluated pairs s + e (about 48 bits)
+// and convert to FP64 once, at the end.
+__device__ __forceinline__ void ff_merge(float &s, float &e, float s2, float e2) {
+  float t, r;
+  two_sum(s, s2, t, r);
+  s = t;
+  e = e + (e2 + r);
+}
+// Warp-wide sum of the pairs (s, e); every lane ends with the total.
+__device__ __forceinline__ void warp_sum_ff(float &s, float &e) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), e2 = __shfl_xor_sync(0xffffffffu, e, o);
+    ff_merge(s, e, s2, e2);
+  }
+}
+// CTA sum of thread partials: FP32 pairs (s, e) summed in float-float, FP64 partials in
+// FP64.  The result is valid in thread 0.  sh: 32 doubles of shared scratch.  All
+// threads must call it.
+__device__ __forceinline__ double block_sum_c(float s, float e, double *sh) {
+  float *f = reinterpret_cast<float *>(sh);
+  warp_sum_ff(s, e);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  __syncthreads();
+  if (lane == 0) {
+    f[2 * w] = s;
+    f[2 * w + 1] = e;
+  }
+  __syncthreads();
+  double out = 0.0;
+  if (w == 0) {
+    float a = lane < nw ? f[2 * lane] : 0.f, b = lane < nw ? f[2 * lane + 1] : 0.f;
+    warp_sum_ff(a, b);
+    if (lane == 0) out = (double)a + (double)b;
+  }
+  return out;
+}
+__device__ __forceinline__ double block_sum_c(double s, double e, double *sh) { return block_sum(s + e, sh); }
+
+// Exact float -> double by integer operations for normal values (the FP64 conversion
+// unit is as slow as the FP64 adder on GB300); zero, subnormal, inf and NaN inputs take
+// the hardware conversion.
+__device__ __forceinline__ double f2d_exact(float v) {
+  const uint32_t u = __float_as_uint(v), ex = (u >> 23) & 0xFFu;
+  if (ex == 0u || ex == 0xFFu) return (double)v;
+  const uint32_t hi = (u & 0x80000000u) | ((ex + 896u) << 20) | ((u & 0x7FFFFFu) >> 3);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ double f2d_exact(double v) { return v; }
+
 // ---------------------------------------------- bulk asynchronous copies (TMA)
 // One-dimensional cp.async.bulk global -> shared copies completing on an mbarrier
 // (transaction bytes).  Addresses 16-byte aligned, sizes multiples of 16 bytes.

@@ -125,14 +125,6 @@ __device__ __forceinline__ void kahan_add(T &s, T &c, T v) {
   s = t;
 }
 
-// Error-free sum: s + e == a + b exactly (Knuth's TwoSum; no ordering of |a|, |b| needed).
-template <typename T>
-__device__ __forceinline__ void two_sum(T a, T b, T &s, T &e) {
-  s = a + b;
-  const T bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-
 // Compensated butterfly on (hi, lo) pairs: the rounding error of each hi sum is added
 // to the lo parts, so hi + lo carries the transform to about twice the precision of T.
 template <typename T>
@@ -431,7 +423,7 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
     P[t + (l << kLOGNT)] = p[l];
     kahan_add(ps, pc, p[l]);
   }
-  const double sps = block_sum((double)ps - (double)pc, red);
+  const double sps = block_sum_c(ps, -pc, red);
   if (t == 0) ft.sp[(uint64_t)r * ft.tiles + tile] = sps;
   xwht_full<T>(p, sm, 0);  // L0 -> L2
   T *PT = reinterpret_cast<T *>(ft.pT) + (uint64_t)r * n + base;
@@ -447,7 +439,7 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
       yv[l] = Y[t + (l << kLOGNT)];
       kahan_add(ys, yc, yv[l]);
     }
-    const double sys = block_sum((double)ys - (double)yc, red);
+    const double sys = block_sum_c(ys, -yc, red);
     if (t == 0) ft.sy[v * ft.tiles + tile] = sys;
     T *YT = reinterpret_cast<T *>(ft.yT) + v * n + base;
     if constexpr (COMP) {
@@ -510,12 +502,12 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
     }
     bad |= !(v > T(0));
     lds += fused_log(v);
-    if (LAM) LAM[wi2(l)] = (double)v;
+    if (LAM) LAM[wi2(l)] = f2d_exact(v);
     lmv[t + (l << kLOGNT)] = v;  // each thread reads back only its own entries
   }
   if (bad && ft.status) atomicOr(ft.status, (uint32_t)QK_STATUS_NOTPD);
   if (floored && ft.status) atomicOr(ft.status, (uint32_t)QK_STATUS_FLOOR);
-  const double ldsum = block_sum((double)lds, red);
+  const double ldsum = block_sum_c(lds, T(0), red);
   if (t == 0) ft.ld[(uint64_t)r * ft.tiles + tau] = ldsum;
   const T inv_n = T(1) / (T)n;
   for (uint32_t q = 0; q < ft.nrhs; ++q) {
@@ -566,8 +558,8 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
     xwht_col<T>(y, sm, c, 1);
 #pragma unroll
     for (int l = 0; l < L; ++l) GT[wi0(l)] = y[l];
-    const double sq = block_sum((double)quad, red);
-    const double sg = block_sum((double)gs, red);
+    const double sq = block_sum_c(quad, T(0), red);
+    const double sg = block_sum_c(gs, T(0), red);
     if (t == 0) {
       ft.qg[(v * ft.tiles + tau) * 2 + 0] = sq;
       ft.qg[(v * ft.tiles + tau) * 2 + 1] = sg;
@@ -628,12 +620,7 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
                                    [&](int l) { return sm[t + (l << kLOGNT)]; }, red);
   __syncthreads();
   double *dst = ft.gr + ((uint64_t)v * ft.tiles + tile) * 2 * d;
-  for (uint32_t q = t; q < 2 * d; q += kFNT) {
-    double s = 0.0;
-#pragma unroll
-    for (int wp = 0; wp < kFNT / 32; ++wp) s += red[(size_t)wp * 2 * d + q];
-    dst[q] = s;
-  }
+  for (uint32_t q = t; q < 2 * d; q += kFNT) dst[q] = red_total<T>(red, kFNT / 32, 2 * d, q);
 }
 
 // ------------------------------------------------------------------ final
@@ -766,16 +753,21 @@ __global__ void __launch_bounds__(kFNT, 4) k_wht_persist(T *__restrict__ x, T sc
                                                          uint32_t spin_limit, uint32_t first_item) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L, m = M, c = 2 * LOGT - M;
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ uint32_t s_item, s_ok;
+  // s_item[k & 1] and s_ok[k & 1] belong to this CTA's item k: thread 0 claims item
+  // k + 1 while item k is processed.  Every path through an item passes a barrier after
+  // its slots are read, so a slot is rewritten (two items on) only after all threads
+  // have read it, and the loop needs no barrier of its own.
+  __shared__ uint32_t s_item[2], s_ok[2];
   T *sm = reinterpret_cast<T *>(smem);
   uint32_t *ticket = ctr, *done = ctr + 1;
   const int t = threadIdx.x;
   const uint32_t total = sc.total(), T_ = 1u << sc.lt;
-  for (;;) {
-    if (t == 0) s_item = first_item + atomicAdd(ticket, 1u);
-    __syncthreads();
-    const uint32_t it = s_item;
+  if (t == 0) s_item[0] = first_item + atomicAdd(ticket, 1u);
+  __syncthreads();
+  for (int k = 0;; ++k) {
+    const uint32_t it = s_item[k & 1];
     if (it >= total) break;
+    if (t == 0) s_item[(k + 1) & 1] = first_item + atomicAdd(ticket, 1u);
     uint32_t v, tile;
     bool high;
     sc.decode(it, v, tile, high);
@@ -792,19 +784,19 @@ __global__ void __launch_bounds__(kFNT, 4) k_wht_persist(T *__restrict__ x, T sc
       if (t == 0) red_release_add_u32(&done[v], 1u);
     } else {
       if (t == 0) {
-        uint32_t k = 0, ok = 1;
+        uint32_t tries = 0, ok = 1;
         while (ld_acquire_u32(&done[v]) < T_) {
-          if (++k > spin_limit) {
+          if (++tries > spin_limit) {
             ok = 0;
             if (status) atomicOr(status, (uint32_t)QK_STATUS_TIMEOUT);
             break;
           }
           __nanosleep(128);
         }
-        s_ok = ok;
+        s_ok[k & 1] = ok;
       }
       __syncthreads();
-      if (s_ok) {
+      if (s_ok[k & 1]) {
         const uint32_t tcol = tile << c;
         auto widx = [&](uint32_t e) -> uint32_t { return ((e >> c) << LOGT) | tcol | (e & ((1u << c) - 1)); };
 #pragma unroll
@@ -814,7 +806,6 @@ __global__ void __launch_bounds__(kFNT, 4) k_wht_persist(T *__restrict__ x, T sc
         for (int l = 0; l < L; ++l) xv[widx(e_of<T>(2, t, l))] = r[l] * scale;
       }
     }
-    __syncthreads();  // s_item and s_ok are rewritten next round
   }
 }
 

@@ -204,12 +204,7 @@ __global__ void __launch_bounds__(kNT) k_grad_partials(ColJob job, uint32_t nrhs
   gradient_sweep<T, FAM, ALPHA, kL>(job, tb, wT, bi, k1, wk, ok, [&](int l) { return uu[l]; }, red);
   __syncthreads();
   double *dst = partial + ((size_t)v * gridDim.x + blockIdx.x) * 2 * d;
-  for (uint32_t q = threadIdx.x; q < 2 * d; q += kNT) {
-    double s = 0.0;
-#pragma unroll
-    for (int w = 0; w < kNT / 32; ++w) s += red[(size_t)w * 2 * d + q];
-    dst[q] = s;
-  }
+  for (uint32_t q = threadIdx.x; q < 2 * d; q += kNT) dst[q] = red_total<T>(red, kNT / 32, 2 * d, q);
 }
 
 uint32_t grad_blocks(uint32_t m) { return ceil_div_u(1ull << m, kTile); }
