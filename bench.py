@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--refine", type=int, default=1, help="refinement steps of the FP32 solve")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--e2e-chunk", type=int, default=8, help="randomizations per host-copy chunk (e2e)")
     return ap.parse_args()
 
 
@@ -269,12 +270,12 @@ def main():
     o_host = torch.empty_like(P32.out, device="cpu").pin_memory()
     g_host = torch.empty_like(P32.grad, device="cpu").pin_memory()
 
+    host_io = [dict(y=y_host, c=c_host, out=o_host, grad=g_host)]
+
     def e2e_step():
-        P32.y.copy_(y_host, non_blocking=True)
-        P32.step()
-        c_host.copy_(P32.c, non_blocking=True)
-        o_host.copy_(P32.out, non_blocking=True)
-        g_host.copy_(P32.grad, non_blocking=True)
+        # the library's host path: chunks of randomizations copied in, computed and copied
+        # back on overlapping streams
+        qk.batch_run_host(P32.ws, host_io, args.e2e_chunk, P32.status, stream=stream)
 
     e2e_ms = time_steps(torch, e2e_step, max(2, args.steps // 2), 1, stream)
     if world > 1:

@@ -289,6 +289,25 @@ QK_API int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream s
  * events and returns, for the idx-th distinct kernel name, its launch count and
  * summed device milliseconds; QK_EINVAL once idx runs past the last name.
  * qk_batch_timing(ws, 0) stops recording and forgets the records. */
+/* Run a planned schedule with HOST inputs and outputs (the planned device buffers are
+ * the staging area): every task's randomizations go in chunks of chunk_r; chunk k's
+ * right-hand sides are copied in on a library stream while chunk k-1 computes on
+ * `stream`, and its results (c, lam, out, grad: those whose host pointer is non-NULL;
+ * each needs its device buffer in the plan) are copied back on another library stream
+ * while chunk k+1 computes.  io: one qk_host_io per planned task (host pointers, same
+ * layouts as the task's device buffers; page-locked memory lets the copies overlap).
+ * Returns after enqueueing; `stream` completes after the last copy back.  Not for
+ * stream capture.  (The paper has no counterpart: this is the runtime's host path.) */
+typedef struct {
+  const void *y; /* (R, nrhs, n) in the schedule dtype, required */
+  void *c;       /* (R, nrhs, n) or NULL */
+  double *lam;   /* (R, n) or NULL */
+  double *out;   /* (R, nrhs, QK_MLL_NOUT), required */
+  double *grad;  /* (R, nrhs, 2d + 2) or NULL */
+} qk_host_io;
+QK_API int qk_batch_run_host(void *ws, size_t ws_bytes, const qk_host_io *io, uint32_t chunk_r, uint32_t *status,
+                             qk_stream stream);
+
 QK_API int qk_batch_timing(void *ws, uint32_t runs);
 QK_API int qk_batch_kernel_ms(void *ws, uint32_t idx, char *name, size_t name_len, uint32_t *launches,
                               double *ms);

@@ -121,19 +121,17 @@ struct OpScope {
   }
 };
 
-static int run_plan(const Plan &p, unsigned char *ws, uint32_t *status, cudaStream_t st, LaunchTimer *tm) {
-  for (const qk_task &t : p.tasks) {
+// One task (or a range of its randomizations, see sub_task) through its kernels.
+static int run_task(const Plan &p, const qk_task &t, unsigned char *ws, uint32_t *status, cudaStream_t st,
+                    LaunchTimer *tm) {
+  {
     const uint32_t R = t.ps.R;
     const size_t tb = p.dtype == QK_F64 ? 8 : 4;
     unsigned char *col = ws;
     unsigned char *scr = ws + align256(tb * ((uint64_t)R << t.m));
     double *lam = t.lam ? t.lam : (double *)(ws + p.lam_off);
     const ColJob job = make_job(&t.ps, &t.k, 0, R, t.m);
-    if (use_fused(t, p.dtype, p.refine)) {
-      int rc = run_fused(t, job, p.dtype, p.refine, ws, status, st, tm);
-      if (rc) return rc;
-      continue;
-    }
+    if (use_fused(t, p.dtype, p.refine)) return run_fused(t, job, p.dtype, p.refine, ws, status, st, tm);
     int rc;
     {
       OpScope s(tm, "op_kernel_col", st);
@@ -154,6 +152,51 @@ static int run_plan(const Plan &p, unsigned char *ws, uint32_t *status, cudaStre
   }
   return QK_OK;
 }
+
+static int run_plan(const Plan &p, unsigned char *ws, uint32_t *status, cudaStream_t st, LaunchTimer *tm) {
+  for (const qk_task &t : p.tasks) {
+    int rc = run_task(p, t, ws, status, st, tm);
+    if (rc) return rc;
+  }
+  return QK_OK;
+}
+
+// Randomizations [r0, r0 + nr) of task t as a task of their own (pointers offset).
+static qk_task sub_task(const qk_task &t, uint32_t r0, uint32_t nr, size_t elem) {
+  qk_task s = t;
+  const uint64_t n = 1ull << t.m, d = t.ps.d;
+  s.ps.R = nr;
+  if (t.ps.Ct) s.ps.Ct = t.ps.Ct + (size_t)r0 * d * 32;
+  if (t.ps.D) s.ps.D = t.ps.D + (size_t)r0 * d;
+  s.y = (const unsigned char *)t.y + elem * r0 * t.nrhs * n;
+  if (t.c) s.c = (unsigned char *)t.c + elem * r0 * t.nrhs * n;
+  if (t.lam) s.lam = t.lam + (size_t)r0 * n;
+  s.out = t.out + (size_t)r0 * t.nrhs * QK_MLL_NOUT;
+  if (t.grad) s.grad = t.grad + (size_t)r0 * t.nrhs * (2 * d + 2);
+  return s;
+}
+
+// Streams and events of the host-buffer runner, created once per device.
+struct HostRunner {
+  cudaStream_t in = nullptr, out = nullptr;
+  std::vector<cudaEvent_t> ev;
+  int ensure(size_t nev) {
+    if (!in) {
+      cudaError_t e = cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "qk_batch_run_host: stream creation");
+    }
+    while (ev.size() < nev) {
+      cudaEvent_t x;
+      cudaError_t e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_fail(e, "qk_batch_run_host: event creation");
+      ev.push_back(x);
+    }
+    return QK_OK;
+  }
+};
+static std::mutex g_host_mu;
+static std::unordered_map<int, HostRunner> g_host_runners;
 
 }  // namespace qk
 
@@ -202,6 +245,84 @@ int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream stream) 
   }
   if (ws_bytes < p.total) return fail(QK_EWORKSPACE, "batch workspace has %zu bytes, %zu needed", ws_bytes, p.total);
   return run_plan(p, (unsigned char *)ws, status, (cudaStream_t)stream, tm);
+}
+
+int qk_batch_run_host(void *ws, size_t ws_bytes, const qk_host_io *io, uint32_t chunk_r, uint32_t *status,
+                      qk_stream stream) {
+  Plan p;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_plans.find(ws);
+    if (it == g_plans.end()) return fail(QK_EINVAL, "no plan recorded for this workspace (call qk_batch_plan)");
+    p = it->second;
+  }
+  if (ws_bytes < p.total) return fail(QK_EWORKSPACE, "batch workspace has %zu bytes, %zu needed", ws_bytes, p.total);
+  if (!io && !p.tasks.empty()) return fail(QK_EINVAL, "qk_batch_run_host: io is NULL");
+  if (chunk_r == 0) return fail(QK_EINVAL, "qk_batch_run_host: chunk_r must be >= 1");
+  const size_t elem = p.dtype == QK_F64 ? 8 : 4;
+  size_t nchunks = 0;
+  for (size_t i = 0; i < p.tasks.size(); ++i) {
+    const qk_task &t = p.tasks[i];
+    if (!io[i].y || !io[i].out) return fail(QK_EINVAL, "task %zu: host y and out are required", i);
+    if ((io[i].c && !t.c) || (io[i].lam && !t.lam) || (io[i].grad && !t.grad))
+      return fail(QK_EINVAL, "task %zu: a host output whose device buffer was not planned", i);
+    nchunks += (t.ps.R + chunk_r - 1) / chunk_r;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_host_mu);
+  HostRunner &hr = g_host_runners[dev];
+  int rc = hr.ensure(2 * nchunks + 1);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the copies must not start before earlier work on the caller's stream
+  cudaEvent_t start = hr.ev[2 * nchunks];
+  cudaError_t e = cudaEventRecord(start, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hr.in, start, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(hr.out, start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
+  size_t k = 0;
+  auto cp = [&](void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s) -> int {
+    if (!bytes) return QK_OK;
+    cudaError_t ce = cudaMemcpyAsync(dst, src, bytes, kind, s);
+    return ce == cudaSuccess ? QK_OK : cuda_fail(ce, "qk_batch_run_host: copy");
+  };
+  for (size_t i = 0; i < p.tasks.size(); ++i) {
+    const qk_task &t = p.tasks[i];
+    const uint64_t n = 1ull << t.m, d = t.ps.d;
+    for (uint32_t r0 = 0; r0 < t.ps.R; r0 += chunk_r, ++k) {
+      const uint32_t nr = t.ps.R - r0 < chunk_r ? t.ps.R - r0 : chunk_r;
+      const qk_task s = sub_task(t, r0, nr, elem);
+      const size_t ybytes = elem * nr * t.nrhs * n, yoff = elem * (size_t)r0 * t.nrhs * n;
+      // host -> device: this chunk's right-hand sides
+      if ((rc = cp((void *)s.y, (const unsigned char *)io[i].y + yoff, ybytes, cudaMemcpyHostToDevice, hr.in)))
+        return rc;
+      if ((e = cudaEventRecord(hr.ev[2 * k], hr.in)) != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
+      // compute on the caller's stream once the chunk has landed
+      if ((e = cudaStreamWaitEvent(st, hr.ev[2 * k], 0)) != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
+      if ((rc = run_task(p, s, (unsigned char *)ws, status, st, nullptr))) return rc;
+      if ((e = cudaEventRecord(hr.ev[2 * k + 1], st)) != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
+      // device -> host: this chunk's results, overlapping the next chunk's compute
+      if ((e = cudaStreamWaitEvent(hr.out, hr.ev[2 * k + 1], 0)) != cudaSuccess)
+        return cuda_fail(e, "qk_batch_run_host");
+      if (io[i].c && (rc = cp((unsigned char *)io[i].c + yoff, s.c, ybytes, cudaMemcpyDeviceToHost, hr.out)))
+        return rc;
+      if (io[i].lam && (rc = cp(io[i].lam + (size_t)r0 * n, s.lam, 8 * nr * n, cudaMemcpyDeviceToHost, hr.out)))
+        return rc;
+      if ((rc = cp(io[i].out + (size_t)r0 * t.nrhs * QK_MLL_NOUT, s.out, 8 * nr * t.nrhs * QK_MLL_NOUT,
+                   cudaMemcpyDeviceToHost, hr.out)))
+        return rc;
+      if (io[i].grad && (rc = cp(io[i].grad + (size_t)r0 * t.nrhs * (2 * d + 2), s.grad,
+                                 8 * nr * t.nrhs * (2 * d + 2), cudaMemcpyDeviceToHost, hr.out)))
+        return rc;
+    }
+  }
+  // the caller's stream completes only after the last copy back
+  if (k) {
+    if ((e = cudaEventRecord(hr.ev[2 * (k - 1)], hr.out)) != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
+    if ((e = cudaStreamWaitEvent(st, hr.ev[2 * (k - 1)], 0)) != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
+  }
+  return QK_OK;
 }
 
 int qk_batch_timing(void *ws, uint32_t runs) {

@@ -32,7 +32,7 @@ EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_sol
             "qk_batch_workspace_bytes", "qk_batch_plan", "qk_batch_run", "qk_workspace_bytes",
             "qk_read_status", "qk_last_error", "qk_version", "qk_fwht", "qk_fftbr", "qk_ifftbr",
             "qk_launch_count", "qk_eigs_static", "qk_batch_timing", "qk_batch_kernel_ms", "qk_fwht_ws",
-            "qk_fwht_tune", "qk_fwht_wait_selftest"]
+            "qk_fwht_tune", "qk_fwht_wait_selftest", "qk_batch_run_host"]
 
 
 class QKError(RuntimeError):
@@ -53,6 +53,11 @@ class Kernel(C.Structure):
 
 class FwhtPlan(C.Structure):
     _fields_ = [("mode", C.c_int32), ("lag", C.c_uint32), ("ctas_per_sm", C.c_uint32), ("ms", C.c_float)]
+
+
+class HostIO(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("c", C.c_void_p), ("lam", C.c_void_p), ("out", C.c_void_p),
+                ("grad", C.c_void_p)]
 
 
 class Task(C.Structure):
@@ -91,6 +96,7 @@ def _load():
         "qk_fwht_ws": [u32, u64, i32, P, P, sz, C.POINTER(FwhtPlan), P, P],
         "qk_fwht_tune": [u32, u64, i32, P, P, sz, C.POINTER(FwhtPlan), P],
         "qk_fwht_wait_selftest": [u32, u64, i32, P, P, sz, u32, P, P],
+        "qk_batch_run_host": [P, sz, C.POINTER(HostIO), u32, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -317,6 +323,16 @@ def batch_plan(tasks, dtype: torch.dtype, refine_steps: int, ws, stream=None):
 
 def batch_run(ws, status=None, stream=None):
     _check(LIB.qk_batch_run(_ptr(ws), ws.numel(), _ptr(status), _stream(stream)))
+
+
+def batch_run_host(ws, host_io, chunk_r: int, status=None, stream=None):
+    """Run the planned schedule from host tensors: host_io is a list (one per task) of dicts
+    with CPU tensors y (required), out (required), c, lam, grad (optional); copies in and out
+    overlap the compute chunk by chunk (pinned tensors for overlap)."""
+    arr = (HostIO * len(host_io))()
+    for i, h in enumerate(host_io):
+        arr[i] = HostIO(*[h[k].data_ptr() if h.get(k) is not None else None for k in ("y", "c", "lam", "out", "grad")])
+    _check(LIB.qk_batch_run_host(_ptr(ws), ws.numel(), arr, chunk_r, _ptr(status), _stream(stream)))
 
 
 def batch_timing(ws, runs: int):

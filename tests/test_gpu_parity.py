@@ -502,3 +502,32 @@ def test_fused_refinement_solves_the_fp32_operator(qk, m, alpha, eta):
         e0 = qc.rel_err(raw["c"][0, q], c_exact)
         assert e1 < 8 * math.sqrt(m) * qc.EPS32, (e1, e0)
         assert e1 < e0, (e1, e0)
+
+
+@pytest.mark.parametrize("chunk_r", [1, 3, 8])
+def test_batch_run_host_matches_device_run(qk, chunk_r):
+    """qk_batch_run_host (host buffers, chunked copies overlapping compute) gives the
+    device-resident schedule's results bit for bit, for every chunk size."""
+    from paper_2502_14256_gb300 import inputs
+    from tests import qkworkloads as W
+    wl = inputs.workload("solve20")
+    for dtype, refine in ((torch.float32, 1), (torch.float64, 0)):
+        inst = W.build_instance(qk, wl, 15, 8, 2)
+        task, bufs = W.outputs(qk, inst, dtype)
+        ws = qk.workspace(qk.batch_workspace_bytes([task], dtype))
+        qk.batch_plan([task], dtype, refine, ws)
+        status = torch.zeros(1, dtype=torch.int32, device=qc.dev())
+        qk.batch_run(ws, status)
+        torch.cuda.synchronize()
+        qk.read_status(status)
+        ref = {k: v.clone() for k, v in bufs.items() if v is not None}
+        host = {k: torch.zeros_like(v, device="cpu").pin_memory() for k, v in ref.items()}
+        host["y"] = ref["y"].cpu().pin_memory()
+        for v in bufs.values():
+            if v is not None:
+                v.zero_()
+        qk.batch_run_host(ws, [host], chunk_r, status)
+        torch.cuda.synchronize()
+        qk.read_status(status)
+        for k in ("c", "lam", "out", "grad"):
+            assert torch.equal(host[k], ref[k].cpu()), (k, dtype, chunk_r)
