@@ -335,13 +335,18 @@ def main():
     #   column sweep 8 flops per dimension (K, a = c K, p update),
     #   13-bit tile transforms 13 adds per vector.
     flops_per_point = {"k_fused_C": 10 * d_ + 2 * 13 + 3, "k_fused_A": 8 * d_ + 2 * 13 + 2}
+    # DRAM bytes (read + write) per launch from one ncu capture of the same kernels at
+    # R = 64, n = 2^20, d = 16 (profiles/fused_pipeline_solve20.md); traffic is per
+    # randomization, so it scales with R.  Only valid for that m and d.
+    ncu_traffic_r64 = {"k_fused_C": 806.0e6 + 248.0e6, "k_fused_A": 269.2e6 + 1010e6}
     roof = None
     if top_name in flops_per_point:
         work = flops_per_point[top_name] * R_ * n_
         ach = work / (top_ms * 1e-3) / 1e12
+        traffic = ncu_traffic_r64.get(top_name) if (W["m"], d_) == (20, 16) else None
         roof = {"kernel": top_name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": None, "ms_per_launch": top_ms,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+                "frac": ach / fp32_peak, "traffic": traffic * R_ / 64 if traffic else None,
+                "ms_per_launch": top_ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
@@ -374,6 +379,9 @@ def main():
             "fwht": {"gbs": fw_gbs, "ms": fw_ms, "frac_of_hbm": fw_gbs / hbm_peak, "bytes": fw_bytes,
                      "peak": hbm_peak, "peak_source": peak_src,
                      "shape": f"{R} x 2^{m} fp32, in place", "plan": fw_plan,
+                     # ncu: dram read + write of one persistent launch at 64 x 2^20
+                     # (profiles/fwht_persistent_64x2p20_fp32.md)
+                     "traffic": (268.5e6 + 213.9e6) if (R, m) == (64, 20) else None,
                      "two_launch_ms": fw2_ms, "two_launch_gbs": fw_bytes / (fw2_ms * 1e-3) / 1e9},
             "roofline": roof,
             "cpu_baseline": cpu,
