@@ -94,6 +94,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+# ------------------------------------------------------------- replicas
+def replica_seed_offset(rank: int) -> int:
+    """Replicas: every rank draws its own randomizations (no data exchange between ranks)."""
+    return 1000 * rank
+
+
+def max_over_ranks(x: float, torch, dist, world: int, device) -> float:
+    """The slowest rank's time: the whole job ends when its last rank does."""
+    if world <= 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job units/s: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------- the workload
 def build_workload(qk, torch, dev, R, m, seed_offset=0):
     """Seeded inputs on the device: scrambled columns, shifts, weights and y."""
@@ -236,7 +256,7 @@ def main():
         dist.barrier()
     from paper_2502_14256_gb300 import qk
 
-    W = build_workload(qk, torch, dev, args.R, args.m, seed_offset=1000 * rank)
+    W = build_workload(qk, torch, dev, args.R, args.m, seed_offset=replica_seed_offset(rank))
     stream = torch.cuda.current_stream()
 
     # ---- the headline: FP32-refined pipeline, device-resident inputs
@@ -258,11 +278,9 @@ def main():
     qk.batch_timing(P32.ws, 0)
     if world > 1:
         dist.barrier()
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, torch, dist, world, dev)
     points_step = world * W["R"] * W["n"]
-    value = points_step / (ms * 1e-3)
+    value = job_throughput(W["R"] * W["n"], world, ms)
 
     # ---- end to end through the public API with host buffers (pinned)
     y_host = P32.y.cpu().pin_memory()
@@ -278,10 +296,7 @@ def main():
         qk.batch_run_host(P32.ws, host_io, args.e2e_chunk, P32.status, stream=stream)
 
     e2e_ms = time_steps(torch, e2e_step, max(2, args.steps // 2), 1, stream)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e2e_ms, torch, dist, world, dev)
     h2d = y_host.numel() * y_host.element_size()
     d2h = sum(t.numel() * t.element_size() for t in (c_host, o_host, g_host))
 

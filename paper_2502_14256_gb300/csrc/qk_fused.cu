@@ -116,13 +116,16 @@ __device__ __forceinline__ void tile_wht(T (&v)[FCfg<T>::L], T *sm, int c) {
   }
 }
 
-// s + c tracks a sum with the rounding error of each addition carried in c (Kahan).
+// s + e tracks a sum exactly up to the rounding of e: the error of each addition to s
+// (TwoSum) is accumulated in e.  (Kahan's single correction term is not enough here: its
+// s - c keeps an error of ~u sum|v| per partial, and Sum y of a centred integrand is a
+// small difference of large terms.)
 template <typename T>
-__device__ __forceinline__ void kahan_add(T &s, T &c, T v) {
-  const T y = v - c;
-  const T t = s + y;
-  c = (t - s) - y;
+__device__ __forceinline__ void ff_add(T &s, T &e, T v) {
+  T t, r;
+  two_sum(s, v, t, r);
   s = t;
+  e += r;
 }
 
 // Compensated butterfly on (hi, lo) pairs: the rounding error of each hi sum is added
@@ -417,13 +420,13 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
   T p[L];
   column_sweep<T, FAM, ALPHA, L>(job, tb, wT, bi, p);
   T *P = reinterpret_cast<T *>(ft.p) + (uint64_t)r * n + base;
-  T ps = T(0), pc = T(0);  // compensated (Kahan) thread partial: the sum cancels
+  T ps = T(0), pe = T(0);  // compensated thread partial: the sum cancels
 #pragma unroll
   for (int l = 0; l < L; ++l) {
     P[t + (l << kLOGNT)] = p[l];
-    kahan_add(ps, pc, p[l]);
+    ff_add(ps, pe, p[l]);
   }
-  const double sps = block_sum_c(ps, -pc, red);
+  const double sps = block_sum_c(ps, pe, red);
   if (t == 0) ft.sp[(uint64_t)r * ft.tiles + tile] = sps;
   xwht_full<T>(p, sm, 0);  // L0 -> L2
   T *PT = reinterpret_cast<T *>(ft.pT) + (uint64_t)r * n + base;
@@ -433,13 +436,13 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
     const uint64_t v = (uint64_t)r * ft.nrhs + q;
     const T *Y = reinterpret_cast<const T *>(ft.y) + v * n + base;
     T yv[L];
-    T ys = T(0), yc = T(0);
+    T ys = T(0), ye = T(0);
 #pragma unroll
     for (int l = 0; l < L; ++l) {
       yv[l] = Y[t + (l << kLOGNT)];
-      kahan_add(ys, yc, yv[l]);
+      ff_add(ys, ye, yv[l]);
     }
-    const double sys = block_sum_c(ys, -yc, red);
+    const double sys = block_sum_c(ys, ye, red);
     if (t == 0) ft.sy[v * ft.tiles + tile] = sys;
     T *YT = reinterpret_cast<T *>(ft.yT) + v * n + base;
     if constexpr (COMP) {
