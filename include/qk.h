@@ -212,7 +212,7 @@ QK_API int qk_fftbr(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_stream
 QK_API int qk_ifftbr(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_stream stream);
 
 /* qk_fwht with a workspace: the same transform (bit for bit: the same butterflies in the
- * same order), for 2^13 < n <= 2^21 (FP32) or 2^12 < n <= 2^19 (FP64) run either as two
+ * same order), for 2^13 < n <= 2^21 (FP32) or 2^12 < n <= 2^20 (FP64) run either as two
  * launches (low bits on contiguous tiles, then high bits on column tiles) or as ONE
  * persistent launch in which resident CTAs take tiles from a global ticket counter and a
  * vector's column tiles are queued `lag` vectors after its low tiles, so that its

@@ -1,5 +1,6 @@
 // Fused solve + marginal log-likelihood + gradient for digital nets with DSI
-// kernels (arXiv 2502.14256, Sec. 5.3-5.4), n = 2^m with LOGT < m <= 2 LOGT - 5.
+// kernels (arXiv 2502.14256, Sec. 5.3-5.4), n = 2^m with LOGT < m <= 2 LOGT - LOGL
+// (2^13 < n <= 2^21 in FP32, 2^12 < n <= 2^20 in FP64).
 //
 // The length-n Hadamard transform is split at bit LOGT (tile = 2^LOGT elements:
 // 8192 FP32 / 4096 FP64).  Three phases per randomization r:
@@ -35,6 +36,9 @@ template <typename T> struct FCfg;
 template <> struct FCfg<float> { static constexpr int LOGT = 13, LOGL = 5, L = 32, PAD = 5; };
 template <> struct FCfg<double> { static constexpr int LOGT = 12, LOGL = 4, L = 16, PAD = 4; };
 constexpr int kFNT = 256, kLOGNT = 8;
+// Largest m of the two-pass split: the column tiles need at least L contiguous elements
+// (c = 2 LOGT - m >= LOGL).
+template <typename T> constexpr int two_pass_max_m() { return 2 * FCfg<T>::LOGT - FCfg<T>::LOGL; }
 
 struct FTask {
   ColJob job;
@@ -395,9 +399,8 @@ __device__ __forceinline__ double fused_log(double v) { return log(v); }
 
 // ------------------------------------------------------------------ phase A
 template <typename T, int FAM, int ALPHA, bool COMP>
-__global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
+__device__ __forceinline__ void fused_A_item(const FTask &ft, uint32_t r, uint32_t tile, unsigned char *smem) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
-  extern __shared__ __align__(16) unsigned char smem[];
   const ColJob &job = ft.job;
   const uint32_t d = job.d;
   double *wd;
@@ -408,7 +411,6 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
   T *sml = reinterpret_cast<T *>(smem + align256(col_smem_bytes<L>(d)) + xtile_bytes<T>());
   double *red = reinterpret_cast<double *>(smem + align256(col_smem_bytes<L>(d)) +
                                            (COMP ? 2 : 1) * xtile_bytes<T>());
-  const uint32_t r = blockIdx.y, tile = blockIdx.x;
   const uint64_t n = 1ull << job.m, base = (uint64_t)tile << LOGT;
   const int t = threadIdx.x;
   for (uint32_t q = t; q < d; q += kFNT) wT[q] = (T)job.w[q];
@@ -464,20 +466,25 @@ __global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
   }
 }
 
+template <typename T, int FAM, int ALPHA, bool COMP>
+__global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  fused_A_item<T, FAM, ALPHA, COMP>(ft, blockIdx.y, blockIdx.x, smem);
+}
+
 // ------------------------------------------------------------------ phase B
 template <typename T, bool COMP>
-__global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
+__device__ __forceinline__ void fused_B_item(const FTask &ft, uint32_t r, uint32_t tau, unsigned char *smem,
+                                             uint32_t *status) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
-  extern __shared__ __align__(16) unsigned char smem[];
   T *sm = reinterpret_cast<T *>(smem);
   T *lmv = reinterpret_cast<T *>(smem + xtile_bytes<T>());      // lambda (own entries)
   T *gst = reinterpret_cast<T *>(smem + 2 * xtile_bytes<T>());  // g (own entries) / lo tile
   double *red = reinterpret_cast<double *>(smem + 3 * xtile_bytes<T>());
-  const uint32_t r = blockIdx.y, tau = blockIdx.x;
   const int c = ft.cB, t = threadIdx.x;
   const uint64_t n = 1ull << ft.job.m;
   // element (t, l) of the tile is w = (row << LOGT) | (tau << c) | col, e = t + 256 l
-  const uint32_t tcol = tau << c;  // fused sizes keep n <= 2^(2 LOGT - 5) < 2^32
+  const uint32_t tcol = tau << c;  // fused sizes keep n <= 2^(2 LOGT - LOGL) < 2^32
   // tile element e -> index in the vector; wi0 / wi2: the elements (t, l) of layouts L0 / L2
   auto widx = [&](uint32_t e) -> uint32_t { return ((e >> c) << LOGT) | tcol | (e & ((1u << c) - 1)); };
   // L0 element (t, l) has e = t + 256 l; for c <= 8 its index is w0 + l * S0
@@ -488,7 +495,7 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
   const T *PT = reinterpret_cast<const T *>(ft.pT) + (uint64_t)r * n;
   T lam[L];
 #pragma unroll
-  for (int l = 0; l < L; ++l) lam[l] = PT[wi0(l)];
+  for (int l = 0; l < L; ++l) lam[l] = __ldcg(&PT[wi0(l)]);
   xwht_col<T>(lam, sm, c, 0);  // L0 -> L2
   const T zeta = (T)ft.job.zeta, eta = (T)ft.eta, zn = (T)(ft.job.zeta * (double)n);
   bool bad = false;
@@ -508,8 +515,8 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
     if (LAM) LAM[wi2(l)] = f2d_exact(v);
     lmv[t + (l << kLOGNT)] = v;  // each thread reads back only its own entries
   }
-  if (bad && ft.status) atomicOr(ft.status, (uint32_t)QK_STATUS_NOTPD);
-  if (floored && ft.status) atomicOr(ft.status, (uint32_t)QK_STATUS_FLOOR);
+  if (bad && status) atomicOr(status, (uint32_t)QK_STATUS_NOTPD);
+  if (floored && status) atomicOr(status, (uint32_t)QK_STATUS_FLOOR);
   const double ldsum = block_sum_c(lds, T(0), red);
   if (t == 0) ft.ld[(uint64_t)r * ft.tiles + tau] = ldsum;
   const T inv_n = T(1) / (T)n;
@@ -519,12 +526,12 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
     T *GT = reinterpret_cast<T *>(ft.gT) + v * n;
     T y[L];
 #pragma unroll
-    for (int l = 0; l < L; ++l) y[l] = YT[wi0(l)];
+    for (int l = 0; l < L; ++l) y[l] = __ldcg(&YT[wi0(l)]);
     T ylo[COMP ? L : 1];
     if constexpr (COMP) {
       const T *YL = reinterpret_cast<const T *>(ft.yL) + v * n;
 #pragma unroll
-      for (int l = 0; l < L; ++l) ylo[l] = YL[wi0(l)];
+      for (int l = 0; l < L; ++l) ylo[l] = __ldcg(&YL[wi0(l)]);
       xwht_col2<T>(y, ylo, sm, gst, c, 0);  // gst doubles as the lo tile here
     } else {
       xwht_col<T>(y, sm, c, 0);
@@ -570,11 +577,16 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
   }
 }
 
+template <typename T, bool COMP>
+__global__ void __launch_bounds__(kFNT, 2) k_fused_B(FTask ft) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  fused_B_item<T, COMP>(ft, blockIdx.y, blockIdx.x, smem, ft.status);
+}
+
 // ------------------------------------------------------------------ phase C
 template <typename T, int FAM, int ALPHA>
-__global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
+__device__ __forceinline__ void fused_C_item(const FTask &ft, uint32_t v, uint32_t tile, unsigned char *smem) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
-  extern __shared__ __align__(16) unsigned char smem[];
   const ColJob &job = ft.job;
   const uint32_t d = job.d;
   double *wd;
@@ -583,14 +595,14 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
   T *wT = reinterpret_cast<T *>(wd);
   T *sm = reinterpret_cast<T *>(smem + align256(col_smem_bytes<L>(d)));
   double *red = reinterpret_cast<double *>(smem + align256(col_smem_bytes<L>(d)) + xtile_bytes<T>());
-  const uint32_t v = blockIdx.y, r = v / ft.nrhs, tile = blockIdx.x;
+  const uint32_t r = v / ft.nrhs;
   const uint64_t n = 1ull << job.m, base = (uint64_t)tile << LOGT;
   const int t = threadIdx.x;
   const T *YT = reinterpret_cast<const T *>(ft.yT) + (uint64_t)v * n + base;
   const T *GT = reinterpret_cast<const T *>(ft.gT) + (uint64_t)v * n + base;
   T cc[L], uu[L];
 #pragma unroll
-  for (int l = 0; l < L; ++l) cc[l] = YT[e_of<T>(2, t, l)];
+  for (int l = 0; l < L; ++l) cc[l] = __ldcg(&YT[e_of<T>(2, t, l)]);
   xwht_full<T>(cc, sm, 1);  // L2 -> L0: the thread's own points
   if (ft.c) {
     T *Cv = reinterpret_cast<T *>(ft.c) + (uint64_t)v * n + base;
@@ -599,7 +611,7 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
   }
   if (!ft.grad) return;
 #pragma unroll
-  for (int l = 0; l < L; ++l) uu[l] = GT[e_of<T>(2, t, l)];
+  for (int l = 0; l < L; ++l) uu[l] = __ldcg(&GT[e_of<T>(2, t, l)]);
   xwht_full<T>(uu, sm, 1);
 #pragma unroll
   for (int l = 0; l < L; ++l) sm[t + (l << kLOGNT)] = uu[l];  // own entries, for the rare fallback
@@ -612,7 +624,7 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
   bool ok[L];
 #pragma unroll
   for (int l = 0; l < L; ++l) {
-    k1[l] = zeta * (T(1) + P[t + (l << kLOGNT)]);
+    k1[l] = zeta * (T(1) + __ldcg(&P[t + (l << kLOGNT)]));
     bi[l] = __brev((uint32_t)(base + t + (l << kLOGNT)));
     ok[l] = true;
     uu[l] *= k1[l];  // from here on uu holds u k1
@@ -626,19 +638,25 @@ __global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
   for (uint32_t q = t; q < 2 * d; q += kFNT) dst[q] = red_total<T>(red, kFNT / 32, 2 * d, q);
 }
 
+template <typename T, int FAM, int ALPHA>
+__global__ void __launch_bounds__(kFNT, 2) k_fused_C(FTask ft) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  fused_C_item<T, FAM, ALPHA>(ft, blockIdx.y, blockIdx.x, smem);
+}
+
 // ------------------------------------------------------------------ final
-__global__ void __launch_bounds__(256) k_fused_final(FTask ft) {
+__device__ __forceinline__ void fused_final_item(const FTask &ft, uint32_t v) {
   __shared__ double sh[32];
-  const uint32_t v = blockIdx.x, r = v / ft.nrhs;
+  const uint32_t r = v / ft.nrhs;
   const uint32_t tiles = ft.tiles, d = ft.job.d;
   const double n = (double)(1ull << ft.job.m), zeta = ft.job.zeta;
   double q = 0, gsum = 0, ld = 0, sp = 0, sy = 0;
   for (uint32_t b = threadIdx.x; b < tiles; b += blockDim.x) {
-    q += ft.qg[((uint64_t)v * tiles + b) * 2 + 0];
-    gsum += ft.qg[((uint64_t)v * tiles + b) * 2 + 1];
-    ld += ft.ld[(uint64_t)r * tiles + b];
-    sp += ft.sp[(uint64_t)r * tiles + b];
-    sy += ft.sy[(uint64_t)v * tiles + b];
+    q += __ldcg(&ft.qg[((uint64_t)v * tiles + b) * 2 + 0]);
+    gsum += __ldcg(&ft.qg[((uint64_t)v * tiles + b) * 2 + 1]);
+    ld += __ldcg(&ft.ld[(uint64_t)r * tiles + b]);
+    sp += __ldcg(&ft.sp[(uint64_t)r * tiles + b]);
+    sy += __ldcg(&ft.sy[(uint64_t)v * tiles + b]);
   }
   q = block_sum(q, sh);
   gsum = block_sum(gsum, sh);
@@ -665,7 +683,7 @@ __global__ void __launch_bounds__(256) k_fused_final(FTask ft) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t j = warp; j < 2 * d; j += blockDim.x >> 5) {
     double s = 0.0;
-    for (uint32_t b = lane; b < tiles; b += 32) s += ft.gr[((uint64_t)v * tiles + b) * 2 * d + j];
+    for (uint32_t b = lane; b < tiles; b += 32) s += __ldcg(&ft.gr[((uint64_t)v * tiles + b) * 2 * d + j]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) {
@@ -679,8 +697,10 @@ __global__ void __launch_bounds__(256) k_fused_final(FTask ft) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_fused_final(FTask ft) { fused_final_item(ft, blockIdx.x); }
+
 // ------------------------------------------------- standalone batched WHT
-// x <- H x * scale for vectors of n = 2^m with LOGT < m <= 2 LOGT - 5, in place, in two
+// x <- H x * scale for vectors of n = 2^m with LOGT < m <= 2 LOGT - LOGL, in place, in two
 // tile passes: low LOGT bits on contiguous tiles, the high bits on column tiles.
 template <typename T>
 __global__ void __launch_bounds__(kFNT) k_wht_low(T *__restrict__ x) {
@@ -836,12 +856,13 @@ static WhtKernels<T> wht_pick(int m, std::integer_sequence<int, I...>) {
 template <typename T>
 static WhtKernels<T> wht_kernels(int m) {
   constexpr int LOGT = FCfg<T>::LOGT;
-  return wht_pick<T>(m, std::make_integer_sequence<int, (2 * LOGT - 5) - LOGT>());
+  return wht_pick<T>(m, std::make_integer_sequence<int, two_pass_max_m<T>() - LOGT>());
 }
 
 bool tiled_wht_supported(uint32_t m, int dtype) {
   const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
-  return (int)m > LOGT && (int)m <= 2 * LOGT - 5;
+  const int MX = dtype == QK_F64 ? two_pass_max_m<double>() : two_pass_max_m<float>();
+  return (int)m > LOGT && (int)m <= MX;
 }
 
 // Vectors may be processed in chunks (chunk_bytes) so that the second pass could find
@@ -878,7 +899,7 @@ static int persist_occupancy() {
   static int occ = -1;
   if (occ < 0) {
     // every instantiation has the same launch bounds and shared memory; query one
-    constexpr int M = 2 * FCfg<T>::LOGT - 6;
+    constexpr int M = two_pass_max_m<T>() - 1;
     const size_t sm = xtile_bytes<T>();
     smem_optin<k_wht_persist<T, M>>(sm);
     int o = 0;
@@ -950,7 +971,8 @@ int persist_wht(void *x, uint32_t m, uint64_t nvec, int dtype, double scale, voi
 bool fused_supported(const qk_task &t, int dtype) {
   if (t.k.family != QK_DSI || t.ps.kind != QK_NET_B2) return false;
   const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
-  return (int)t.m > LOGT && (int)t.m <= 2 * LOGT - 5;
+  const int MX = dtype == QK_F64 ? two_pass_max_m<double>() : two_pass_max_m<float>();
+  return (int)t.m > LOGT && (int)t.m <= MX;
 }
 
 static size_t fused_elem(int dtype) { return dtype == QK_F64 ? 8 : 4; }
@@ -1010,8 +1032,9 @@ static int dispatch_fused(const FTask &ft, cudaStream_t st, LaunchTimer *tm) {
   }
 }
 
-int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *ws, uint32_t *status,
-              cudaStream_t st, LaunchTimer *tm) {
+// The fused view of a task: its pointers and the scratch buffers carved from ws (in the
+// order and sizes of fused_ws_bytes).
+static FTask make_ftask(const qk_task &t, const ColJob &job, int dtype, int refine, void *ws, uint32_t *status) {
   const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
   const uint64_t R = t.ps.R, n = 1ull << t.m, tiles = n >> LOGT, nv = R * t.nrhs;
   const size_t e = fused_elem(dtype);
@@ -1038,14 +1061,17 @@ int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *
   ft.qg = (double *)p, p += align256(16 * nv * tiles);
   ft.gr = (double *)p;
   p += align256(8 * nv * tiles * 2 * (uint64_t)t.ps.d);
-  ft.yL = nullptr;
+  ft.yL = (dtype == QK_F32 && refine > 0) ? p : nullptr;
+  return ft;
+}
+
+int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *ws, uint32_t *status,
+              cudaStream_t st, LaunchTimer *tm) {
+  const FTask ft = make_ftask(t, job, dtype, refine, ws, status);
   // FP64 needs no refinement; FP32 with refine >= 1 runs the compensated variant
   // (one exact-residual step; further steps change nothing at FP32 resolution)
   if (dtype == QK_F64) return dispatch_fused<double, false>(ft, st, tm);
-  if (refine > 0) {
-    ft.yL = p;
-    return dispatch_fused<float, true>(ft, st, tm);
-  }
+  if (refine > 0) return dispatch_fused<float, true>(ft, st, tm);
   return dispatch_fused<float, false>(ft, st, tm);
 }
 

@@ -1,6 +1,6 @@
 // Batched FWHT with a workspace (qk_fwht_ws) and its autotuner (qk_fwht_tune).
 //
-// For LOGT < m <= 2 LOGT - 5 the transform is two tile passes (low bits on contiguous
+// For LOGT < m <= 2 LOGT - LOGL the transform is two tile passes (low bits on contiguous
 // tiles, high bits on column tiles).  They run either as two launches over the whole
 // batch, or as one persistent launch that queues a vector's column tiles `lag` vectors
 // after its low tiles (qk_fused.cu).  Which is faster, and with which lag and number of

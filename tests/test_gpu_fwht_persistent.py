@@ -25,7 +25,7 @@ def _data(nvec, m, dtype, seed):
 
 
 CASES = [(torch.float32, 14, 1), (torch.float32, 16, 37), (torch.float32, 20, 9), (torch.float32, 21, 3),
-         (torch.float64, 13, 5), (torch.float64, 17, 11), (torch.float64, 19, 2)]
+         (torch.float64, 13, 5), (torch.float64, 17, 11), (torch.float64, 19, 2), (torch.float64, 20, 3)]
 
 
 @pytest.mark.parametrize("dtype,m,nvec", CASES)
