@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-chunk", type=int, default=8, help="randomizations per host-copy chunk (e2e)")
+    ap.add_argument("--sched", default="launches", choices=["launches", "persistent"],
+                    help="batched schedule: per-phase launches or one persistent launch")
+    ap.add_argument("--lag", type=int, default=1, help="persistent schedule: units between phases")
     return ap.parse_args()
 
 
@@ -261,6 +264,8 @@ def main():
 
     # ---- the headline: FP32-refined pipeline, device-resident inputs
     P32 = Pipeline(qk, torch, dev, W, torch.float32, refine=args.refine)
+    if args.sched == "persistent":
+        qk.batch_schedule(P32.ws, qk.QK_SCHED_PERSISTENT, args.lag)
     for _ in range(args.warmup):
         P32.step()
     qk.read_status(P32.status)

@@ -289,6 +289,22 @@ QK_API int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream s
  * events and returns, for the idx-th distinct kernel name, its launch count and
  * summed device milliseconds; QK_EINVAL once idx runs past the last name.
  * qk_batch_timing(ws, 0) stops recording and forgets the records. */
+/* How qk_batch_run executes a recorded plan.  QK_SCHED_LAUNCHES (the default after
+ * qk_batch_plan): per task, a sequence of kernel launches (4 for fused tasks).
+ * QK_SCHED_PERSISTENT: ONE launch of resident CTAs for the whole plan; every
+ * randomization of every task is a unit whose tiles (column sweep, high-bit transform
+ * and epilogue, inverse and gradient sweep, final reduction) are taken in ticket order,
+ * a unit's next phase `lag` units (1 or 2; 0 = 1) after its previous one, with bounded
+ * waits on per-unit completion counters (QK_STATUS_TIMEOUT if one ever runs out).  Needs
+ * every task to be a DSI net of one order in the fused size range (2^13 < n <= 2^21 FP32,
+ * 2^12 < n <= 2^20 FP64); QK_EINVAL otherwise.  Uploads the schedule tables into the
+ * workspace synchronously: call it outside stream capture; runs are capturable.
+ * Results equal the launch sequence's bit for bit.  qk_batch_run_host always uses the
+ * launch sequence. */
+#define QK_SCHED_LAUNCHES 0
+#define QK_SCHED_PERSISTENT 1
+QK_API int qk_batch_schedule(void *ws, size_t ws_bytes, int32_t mode, uint32_t lag);
+
 /* Run a planned schedule with HOST inputs and outputs (the planned device buffers are
  * the staging area): every task's randomizations go in chunks of chunk_r; chunk k's
  * right-hand sides are copied in on a library stream while chunk k-1 computes on

@@ -53,9 +53,14 @@ struct Plan {
   int32_t refine = 0;
   size_t scratch = 0;   // bytes of the shared scratch region
   size_t lam_off = 0;   // offset of the eigenvalue buffer
+  size_t persist_off = 0, persist_bytes = 0;  // region of the persistent schedule (if eligible)
   size_t total = 0;
+  int32_t mode = QK_SCHED_LAUNCHES;
+  PersistState persist;
   std::shared_ptr<EventTimer> timer;
 };
+
+constexpr uint32_t kMaxPersistLag = 2;  // the workspace is sized for lags up to this
 
 static std::mutex g_mu;
 static std::unordered_map<const void *, Plan> g_plans;
@@ -106,6 +111,15 @@ static int make_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, int32
   p.scratch = align256(scratch);
   p.lam_off = p.scratch;
   p.total = p.scratch + lam;
+  p.persist_off = align256(p.total);
+  p.persist_bytes = 0;
+  if (persist_eligible(p.tasks, dtype)) {
+    for (uint32_t lag = 1; lag <= kMaxPersistLag; ++lag) {
+      const size_t b = persist_ws_bytes(p.tasks, dtype, refine, lag);
+      if (b > p.persist_bytes) p.persist_bytes = b;
+    }
+    p.total = p.persist_off + p.persist_bytes;
+  }
   return QK_OK;
 }
 
@@ -154,6 +168,7 @@ static int run_task(const Plan &p, const qk_task &t, unsigned char *ws, uint32_t
 }
 
 static int run_plan(const Plan &p, unsigned char *ws, uint32_t *status, cudaStream_t st, LaunchTimer *tm) {
+  if (p.mode == QK_SCHED_PERSISTENT && p.persist.ok) return persist_run(p.persist, status, st, tm);
   for (const qk_task &t : p.tasks) {
     int rc = run_task(p, t, ws, status, st, tm);
     if (rc) return rc;
@@ -245,6 +260,30 @@ int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream stream) 
   }
   if (ws_bytes < p.total) return fail(QK_EWORKSPACE, "batch workspace has %zu bytes, %zu needed", ws_bytes, p.total);
   return run_plan(p, (unsigned char *)ws, status, (cudaStream_t)stream, tm);
+}
+
+int qk_batch_schedule(void *ws, size_t ws_bytes, int32_t mode, uint32_t lag) {
+  if (mode != QK_SCHED_LAUNCHES && mode != QK_SCHED_PERSISTENT)
+    return fail(QK_EINVAL, "mode must be QK_SCHED_LAUNCHES or QK_SCHED_PERSISTENT");
+  if (lag > kMaxPersistLag) return fail(QK_EINVAL, "lag must be 0..%u", kMaxPersistLag);
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_plans.find(ws);
+  if (it == g_plans.end()) return fail(QK_EINVAL, "no plan recorded for this workspace (call qk_batch_plan)");
+  Plan &p = it->second;
+  if (ws_bytes < p.total) return fail(QK_EWORKSPACE, "batch workspace has %zu bytes, %zu needed", ws_bytes, p.total);
+  if (mode == QK_SCHED_LAUNCHES) {
+    p.mode = mode;
+    return QK_OK;
+  }
+  if (!p.persist_bytes)
+    return fail(QK_EINVAL, "the persistent schedule needs every task to be a fused DSI net task of one order");
+  PersistState st;
+  int rc = persist_setup(p.tasks, p.dtype, p.refine, lag ? lag : 1, (unsigned char *)ws + p.persist_off,
+                         p.persist_bytes, st);
+  if (rc) return rc;
+  p.persist = st;
+  p.mode = mode;
+  return QK_OK;
 }
 
 int qk_batch_run_host(void *ws, size_t ws_bytes, const qk_host_io *io, uint32_t chunk_r, uint32_t *status,

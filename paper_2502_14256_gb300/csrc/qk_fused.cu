@@ -1075,4 +1075,287 @@ int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *
   return dispatch_fused<float, false>(ft, st, tm);
 }
 
+// -------------------------------------- persistent whole-pipeline schedule (one launch)
+// Every randomization of every task is a unit u with four kinds of work items: A tiles,
+// B column tiles, C tiles (x right-hand sides) and F (the final reduction, one per
+// right-hand side).  Resident CTAs take items in ticket order; step s of the sequence
+// holds A(s), B(s - lag), C(s - 2 lag), F(s - 2 lag - 1), so a unit's phases follow each
+// other while its intermediate vectors are in L2.  Units cycle through nslot scratch
+// slots; A(u) reuses the slot of u - nslot once F(u - nslot) has finished.
+//
+// Item dependencies: B(u) after all A(u), C(u) after all B(u), F(u) after all C(u) (after
+// all B(u) when the unit wants neither c nor the gradient), A(u) after all F(u - nslot).
+// Each is on items with smaller tickets (nslot > 2 lag + 1), a CTA waits only while it
+// holds no unpublished item, and those items were claimed by CTAs that are running: the
+// waits end.  They are bounded all the same: past the limit the CTA raises
+// QK_STATUS_TIMEOUT and the shared abort flag, and every later wait gives up at once, so
+// the launch finishes.
+struct PUnit {
+  FTask ft;                   // one randomization: r = 0, scratch in slot u mod nslot
+  uint32_t tiles, nrhs, ncv;  // ncv: C items (tiles x nrhs, 0 when neither c nor grad is wanted)
+};
+struct PSched {
+  const PUnit *units;
+  const uint32_t *step_off;  // S + 1 prefix counts of items per step
+  uint32_t U, S, lag, nslot;
+  uint32_t *ctr;  // ticket, abort flag, then cntA, cntB, cntC, cntF (U each)
+  uint32_t *status;
+  uint32_t spin_limit;
+};
+enum { PK_A = 0, PK_B = 1, PK_C = 2, PK_F = 3 };
+
+__device__ __forceinline__ void psched_decode(const PSched &ps, uint32_t it, uint32_t &kind, uint32_t &u,
+                                              uint32_t &idx) {
+  uint32_t lo = 0, hi = ps.S;  // step_off[lo] <= it < step_off[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (ps.step_off[mid] <= it) lo = mid;
+    else hi = mid;
+  }
+  const uint32_t s = lo, L = ps.lag;
+  uint32_t k = it - ps.step_off[s];
+  if (s < ps.U) {
+    const uint32_t nA = ps.units[s].tiles;
+    if (k < nA) {
+      kind = PK_A, u = s, idx = k;
+      return;
+    }
+    k -= nA;
+  }
+  if (s >= L && s - L < ps.U) {
+    const uint32_t nB = ps.units[s - L].tiles;
+    if (k < nB) {
+      kind = PK_B, u = s - L, idx = k;
+      return;
+    }
+    k -= nB;
+  }
+  if (s >= 2 * L && s - 2 * L < ps.U) {
+    const uint32_t nC = ps.units[s - 2 * L].ncv;
+    if (k < nC) {
+      kind = PK_C, u = s - 2 * L, idx = k;
+      return;
+    }
+    k -= nC;
+  }
+  kind = PK_F, u = s - 2 * L - 1, idx = k;
+}
+
+// Thread 0: wait until *cnt >= need (bounded); false if this item must be skipped.
+__device__ __forceinline__ bool psched_wait(const PSched &ps, const uint32_t *cnt, uint32_t need) {
+  volatile uint32_t *abort_flag = ps.ctr + 1;
+  uint32_t k = 0;
+  while (ld_acquire_u32(cnt) < need) {
+    if (*abort_flag) return false;
+    if (++k > ps.spin_limit) {
+      atomicExch(ps.ctr + 1, 1u);
+      if (ps.status) atomicOr(ps.status, (uint32_t)QK_STATUS_TIMEOUT);
+      return false;
+    }
+    __nanosleep(128);
+  }
+  return true;
+}
+
+template <typename T, int FAM, int ALPHA, bool COMP>
+__global__ void __launch_bounds__(kFNT, 2) k_fused_persist(PSched ps) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ uint32_t s_it, s_ok;
+  const int t = threadIdx.x;
+  const uint32_t total = ps.step_off[ps.S];
+  uint32_t *cntA = ps.ctr + 2, *cntB = cntA + ps.U, *cntC = cntB + ps.U, *cntF = cntC + ps.U;
+  for (;;) {
+    if (t == 0) s_it = atomicAdd(ps.ctr, 1u);
+    __syncthreads();
+    const uint32_t it = s_it;
+    if (it >= total) break;
+    uint32_t kind, u, idx;
+    psched_decode(ps, it, kind, u, idx);
+    const PUnit &pu = ps.units[u];
+    if (t == 0) {
+      bool ok = true;
+      if (kind == PK_A && u >= ps.nslot) ok = psched_wait(ps, cntF + (u - ps.nslot), ps.units[u - ps.nslot].nrhs);
+      else if (kind == PK_B) ok = psched_wait(ps, cntA + u, pu.tiles);
+      else if (kind == PK_C) ok = psched_wait(ps, cntB + u, pu.tiles);
+      else if (kind == PK_F)  // after C, or after B when the unit has no C items
+        ok = pu.ncv ? psched_wait(ps, cntC + u, pu.ncv) : psched_wait(ps, cntB + u, pu.tiles);
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) continue;  // uniform; the loop's first barrier separates s_ok's next write
+    if (kind == PK_A) {
+      fused_A_item<T, FAM, ALPHA, COMP>(pu.ft, 0, idx, smem);
+    } else if (kind == PK_B) {
+      fused_B_item<T, COMP>(pu.ft, 0, idx, smem, ps.status);
+    } else if (kind == PK_C) {
+      fused_C_item<T, FAM, ALPHA>(pu.ft, idx / pu.tiles, idx % pu.tiles, smem);
+    } else {
+      fused_final_item(pu.ft, idx);
+    }
+    __syncthreads();  // every thread's stores (and shared-memory reads) are done
+    if (t == 0)
+      red_release_add_u32((kind == PK_A ? cntA : kind == PK_B ? cntB : kind == PK_C ? cntC : cntF) + u, 1u);
+  }
+}
+
+template <typename T, int FAM, int ALPHA, bool COMP>
+static int persist_launch_t(const PSched &ps, uint32_t dmax, cudaStream_t st) {
+  constexpr int L = FCfg<T>::L;
+  const size_t colb = align256(col_smem_bytes<L>(dmax));
+  const size_t smA = colb + (COMP ? 2 : 1) * xtile_bytes<T>() + 32 * sizeof(double);
+  const size_t smB = 3 * xtile_bytes<T>() + 32 * sizeof(double);
+  const size_t smC = colb + xtile_bytes<T>() + (size_t)(kFNT / 32) * 2 * dmax * sizeof(double);
+  size_t sm = smA > smB ? smA : smB;
+  if (smC > sm) sm = smC;
+  smem_optin<k_fused_persist<T, FAM, ALPHA, COMP>>(sm);
+  int occ = 0, dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fused_persist<T, FAM, ALPHA, COMP>, kFNT, sm);
+  if (e != cudaSuccess || occ < 1)
+    return fail(QK_ECUDA, "persistent schedule: %zu bytes of shared memory per CTA do not fit", sm);
+  k_fused_persist<T, FAM, ALPHA, COMP><<<(unsigned)(sms * occ), kFNT, sm, st>>>(ps);
+  return check_launch("fused persistent");
+}
+
+static int persist_launch(const PSched &ps, int dtype, int refine, int alpha, uint32_t dmax, cudaStream_t st) {
+  if (dtype == QK_F64) {
+    switch (alpha) {
+      case 1: return persist_launch_t<double, 0, 1, false>(ps, dmax, st);
+      case 2: return persist_launch_t<double, 0, 2, false>(ps, dmax, st);
+      case 3: return persist_launch_t<double, 0, 3, false>(ps, dmax, st);
+      case 4: return persist_launch_t<double, 0, 4, false>(ps, dmax, st);
+    }
+  } else if (refine > 0) {
+    switch (alpha) {
+      case 1: return persist_launch_t<float, 0, 1, true>(ps, dmax, st);
+      case 2: return persist_launch_t<float, 0, 2, true>(ps, dmax, st);
+      case 3: return persist_launch_t<float, 0, 3, true>(ps, dmax, st);
+      case 4: return persist_launch_t<float, 0, 4, true>(ps, dmax, st);
+    }
+  } else {
+    switch (alpha) {
+      case 1: return persist_launch_t<float, 0, 1, false>(ps, dmax, st);
+      case 2: return persist_launch_t<float, 0, 2, false>(ps, dmax, st);
+      case 3: return persist_launch_t<float, 0, 3, false>(ps, dmax, st);
+      case 4: return persist_launch_t<float, 0, 4, false>(ps, dmax, st);
+    }
+  }
+  return fail(QK_EINVAL, "DSI order must be 1..4");
+}
+
+// Host side: the unit table, step table and counters live in the workspace region given
+// to persist_setup (tables uploaded once, synchronously); persist_run resets the counters
+// and launches.
+bool persist_eligible(const std::vector<qk_task> &tasks, int dtype) {
+  if (tasks.empty()) return false;
+  for (const qk_task &t : tasks)
+    if (!fused_supported(t, dtype) || t.k.alpha != tasks[0].k.alpha) return false;
+  return true;
+}
+
+static size_t unit_scratch(const qk_task &t, int dtype, int refine) {
+  qk_task one = t;
+  one.ps.R = 1;
+  return align256(fused_ws_bytes(one, dtype, refine));
+}
+
+static uint32_t persist_nslot(uint32_t lag) { return 2 * lag + 3; }
+
+size_t persist_ws_bytes(const std::vector<qk_task> &tasks, int dtype, int refine, uint32_t lag) {
+  if (lag == 0) lag = 1;
+  size_t slot = 0, U = 0;
+  for (const qk_task &t : tasks) {
+    const size_t b = unit_scratch(t, dtype, refine);
+    if (b > slot) slot = b;
+    U += t.ps.R;
+  }
+  const size_t S = U + 2 * lag + 2;
+  return persist_nslot(lag) * slot + align256(sizeof(PUnit) * U) + align256(sizeof(uint32_t) * (S + 1)) +
+         align256(sizeof(uint32_t) * (2 + 4 * U));
+}
+
+int persist_setup(const std::vector<qk_task> &tasks, int dtype, int refine, uint32_t lag, void *region, size_t bytes,
+                  PersistState &out) {
+  if (lag == 0) lag = 1;
+  if (!persist_eligible(tasks, dtype))
+    return fail(QK_EINVAL, "persistent schedule: tasks are not all fused DSI nets of one order");
+  if (bytes < persist_ws_bytes(tasks, dtype, refine, lag))
+    return fail(QK_EWORKSPACE, "persistent schedule: workspace too small");
+  const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
+  size_t slot = 0;
+  uint32_t U = 0, dmax = 0;
+  for (const qk_task &t : tasks) {
+    const size_t b = unit_scratch(t, dtype, refine);
+    if (b > slot) slot = b;
+    U += t.ps.R;
+    if (t.ps.d > dmax) dmax = t.ps.d;
+  }
+  const uint32_t nslot = persist_nslot(lag), S = U + 2 * lag + 2;
+  unsigned char *base = (unsigned char *)region;
+  unsigned char *units_d = base + nslot * slot;
+  unsigned char *steps_d = units_d + align256(sizeof(PUnit) * U);
+  unsigned char *ctr_d = steps_d + align256(sizeof(uint32_t) * (S + 1));
+  std::vector<PUnit> units;
+  units.reserve(U);
+  const size_t elem = dtype == QK_F64 ? 8 : 4;
+  for (const qk_task &t : tasks) {
+    const uint64_t n = 1ull << t.m, d = t.ps.d;
+    for (uint32_t r = 0; r < t.ps.R; ++r) {
+      qk_task one = t;  // randomization r as a task of its own
+      one.ps.R = 1;
+      if (t.ps.Ct) one.ps.Ct = t.ps.Ct + (size_t)r * d * 32;
+      one.y = (const unsigned char *)t.y + elem * (size_t)r * t.nrhs * n;
+      if (t.c) one.c = (unsigned char *)t.c + elem * (size_t)r * t.nrhs * n;
+      if (t.lam) one.lam = t.lam + (size_t)r * n;
+      one.out = t.out + (size_t)r * t.nrhs * QK_MLL_NOUT;
+      if (t.grad) one.grad = t.grad + (size_t)r * t.nrhs * (2 * d + 2);
+      const ColJob job = make_job(&one.ps, &one.k, 0, 1, one.m);
+      PUnit pu;
+      pu.ft = make_ftask(one, job, dtype, refine, base + (size_t)(units.size() % nslot) * slot, nullptr);
+      pu.tiles = (uint32_t)(n >> LOGT);
+      pu.nrhs = t.nrhs;
+      pu.ncv = (t.c || t.grad) ? pu.tiles * t.nrhs : 0;
+      units.push_back(pu);
+    }
+  }
+  std::vector<uint32_t> off(S + 1, 0);
+  for (uint32_t s = 0; s < S; ++s) {
+    uint64_t c = 0;
+    if (s < U) c += units[s].tiles;
+    if (s >= lag && s - lag < U) c += units[s - lag].tiles;
+    if (s >= 2 * lag && s - 2 * lag < U) c += units[s - 2 * lag].ncv;
+    if (s >= 2 * lag + 1 && s - 2 * lag - 1 < U) c += units[s - 2 * lag - 1].nrhs;
+    if (off[s] + c >= (1ull << 31)) return fail(QK_EINVAL, "persistent schedule: more than 2^31 work items");
+    off[s + 1] = off[s] + (uint32_t)c;
+  }
+  cudaError_t e = cudaMemcpy(units_d, units.data(), sizeof(PUnit) * U, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(steps_d, off.data(), sizeof(uint32_t) * (S + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent schedule: table upload");
+  out.units = units_d;
+  out.steps = steps_d;
+  out.ctr = ctr_d;
+  out.ctr_bytes = sizeof(uint32_t) * (2 + 4 * (size_t)U);
+  out.U = U, out.S = S, out.lag = lag, out.nslot = nslot, out.dmax = dmax;
+  out.dtype = dtype, out.refine = refine, out.alpha = tasks[0].k.alpha;
+  out.ok = true;
+  return QK_OK;
+}
+
+int persist_run(const PersistState &p, uint32_t *status, cudaStream_t st, LaunchTimer *tm, uint32_t spin_limit) {
+  cudaError_t e = cudaMemsetAsync(p.ctr, 0, p.ctr_bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent schedule: counter reset");
+  PSched ps;
+  ps.units = (const PUnit *)p.units;
+  ps.step_off = (const uint32_t *)p.steps;
+  ps.U = p.U, ps.S = p.S, ps.lag = p.lag, ps.nslot = p.nslot;
+  ps.ctr = (uint32_t *)p.ctr;
+  ps.status = status;
+  ps.spin_limit = spin_limit;
+  if (tm) tm->begin("k_fused_persist", st);
+  int rc = persist_launch(ps, p.dtype, p.refine, p.alpha, p.dmax, st);
+  if (tm) tm->end(st);
+  return rc;
+}
+
 }  // namespace qk

@@ -1,6 +1,8 @@
 // Host-side launchers shared between the libqk translation units.
 #pragma once
 
+#include <vector>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,6 +28,9 @@ struct ColJob {
   int32_t family, alpha;
   uint32_t nr;          // randomizations in this job
 };
+
+// The job of randomizations r0 .. r0+nr-1 of a (validated) point set and kernel (qk_api.cu).
+ColJob make_job(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr, uint32_t m);
 
 // First column (form QK_COL_K1 / QK_COL_P) of nr randomizations: out (nr, n).
 int launch_kernel_col(const ColJob &job, int32_t dtype, int32_t form, void *out, cudaStream_t st);
@@ -55,6 +60,22 @@ int persist_wht(void *x, uint32_t m, uint64_t nvec, int dtype, double scale, voi
                 cudaStream_t st, uint32_t lag, uint32_t ctas_per_sm, uint32_t spin_limit = kSpinLimit,
                 bool columns_only = false);
 size_t fused_ws_bytes(const qk_task &t, int dtype, int refine);
+
+// Persistent whole-pipeline schedule (qk_fused.cu): one launch for every randomization of
+// every task (all fused DSI nets of one order).
+struct PersistState {
+  bool ok = false;
+  void *units = nullptr, *steps = nullptr, *ctr = nullptr;
+  size_t ctr_bytes = 0;
+  uint32_t U = 0, S = 0, lag = 0, nslot = 0, dmax = 0;
+  int dtype = 0, refine = 0, alpha = 0;
+};
+bool persist_eligible(const std::vector<qk_task> &tasks, int dtype);
+size_t persist_ws_bytes(const std::vector<qk_task> &tasks, int dtype, int refine, uint32_t lag);
+int persist_setup(const std::vector<qk_task> &tasks, int dtype, int refine, uint32_t lag, void *region,
+                  size_t bytes, PersistState &out);
+int persist_run(const PersistState &p, uint32_t *status, cudaStream_t st, LaunchTimer *tm,
+                uint32_t spin_limit = kSpinLimit);
 int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *ws, uint32_t *status,
               cudaStream_t st, LaunchTimer *tm = nullptr);
 }  // namespace qk

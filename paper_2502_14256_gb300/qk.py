@@ -27,12 +27,13 @@ QK_COL_K1, QK_COL_P = 0, 1
 QK_MLL_QUAD, QK_MLL_LOGDET, QK_MLL_MLL, QK_MLL_MEAN, QK_MLL_VAR, QK_MLL_NOUT = range(6)
 OP_EIGS, OP_SOLVE, OP_MATVEC, OP_MLL, OP_FWHT = 0, 1, 2, 3, 4
 QK_FWHT_TWO_PASS, QK_FWHT_PERSISTENT = 0, 1
+QK_SCHED_LAUNCHES, QK_SCHED_PERSISTENT = 0, 1
 
 EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_solve", "qk_matvec", "qk_mll",
             "qk_batch_workspace_bytes", "qk_batch_plan", "qk_batch_run", "qk_workspace_bytes",
             "qk_read_status", "qk_last_error", "qk_version", "qk_fwht", "qk_fftbr", "qk_ifftbr",
             "qk_launch_count", "qk_eigs_static", "qk_batch_timing", "qk_batch_kernel_ms", "qk_fwht_ws",
-            "qk_fwht_tune", "qk_fwht_wait_selftest", "qk_batch_run_host"]
+            "qk_fwht_tune", "qk_fwht_wait_selftest", "qk_batch_run_host", "qk_batch_schedule"]
 
 
 class QKError(RuntimeError):
@@ -97,6 +98,7 @@ def _load():
         "qk_fwht_tune": [u32, u64, i32, P, P, sz, C.POINTER(FwhtPlan), P],
         "qk_fwht_wait_selftest": [u32, u64, i32, P, P, sz, u32, P, P],
         "qk_batch_run_host": [P, sz, C.POINTER(HostIO), u32, P, P],
+        "qk_batch_schedule": [P, sz, i32, u32],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -323,6 +325,11 @@ def batch_plan(tasks, dtype: torch.dtype, refine_steps: int, ws, stream=None):
 
 def batch_run(ws, status=None, stream=None):
     _check(LIB.qk_batch_run(_ptr(ws), ws.numel(), _ptr(status), _stream(stream)))
+
+
+def batch_schedule(ws, mode: int, lag: int = 0):
+    """Choose how batch_run executes the recorded plan (QK_SCHED_LAUNCHES / QK_SCHED_PERSISTENT)."""
+    _check(LIB.qk_batch_schedule(_ptr(ws), ws.numel(), mode, lag))
 
 
 def batch_run_host(ws, host_io, chunk_r: int, status=None, stream=None):

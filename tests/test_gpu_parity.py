@@ -531,3 +531,49 @@ def test_batch_run_host_matches_device_run(qk, chunk_r):
         qk.read_status(status)
         for k in ("c", "lam", "out", "grad"):
             assert torch.equal(host[k], ref[k].cpu()), (k, dtype, chunk_r)
+
+
+@pytest.mark.parametrize("dtype,refine,lag", [(torch.float32, 1, 1), (torch.float32, 0, 2), (torch.float64, 0, 1)])
+def test_persistent_schedule_matches_launch_sequence(qk, dtype, refine, lag):
+    """QK_SCHED_PERSISTENT (one launch, ticket-ordered unit phases, slot reuse) gives the
+    launch sequence's results bit for bit, on uneven n (three tasks, m = 14, 16, 15) with
+    several right-hand sides, also when captured in a CUDA graph and replayed."""
+    from paper_2502_14256_gb300 import inputs
+    from tests import qkworkloads as W
+    wl = inputs.workload("batch")
+    insts = [W.build_instance(qk, wl, m, R, 3, seed_shift=i) for i, (m, R) in enumerate([(14, 5), (16, 3), (15, 4)])]
+    tasks, bufs = zip(*[W.outputs(qk, inst, dtype, with_lam=(i != 1)) for i, inst in enumerate(insts)])
+    ws = qk.workspace(qk.batch_workspace_bytes(list(tasks), dtype))
+    qk.batch_plan(list(tasks), dtype, refine, ws)
+    status = torch.zeros(1, dtype=torch.int32, device=qc.dev())
+    qk.batch_run(ws, status)
+    torch.cuda.synchronize()
+    qk.read_status(status)
+    ref = [{k: v.clone() for k, v in b.items() if v is not None} for b in bufs]
+    for b in bufs:
+        for k, v in b.items():
+            if v is not None and k != "y":
+                v.fill_(float("nan"))
+    qk.batch_schedule(ws, qk.QK_SCHED_PERSISTENT, lag)
+    qk.batch_run(ws, status)
+    torch.cuda.synchronize()
+    qk.read_status(status)
+    for i, b in enumerate(bufs):
+        for k in ("c", "lam", "out", "grad"):
+            if b[k] is not None:
+                assert torch.equal(b[k], ref[i][k]), (i, k)
+    # graph capture and replay of the single launch
+    for b in bufs:
+        for k, v in b.items():
+            if v is not None and k != "y":
+                v.zero_()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            qk.batch_run(ws, status, stream=s)
+    g.replay()
+    torch.cuda.synchronize()
+    qk.read_status(status)
+    for i, b in enumerate(bufs):
+        assert torch.equal(b["out"], ref[i]["out"]) and torch.equal(b["grad"], ref[i]["grad"])
