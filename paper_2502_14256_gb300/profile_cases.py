@@ -2,7 +2,7 @@
 under a profiler (ncu -k <kernel> -c <n>) with inputs sized like the benchmark workload.
 
     python -m paper_2502_14256_gb300.profile_cases fwht  --m 20 --R 64 [--two-pass]
-    python -m paper_2502_14256_gb300.profile_cases fused --m 20 --R 8  [--refine 0|1] [--fp64]
+    python -m paper_2502_14256_gb300.profile_cases fused --m 20 --R 8  [--refine 0|1] [--fp64] [--persistent]
 
 `fwht` transforms R vectors of 2^m FP32 values in place (qk_fwht_ws, persistent plan with
 the default lag unless --two-pass); `fused` runs the batched solve + MLL + gradient
@@ -49,6 +49,8 @@ def _fused(args):
     task = qk.Task(ps, kern, args.m, 1, wl.eta, y.data_ptr(), c.data_ptr(), None, out.data_ptr(), grad.data_ptr())
     ws = qk.workspace(qk.batch_workspace_bytes([task], dt))
     qk.batch_plan([task], dt, args.refine, ws)
+    if args.persistent:
+        qk.batch_schedule(ws, qk.QK_SCHED_PERSISTENT, 1)
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
     for _ in range(1 + args.reps):
         qk.batch_run(ws, status)
@@ -65,6 +67,7 @@ def main(argv=None):
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--fp64", action="store_true")
     ap.add_argument("--two-pass", action="store_true")
+    ap.add_argument("--persistent", action="store_true", help="fused: one persistent launch")
     args = ap.parse_args(argv)
     (_fwht if args.case == "fwht" else _fused)(args)
     print("ok")
