@@ -141,6 +141,12 @@ QK_API int qk_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64
 QK_API int qk_kernel_col(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr,
                   uint32_t m, int32_t dtype, int32_t form, void *col, qk_stream stream);
 
+/* qk_kernel_col for the 2^m points at positions i0 .. i0 + 2^m - 1 of the same
+ * sequence (i0 a multiple of 2048): e.g. the new half of an extended point set, for
+ * qk_eigs_extend.  col: (nr, 2^m) in dtype and form. */
+QK_API int qk_kernel_col_at(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr, uint64_t i0,
+                            uint32_t m, int32_t dtype, int32_t form, void *col, qk_stream stream);
+
 /* ------------------------------------------------------------- spectrum --- */
 
 /* Eigenvalues lambda = sqrt(n) conj(V) k_1 + eta (Sec. 5.4) of `batch` Gram
@@ -170,6 +176,21 @@ QK_API int qk_eigs(int32_t family, uint32_t m, uint32_t batch, int32_t dtype, in
 QK_API int qk_eigs_static(int32_t family, uint32_t m, uint32_t batch, int32_t dtype, int32_t form,
                           const void *col, double zeta, double eta, double *lam, uint32_t *status,
                           qk_stream stream);
+
+/* Doubling update of the eigenvalues (Sec. 5.4, efficient eigenvalue updates): for a
+ * point set extended from n = 2^m to 2n points (its first n points being the n-point
+ * set: nets in natural or Gray order, lattices in natural order), the eigenvalues of the
+ * 2n-point Gram matrix from those of the n-point matrix and the first-column entries of
+ * the n new points only:
+ *   lambda' = [lambda + w (.) t, lambda - w (.) t],  t = sqrt(n) conj(V_m) k_new,
+ * w_k = 1 (nets) or exp(-pi i k / n) (lattices); one transform of length n instead of 2n.
+ * lam_old: (batch, n) doubles from qk_eigs (nugget included); col_new: (batch, n) in
+ * dtype and form (qk_kernel_col_at with i0 = n); lam: (batch, 2n) doubles, must not
+ * overlap lam_old.  The floor / sign tests of qk_eigs apply to the result.
+ * Workspace: qk_workspace_bytes op 0 with (family, m, batch). */
+QK_API int qk_eigs_extend(int32_t family, uint32_t m, uint32_t batch, int32_t dtype, int32_t form,
+                          const void *col_new, double zeta, double eta, const double *lam_old, double *lam,
+                          void *ws, size_t ws_bytes, uint32_t *status, qk_stream stream);
 
 /* Solve K c = y for `batch` Gram matrices and nrhs right-hand sides each:
  * c = V (y~ / lambda), y~ = conj(V) y (Sec. 5.4).  y, c: (batch, nrhs, n) in
@@ -210,6 +231,17 @@ QK_API int qk_mll(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32
 QK_API int qk_fwht(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_stream stream);
 QK_API int qk_fftbr(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_stream stream);
 QK_API int qk_ifftbr(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_stream stream);
+
+/* Doubling update of transformed data (Sec. 5.4): from xt_old = the transform of the
+ * first n = 2^m values of each vector (as qk_fwht / qk_fftbr return it) and x_new = its
+ * next n values (raw; transformed in place here), out = the transform of all 2n values:
+ *   out = [xt_old + w (.) xt_new, xt_old - w (.) xt_new] / sqrt(2),
+ * w_k = 1 (qk_fwht_extend) or exp(-pi i k / n) (qk_fftbr_extend; interleaved complex).
+ * xt_old, x_new: (nvec, n); out: (nvec, 2n); out must not overlap the inputs. */
+QK_API int qk_fwht_extend(uint32_t m, uint64_t nvec, int32_t dtype, const void *xt_old, void *x_new, void *out,
+                          qk_stream stream);
+QK_API int qk_fftbr_extend(uint32_t m, uint64_t nvec, int32_t dtype, const void *xt_old, void *x_new, void *out,
+                           qk_stream stream);
 
 /* qk_fwht with a workspace: the same transform (bit for bit: the same butterflies in the
  * same order), for 2^13 < n <= 2^21 (FP32) or 2^12 < n <= 2^20 (FP64) run either as two

@@ -486,6 +486,37 @@ def inverse_transform(family, yt) -> np.ndarray:
     return to_natural_order(np.fft.ifft(yt, axis=-1) * math.sqrt(n), m).real
 
 
+def update_weights(family, m: int) -> np.ndarray:
+    """Weights w_m of the doubling update (Sec. 5.4): all ones for the Hadamard matrix
+    (nets), exp(-pi i k / 2^m) for the bit-reversed Fourier matrix (lattices)."""
+    n = 1 << m
+    if family == "dsi":
+        return np.ones(n)
+    return np.exp(-1j * np.pi * np.arange(n) / n)
+
+
+def extend_transformed(family, yt_old, yt_new):
+    """conj(V_{m+1}) [y; y_new] from yt_old = conj(V_m) y and yt_new = conj(V_m) y_new
+    (Sec. 5.4 update; the weights multiply the new half):
+    [yt_old + w yt_new, yt_old - w yt_new] / sqrt(2)."""
+    yt_old = np.asarray(yt_old)
+    m = yt_old.shape[-1].bit_length() - 1
+    wy = update_weights(family, m) * np.asarray(yt_new)
+    return np.concatenate([yt_old + wy, yt_old - wy], axis=-1) / math.sqrt(2.0)
+
+
+def extend_eigenvalues(family, lam_old, k1_new):
+    """Eigenvalues of the doubled Gram matrix from lam_old (those of the first n points,
+    nugget included) and the first-column entries k1_new of the n new points: with
+    t = sqrt(n) conj(V_m) k1_new, lam' = [lam_old + w t, lam_old - w t] (real)."""
+    k1_new = np.asarray(k1_new, dtype=np.float64)
+    n = k1_new.shape[-1]
+    m = n.bit_length() - 1
+    t = forward_transform(family, k1_new) * math.sqrt(n)
+    wt = (update_weights(family, m) * t).real
+    return np.concatenate([lam_old + wt, lam_old - wt], axis=-1)
+
+
 def spectral_solve(family, lam, y):
     """K^-1 y = V (y~ / lambda) (Sec. 5.4)."""
     return inverse_transform(family, forward_transform(family, y) / lam)

@@ -171,6 +171,64 @@ int qk_kernel_col(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32
   return launch_kernel_col(make_job(ps, k, r0, nr, m), dtype, form, col, (cudaStream_t)stream);
 }
 
+int qk_kernel_col_at(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr, uint64_t i0, uint32_t m,
+                     int32_t dtype, int32_t form, void *col, qk_stream stream) {
+  g_err[0] = 0;
+  QK_TRY(check_pointset(ps, r0, nr));
+  QK_TRY(check_kernel(k, ps));
+  QK_TRY(check_dtype(dtype));
+  QK_TRY(check_m(m));
+  if (form != QK_COL_K1 && form != QK_COL_P) return fail(QK_EINVAL, "form must be QK_COL_K1 or QK_COL_P");
+  if (i0 % 2048 != 0) return fail(QK_EINVAL, "qk_kernel_col_at: i0 = %llu is not a multiple of 2048", (unsigned long long)i0);
+  if (i0 + (1ull << m) > (1ull << 32)) return fail(QK_EINVAL, "qk_kernel_col_at: positions beyond 2^32");
+  if (!col && nr) return fail(QK_EINVAL, "qk_kernel_col_at: output is NULL");
+  ColJob job = make_job(ps, k, r0, nr, m);
+  job.i0 = i0;
+  return launch_kernel_col(job, dtype, form, col, (cudaStream_t)stream);
+}
+
+int qk_eigs_extend(int32_t family, uint32_t m, uint32_t batch, int32_t dtype, int32_t form, const void *col_new,
+                   double zeta, double eta, const double *lam_old, double *lam, void *ws, size_t ws_bytes,
+                   uint32_t *status, qk_stream stream) {
+  g_err[0] = 0;
+  QK_TRY(check_family(family));
+  QK_TRY(check_dtype(dtype));
+  QK_TRY(check_m(m));
+  if (m + 1 > QK_MAX_M) return fail(QK_EINVAL, "qk_eigs_extend: 2^(m+1) exceeds 2^%d", QK_MAX_M);
+  if (form != QK_COL_K1 && form != QK_COL_P) return fail(QK_EINVAL, "form must be QK_COL_K1 or QK_COL_P");
+  if (batch == 0) return QK_OK;
+  if (!col_new || !lam_old || !lam) return fail(QK_EINVAL, "qk_eigs_extend: NULL array");
+  if (!(zeta > 0.0)) return fail(QK_EINVAL, "zeta must be > 0");
+  const uint64_t n = 1ull << m;
+  const double *lo = lam_old, *hi = lam_old + (uint64_t)batch * n;
+  if (!(lam + ((uint64_t)batch << (m + 1)) <= lo || lam >= hi))
+    return fail(QK_EINVAL, "qk_eigs_extend: lam must not overlap lam_old");
+  QK_TRY(check_ws(ws, ws_bytes, ws_eigs(family, m, batch, dtype)));
+  return op_eigs_extend(family, m, batch, dtype, form, col_new, zeta, eta, lam_old, lam, ws, status,
+                        (cudaStream_t)stream);
+}
+
+static int transform_extend_entry(int kind, uint32_t m, uint64_t nvec, int32_t dtype, const void *xt_old, void *x_new,
+                                  void *out, qk_stream stream) {
+  g_err[0] = 0;
+  QK_TRY(check_dtype(dtype));
+  QK_TRY(check_m(m));
+  if (m + 1 > QK_MAX_M) return fail(QK_EINVAL, "2^(m+1) exceeds 2^%d", QK_MAX_M);
+  if (nvec == 0) return QK_OK;
+  if (!xt_old || !x_new || !out) return fail(QK_EINVAL, "transform extension: NULL array");
+  return op_transform_extend(kind, m, nvec, dtype, xt_old, x_new, out, (cudaStream_t)stream);
+}
+
+int qk_fwht_extend(uint32_t m, uint64_t nvec, int32_t dtype, const void *xt_old, void *x_new, void *out,
+                   qk_stream stream) {
+  return transform_extend_entry(0, m, nvec, dtype, xt_old, x_new, out, stream);
+}
+
+int qk_fftbr_extend(uint32_t m, uint64_t nvec, int32_t dtype, const void *xt_old, void *x_new, void *out,
+                    qk_stream stream) {
+  return transform_extend_entry(1, m, nvec, dtype, xt_old, x_new, out, stream);
+}
+
 int qk_workspace_bytes(int32_t op, int32_t family, uint32_t m, uint32_t batch, uint32_t nrhs, int32_t dtype,
                        uint32_t d, size_t *bytes) {
   g_err[0] = 0;

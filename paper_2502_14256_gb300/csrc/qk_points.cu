@@ -110,7 +110,9 @@ __global__ void __launch_bounds__(kNT) k_kernel_col(ColJob job, int form, T *__r
   T *wT = reinterpret_cast<T *>(wd);
   const uint32_t rl = blockIdx.y;
   const uint64_t n = 1ull << job.m;
-  const uint64_t tile_base = (uint64_t)blockIdx.x * kTile;
+  // positions job.i0 + [0, n); job.i0 is a multiple of kTile, so position bits split into
+  // disjoint tile, l, warp and lane fields for the XOR tables
+  const uint64_t tile_base = job.i0 + (uint64_t)blockIdx.x * kTile;
   for (uint32_t q = threadIdx.x; q < job.d; q += kNT) wT[q] = (T)job.w[q];
   build_all<T, FAM, ALPHA, kL>(job, job.Ct ? job.Ct + (size_t)rl * job.d * 32 : nullptr, job.g, tile_base, tb);
   __syncthreads();
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(kNT) k_kernel_col(ColJob job, int form, T *__r
   const T zeta = (T)job.zeta;
 #pragma unroll
   for (int l = 0; l < kL; ++l) {
-    const uint64_t i = tile_base + threadIdx.x + ((uint64_t)l << 8);
+    const uint64_t i = tile_base - job.i0 + threadIdx.x + ((uint64_t)l << 8);
     if (i < n) out[(size_t)rl * n + i] = form == QK_COL_P ? p[l] : zeta * (T(1) + p[l]);
   }
 }

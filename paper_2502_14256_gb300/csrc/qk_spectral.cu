@@ -278,6 +278,129 @@ static int eigs_t(int family, uint32_t m, uint32_t batch, int form, const void *
   return check_launch("eigs finalize");
 }
 
+// ------------------------------------------------ doubling updates (Sec. 5.4)
+// With 2n = 2^(m+1) points whose first n are the n-point set, the transform of the
+// doubled set splits into the transforms of the two halves:
+//   conj(V_{m+1}) [a; b] = [conj(V_m) a + w (.) conj(V_m) b; conj(V_m) a - w (.) conj(V_m) b] / sqrt(2)
+// with w_k = 1 (Hadamard, nets) or exp(-pi i k / n) (bit-reversed Fourier, lattices).
+
+// Imaginary and real parts of w_k times a value (nets: w = 1).
+template <typename E> struct Twid {
+  static __device__ __forceinline__ void apply(E v, int, uint64_t, double &r, double &i) {
+    r = (double)v;
+    i = 0.0;
+  }
+};
+template <> struct Twid<float2> {
+  static __device__ __forceinline__ void apply(float2 v, int m, uint64_t k, double &r, double &i) {
+    double s, c;
+    sincospi(-(double)k / (double)(1ull << m), &s, &c);
+    r = c * v.x - s * v.y;
+    i = s * v.x + c * v.y;
+  }
+};
+template <> struct Twid<double2> {
+  static __device__ __forceinline__ void apply(double2 v, int m, uint64_t k, double &r, double &i) {
+    double s, c;
+    sincospi(-(double)k / (double)(1ull << m), &s, &c);
+    r = c * v.x - s * v.y;
+    i = s * v.x + c * v.y;
+  }
+};
+
+// lambda' = [lambda + w (.) t, lambda - w (.) t] with t = zmul X (+ dc at k = 0) the
+// unnormalised transform of the new half of the first column; the result is real.  The
+// eigenvalue floor and sign test of k_lam_final apply to lambda'.
+template <typename E>
+__global__ void k_lam_extend(const E *__restrict__ X, const double *__restrict__ lam_old, double *__restrict__ lam,
+                             uint64_t total, int m, double zmul, double dc, double eta, uint32_t *status) {
+  bool bad = false, floored = false;
+  const uint64_t mask = (1ull << m) - 1;
+  for (uint64_t i = gtid(); i < total; i += gstride()) {
+    const uint64_t b = i >> m, k = i & mask;
+    double tr, ti;
+    Twid<E>::apply(X[i], m, k, tr, ti);
+    tr = zmul * tr + (k == 0 ? dc : 0.0);
+    const double a = lam_old[i];
+    double v[2] = {a + tr, a - tr};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (eta > 0.0 && !(v[h] >= eta)) {
+        v[h] = eta;
+        floored = true;
+      }
+      bad |= !(v[h] > 0.0);
+      lam[(b << (m + 1)) + ((uint64_t)h << m) + k] = v[h];
+    }
+  }
+  if (bad && status) atomicOr(status, (uint32_t)QK_STATUS_NOTPD);
+  if (floored && status) atomicOr(status, (uint32_t)QK_STATUS_FLOOR);
+}
+
+template <typename T, typename E>
+static int eigs_extend_t(int family, uint32_t m, uint32_t batch, int form, const void *col_new, double zeta,
+                         double eta, const double *lam_old, double *lam, void *ws, uint32_t *status, cudaStream_t st) {
+  const uint64_t cnt = (uint64_t)batch << m;
+  E *X = (E *)ws;
+  k_load_real<T, E><<<grid_for(cnt), 256, 0, st>>>((const T *)col_new, X, cnt);
+  int rc = check_launch("eigs extend load");
+  if (rc) return rc;
+  if ((rc = fwd<E>(family, X, m, batch, st))) return rc;
+  const double zmul = form == QK_COL_P ? zeta : 1.0;
+  const double dc = form == QK_COL_P ? zeta * (double)(1ull << m) : 0.0;
+  k_lam_extend<E><<<grid_for(cnt), 256, 0, st>>>(X, lam_old, lam, cnt, (int)m, zmul, dc, eta, status);
+  return check_launch("eigs extend");
+}
+
+int op_eigs_extend(int family, uint32_t m, uint32_t batch, int dtype, int form, const void *col_new, double zeta,
+                   double eta, const double *lam_old, double *lam, void *ws, uint32_t *status, cudaStream_t st) {
+  if (family == QK_DSI)
+    return dtype == QK_F64 ? eigs_extend_t<double, double>(family, m, batch, form, col_new, zeta, eta, lam_old, lam, ws, status, st)
+                           : eigs_extend_t<float, float>(family, m, batch, form, col_new, zeta, eta, lam_old, lam, ws, status, st);
+  return dtype == QK_F64 ? eigs_extend_t<double, double2>(family, m, batch, form, col_new, zeta, eta, lam_old, lam, ws, status, st)
+                         : eigs_extend_t<float, float2>(family, m, batch, form, col_new, zeta, eta, lam_old, lam, ws, status, st);
+}
+
+// out = [xt_old + w (.) xt_new, xt_old - w (.) xt_new] / sqrt(2) per vector (normalised transforms).
+template <typename E>
+__global__ void k_xform_extend(const E *__restrict__ xt_old, const E *__restrict__ xt_new, E *__restrict__ out,
+                               uint64_t total, int m) {
+  const uint64_t mask = (1ull << m) - 1;
+  const double r2 = 0.70710678118654752440;
+  for (uint64_t i = gtid(); i < total; i += gstride()) {
+    const uint64_t b = i >> m, k = i & mask;
+    double tr, ti;
+    Twid<E>::apply(xt_new[i], m, k, tr, ti);
+    const E a = xt_old[i];
+    E lo, hi;
+    if constexpr (IsCplx<E>::value) {
+      using S = decltype(a.x);
+      lo.x = (S)(((double)a.x + tr) * r2), lo.y = (S)(((double)a.y + ti) * r2);
+      hi.x = (S)(((double)a.x - tr) * r2), hi.y = (S)(((double)a.y - ti) * r2);
+    } else {
+      lo = (E)(((double)a + tr) * r2);
+      hi = (E)(((double)a - tr) * r2);
+    }
+    out[(b << (m + 1)) + k] = lo;
+    out[(b << (m + 1)) + (1ull << m) + k] = hi;
+  }
+}
+
+int op_transform_extend(int kind, uint32_t m, uint64_t nvec, int dtype, const void *xt_old, void *x_new, void *out,
+                        cudaStream_t st) {
+  int rc = op_transform(kind, m, nvec, dtype, x_new, st);  // normalised forward transform of the new half
+  if (rc) return rc;
+  const uint64_t cnt = nvec << m;
+  if (kind == XF_WHT) {
+    if (dtype == QK_F64) k_xform_extend<double><<<grid_for(cnt), 256, 0, st>>>((const double *)xt_old, (const double *)x_new, (double *)out, cnt, (int)m);
+    else k_xform_extend<float><<<grid_for(cnt), 256, 0, st>>>((const float *)xt_old, (const float *)x_new, (float *)out, cnt, (int)m);
+  } else {
+    if (dtype == QK_F64) k_xform_extend<double2><<<grid_for(cnt), 256, 0, st>>>((const double2 *)xt_old, (const double2 *)x_new, (double2 *)out, cnt, (int)m);
+    else k_xform_extend<float2><<<grid_for(cnt), 256, 0, st>>>((const float2 *)xt_old, (const float2 *)x_new, (float2 *)out, cnt, (int)m);
+  }
+  return check_launch("transform extend");
+}
+
 int op_eigs(int family, uint32_t m, uint32_t batch, int dtype, int form, const void *col, double zeta, double eta,
             double *lam, void *ws, uint32_t *status, cudaStream_t st) {
   if (family == QK_DSI)

@@ -33,7 +33,8 @@ EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_sol
             "qk_batch_workspace_bytes", "qk_batch_plan", "qk_batch_run", "qk_workspace_bytes",
             "qk_read_status", "qk_last_error", "qk_version", "qk_fwht", "qk_fftbr", "qk_ifftbr",
             "qk_launch_count", "qk_eigs_static", "qk_batch_timing", "qk_batch_kernel_ms", "qk_fwht_ws",
-            "qk_fwht_tune", "qk_fwht_wait_selftest", "qk_batch_run_host", "qk_batch_schedule"]
+            "qk_fwht_tune", "qk_fwht_wait_selftest", "qk_batch_run_host", "qk_batch_schedule",
+            "qk_kernel_col_at", "qk_eigs_extend", "qk_fwht_extend", "qk_fftbr_extend"]
 
 
 class QKError(RuntimeError):
@@ -99,6 +100,10 @@ def _load():
         "qk_fwht_wait_selftest": [u32, u64, i32, P, P, sz, u32, P, P],
         "qk_batch_run_host": [P, sz, C.POINTER(HostIO), u32, P, P],
         "qk_batch_schedule": [P, sz, i32, u32],
+        "qk_kernel_col_at": [C.POINTER(PointSet), C.POINTER(Kernel), u32, u32, u64, u32, i32, i32, P, P],
+        "qk_eigs_extend": [i32, u32, u32, i32, i32, P, dbl, dbl, P, P, P, sz, P, P],
+        "qk_fwht_extend": [u32, u64, i32, P, P, P, P],
+        "qk_fftbr_extend": [u32, u64, i32, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -170,6 +175,37 @@ def kernel_col(ps: PointSet, k: Kernel, r0: int, nr: int, m: int, col, form: int
     _check(LIB.qk_kernel_col(C.byref(ps), C.byref(k), r0, nr, m, dtype_code(col.dtype), form, _ptr(col),
                              _stream(stream)))
     return col
+
+
+def kernel_col_at(ps: PointSet, k: Kernel, r0: int, nr: int, i0: int, m: int, col, form: int = QK_COL_K1,
+                  stream=None):
+    """First-column entries of the 2^m points at positions i0 .. i0 + 2^m - 1."""
+    _check(LIB.qk_kernel_col_at(C.byref(ps), C.byref(k), r0, nr, i0, m, dtype_code(col.dtype), form, _ptr(col),
+                                _stream(stream)))
+    return col
+
+
+def eigs_extend(family: int, m: int, col_new, lam_old, lam, zeta: float = 1.0, eta: float = 0.0,
+                form: int = QK_COL_K1, ws=None, status=None, stream=None):
+    """Eigenvalues of the doubled point set (2^(m+1) points) from those of the first 2^m."""
+    batch = col_new.numel() >> m
+    if ws is None:
+        ws = workspace(workspace_bytes(OP_EIGS, family, m, batch, 1, col_new.dtype), col_new.device)
+    _check(LIB.qk_eigs_extend(family, m, batch, dtype_code(col_new.dtype), form, _ptr(col_new), zeta, eta,
+                              _ptr(lam_old), _ptr(lam), _ptr(ws), ws.numel(), _ptr(status), _stream(stream)))
+    return lam
+
+
+def fwht_extend(m: int, xt_old, x_new, out, stream=None):
+    _check(LIB.qk_fwht_extend(m, _nvec_m(xt_old, m, False), dtype_code(xt_old.dtype), _ptr(xt_old), _ptr(x_new),
+                              _ptr(out), _stream(stream)))
+    return out
+
+
+def fftbr_extend(m: int, xt_old, x_new, out, stream=None):
+    _check(LIB.qk_fftbr_extend(m, _nvec_m(xt_old, m, True), dtype_code(xt_old.dtype), _ptr(xt_old), _ptr(x_new),
+                               _ptr(out), _stream(stream)))
+    return out
 
 
 def workspace_bytes(op: int, family: int, m: int, batch: int, nrhs: int, dtype: torch.dtype, d: int = 0) -> int:

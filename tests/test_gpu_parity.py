@@ -577,3 +577,66 @@ def test_persistent_schedule_matches_launch_sequence(qk, dtype, refine, lag):
     qk.read_status(status)
     for i, b in enumerate(bufs):
         assert torch.equal(b["out"], ref[i]["out"]) and torch.equal(b["grad"], ref[i]["grad"])
+
+
+DOUBLING_CASES = [("net", "dsi", 2, "gray"), ("net", "dsi", 4, "natural"), ("lattice", "si", 2, "natural")]
+
+
+@pytest.mark.parametrize("kind,family,alpha,order", DOUBLING_CASES)
+def test_doubling_update_of_eigenvalues_and_transforms(qk, kind, family, alpha, order):
+    """Sec. 5.4 doubling updates: the column of the n new points (qk_kernel_col_at) equals
+    the second half of the 2n-point column bit for bit; qk_eigs_extend equals qk_eigs of
+    the 2n column (and the oracle's update); qk_fwht_extend / qk_fftbr_extend equal the
+    transform of the doubled vectors."""
+    m, d, R = 11, 5, 2
+    n = 1 << m
+    case = qc.make_case(kind, family, alpha, d, R, seed=41, order=order, m_gen=20)
+    kern = qc.kernel_of(case)
+    fam = qk.QK_DSI if family == "dsi" else qk.QK_SI
+    eta = 1e-6
+    for dtype, tol in ((F64, 1e-12), (torch.float32, 2e-6)):
+        for form in (qk.QK_COL_K1, qk.QK_COL_P):
+            full = torch.empty((R, 2 * n), dtype=dtype, device=qc.dev())
+            qk.kernel_col(case.ps, kern, 0, R, m + 1, full, form=form)
+            old = torch.empty((R, n), dtype=dtype, device=qc.dev())
+            qk.kernel_col(case.ps, kern, 0, R, m, old, form=form)
+            new = torch.empty((R, n), dtype=dtype, device=qc.dev())
+            qk.kernel_col_at(case.ps, kern, 0, R, n, m, new, form=form)
+            assert torch.equal(old, full[:, :n]) and torch.equal(new, full[:, n:])
+            status = torch.zeros(1, dtype=torch.int32, device=qc.dev())
+            lam_old = torch.empty((R, n), dtype=F64, device=qc.dev())
+            qk.eigs(fam, m, old, lam_old, eta=eta, form=form, status=status)
+            lam_ext = torch.empty((R, 2 * n), dtype=F64, device=qc.dev())
+            qk.eigs_extend(fam, m, new, lam_old, lam_ext, eta=eta, form=form, status=status)
+            lam_full = torch.empty((R, 2 * n), dtype=F64, device=qc.dev())
+            qk.eigs(fam, m + 1, full, lam_full, eta=eta, form=form, status=status)
+            torch.cuda.synchronize()
+            if dtype == F64:
+                qk.read_status(status)
+            else:
+                status.zero_()
+            assert qc.rel_err(lam_ext.cpu().numpy(), lam_full.cpu().numpy()) < tol, (dtype, form)
+    # against the oracle's update on the oracle's own column (FP64)
+    k2, _ = case.k1_ref(1, m + 1)
+    lam1 = o.eigenvalues(family, k2[:n], eta)
+    want = o.extend_eigenvalues(family, lam1, k2[n:])
+    new = torch.from_numpy(np.ascontiguousarray(k2[n:])).to(qc.dev()).reshape(1, n)
+    lam_old = torch.from_numpy(lam1).to(qc.dev()).reshape(1, n)
+    got = torch.empty((1, 2 * n), dtype=F64, device=qc.dev())
+    qk.eigs_extend(fam, m, new, lam_old, got, eta=eta)
+    assert qc.rel_err(got.cpu().numpy()[0], want) < 1e-13
+    # transforms of doubled vectors
+    g = torch.Generator(device=qc.dev()).manual_seed(3)
+    cplx = family == "si"
+    width = 2 if cplx else 1
+    for dtype, tol in ((F64, 1e-13), (torch.float32, 1e-6)):
+        y = torch.randn((3, 2 * n * width), dtype=dtype, device=qc.dev(), generator=g)
+        ref = y.clone()
+        (qk.fftbr if cplx else qk.fwht)(m + 1, ref)
+        halves = y.view(3, 2, n * width)
+        xt_old = halves[:, 0].contiguous()
+        (qk.fftbr if cplx else qk.fwht)(m, xt_old)
+        x_new = halves[:, 1].contiguous()
+        out = torch.empty_like(y)
+        (qk.fftbr_extend if cplx else qk.fwht_extend)(m, xt_old, x_new, out)
+        assert qc.rel_err(out.cpu().numpy(), ref.cpu().numpy()) < tol, dtype

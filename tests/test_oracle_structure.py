@@ -215,3 +215,44 @@ def test_scale_zeta_enters_posterior_as_in_the_dense_definition(family):
     assert abs(sp["post_mean"] - mean_ref) < 1e-10 * max(1.0, abs(mean_ref))
     assert abs(sp["post_var"] - var_ref) < 1e-9
     assert abs(var_ref) > 1e-6
+
+
+@pytest.mark.parametrize("family", ["dsi", "si"])
+def test_doubling_update_of_transformed_data(family):
+    """Sec. 5.4 update: the transform of [y; y_new] from the transforms of its halves."""
+    rng = np.random.default_rng(5)
+    m = 6
+    n = 1 << m
+    y = rng.standard_normal((3, 2 * n))
+    full = o.forward_transform(family, y)
+    ext = o.extend_transformed(family, o.forward_transform(family, y[:, :n]), o.forward_transform(family, y[:, n:]))
+    assert np.allclose(ext, full, rtol=0, atol=1e-13)
+    # the weights belong to the new half: putting them on the old half is wrong
+    w = o.update_weights(family, m)
+    if family == "si":
+        a, b = o.forward_transform(family, y[:, :n]), o.forward_transform(family, y[:, n:])
+        wrong = np.concatenate([w * a + b, w * a - b], axis=-1) / math.sqrt(2)
+        assert not np.allclose(wrong, full, atol=1e-6)
+
+
+@pytest.mark.parametrize("family,order", [("dsi", "natural"), ("dsi", "gray"), ("si", "natural")])
+def test_doubling_update_of_eigenvalues(family, order):
+    """Eigenvalues of the 2n-point Gram matrix from those of the first n points and the
+    column entries of the n new points, against the dense 2n-point matrix."""
+    m, d = 6, 3
+    n = 1 << m
+    c = np.array([1.0, 0.5, 0.25])
+    alpha, eta = (2, 1e-3) if family == "dsi" else (1, 1e-3)
+    if family == "dsi":
+        X2, X1 = _net_points(m + 1, d, order, seed=31), _net_points(m, d, order, seed=31)
+    else:
+        lat = inputs.make_lattice(33, d, 1, 12)
+        X2 = o.lattice_points(lat.g, lat.D[0], np.arange(2 * n))
+        X1 = o.lattice_points(lat.g, lat.D[0], np.arange(n))
+    assert np.array_equal(X2[:n], X1)  # the first n points of the doubled set are the n-point set
+    k2 = o.first_column(family, alpha, X2, c)
+    lam1 = o.eigenvalues(family, o.first_column(family, alpha, X1, c), eta)
+    ext = o.extend_eigenvalues(family, lam1, k2[n:])
+    assert np.allclose(ext, o.eigenvalues(family, k2, eta), rtol=0, atol=1e-12 * np.abs(ext).max())
+    K2 = o.gram_dense(family, alpha, X2, c, eta=eta)
+    assert np.allclose(np.sort(ext), np.linalg.eigvalsh(K2), rtol=1e-10, atol=1e-10)
