@@ -313,6 +313,32 @@ def main():
     stage = {}
     stage["kernel_col"] = time_steps(torch, lambda: q.kernel_col(W["ps"], kern, 0, R, m, col, form=q.QK_COL_P),
                                      3, 1, stream)
+    # doubling update (extensible n): eigenvalues of the 2^m-point sets from those of their
+    # first 2^(m-1) points plus the new half's column and one half-length transform,
+    # against computing the full column and transform
+    lam_full = torch.empty((R, n), dtype=torch.float64, device=dev)
+    lam_half = torch.empty((R, n // 2), dtype=torch.float64, device=dev)
+    col_half = torch.empty((R, n // 2), dtype=torch.float32, device=dev)
+    ws_e = q.workspace(q.workspace_bytes(q.OP_EIGS, q.QK_DSI, m, R, 1, torch.float32), dev)
+    eta_ = W["wl"].eta
+
+    def eig_full():
+        q.kernel_col(W["ps"], kern, 0, R, m, col, form=q.QK_COL_P)
+        q.eigs(q.QK_DSI, m, col, lam_full, zeta=W["wl"].zeta, eta=eta_, form=q.QK_COL_P, ws=ws_e)
+
+    q.kernel_col(W["ps"], kern, 0, R, m - 1, col_half, form=q.QK_COL_P)
+    q.eigs(q.QK_DSI, m - 1, col_half, lam_half, zeta=W["wl"].zeta, eta=eta_, form=q.QK_COL_P, ws=ws_e)
+
+    def eig_extend():
+        q.kernel_col_at(W["ps"], kern, 0, R, n // 2, m - 1, col_half, form=q.QK_COL_P)
+        q.eigs_extend(q.QK_DSI, m - 1, col_half, lam_half, lam_full, zeta=W["wl"].zeta, eta=eta_,
+                      form=q.QK_COL_P, ws=ws_e)
+
+    doubling = {"eigs_full_ms": time_steps(torch, eig_full, 3, 1, stream),
+                "eigs_extend_ms": time_steps(torch, eig_extend, 3, 1, stream),
+                "what": f"{R} x 2^{m} FP32 column + eigenvalues: from scratch vs from the first 2^{m - 1} points"}
+    del lam_full, lam_half, col_half, ws_e
+
     # FWHT alone on the same data volume (in place, FP32): HBM roofline of the transform
     xf = torch.randn((R, n), dtype=torch.float32, device=dev)
     fw_ws = q.fwht_workspace(R, dev)
@@ -395,6 +421,7 @@ def main():
             "gpu_launches_per_step": launches / max(1, args.steps),
             "fp64_plain": fp64,
             "stages_ms": stage,
+            "doubling": doubling,
             "kernels_ms_per_step": {k: v[1] / max(1, args.steps) for k, v in kernel_ms.items()},
             "fwht": {"gbs": fw_gbs, "ms": fw_ms, "frac_of_hbm": fw_gbs / hbm_peak, "bytes": fw_bytes,
                      "peak": hbm_peak, "peak_source": peak_src,
