@@ -348,6 +348,11 @@ def main():
     fw_bytes = 2 * xf.numel() * 4  # one read + one write per element (the algorithmic minimum)
     fw_gbs = fw_bytes / (fw_ms * 1e-3) / 1e9
     del xf, fw_ws
+    # FFTBR (the lattice transform) on R complex FP32 vectors of the same length
+    xc = torch.randn((R, 2 * n), dtype=torch.float32, device=dev)
+    ff_ms = time_steps(torch, lambda: q.fftbr(m, xc), args.steps, 2, stream)
+    ff_bytes = 2 * xc.numel() * 4
+    del xc
 
     # ---- plain FP64 pipeline beside it
     fp64 = None
@@ -402,7 +407,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        v, sample = oracle_sample(W, min(18, m), 1, 0)
+        v, sample = oracle_sample(W, min(18, m), 2, 0)  # ~10 s of host work
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
 
     if rank == 0:
@@ -430,6 +435,9 @@ def main():
                      # (profiles/fwht_persistent_64x2p20_fp32.md)
                      "traffic": (268.5e6 + 213.9e6) if (R, m) == (64, 20) else None,
                      "two_launch_ms": fw2_ms, "two_launch_gbs": fw_bytes / (fw2_ms * 1e-3) / 1e9},
+            "fftbr": {"gbs": ff_bytes / (ff_ms * 1e-3) / 1e9, "ms": ff_ms, "bytes": ff_bytes,
+                      "frac_of_hbm": ff_bytes / (ff_ms * 1e-3) / 1e9 / hbm_peak,
+                      "shape": f"{R} x 2^{m} complex fp32, in place, two tile passes"},
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks,
