@@ -293,7 +293,7 @@ __device__ __forceinline__ double ratio(double a, double b) { return a / b; }
 // dk1_i/dc_j = k1_i K_ij / (1 + c_j K_ij).  wk[l] = u_l k1_l; uget(l) returns u_l and
 // is called only for the rare exact zero of 1 + c_j K_ij, handled after the loop by
 // the explicit product over the other dimensions.
-template <typename T, int FAM, int ALPHA, int L, typename UF>
+template <typename T, int FAM, int ALPHA, int L, bool ALL_OK = false, typename UF>
 __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTables &tb, const T *wT,
                                                const uint32_t (&bi)[L], const T (&k1)[L], const T (&wk)[L],
                                                const bool (&ok)[L], UF uget, double *red) {
@@ -304,28 +304,25 @@ __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTabl
     T su = T(0), s1 = T(0);
     uint32_t base = 0;
     if constexpr (FAM == 0) base = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * d + j];
-    uint32_t zero_mask = 0;
+    bool anyzero = false;
 #pragma unroll
     for (int l = 0; l < L; ++l) {
       const T K = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
       const T f = fmadd(wj, K, T(1));
-      zero_mask |= (f == T(0)) ? (1u << l) : 0u;
-      const T q = ok[l] ? ratio(K, f) : T(0);
+      anyzero |= f == T(0);
+      T q = ratio(K, f);
+      if constexpr (!ALL_OK) q = ok[l] ? q : T(0);
       su = fmadd(wk[l], q, su);
       s1 = fmadd(k1[l], q, s1);
     }
-    if (zero_mask) {  // exact zeros of 1 + c_j K: use prod_{j' != j} (1 + c_j' K_j') directly
+    if (anyzero) {  // exact zeros of 1 + c_j K: use prod_{j' != j} (1 + c_j' K_j') directly
       su = T(0), s1 = T(0);
 #pragma unroll
       for (int l = 0; l < L; ++l) {
         if (!ok[l]) continue;
-        T dk;
-        if (zero_mask & (1u << l)) {
-          dk = dk_explicit<T, FAM, ALPHA, L>(job, tb, wT, bi[l], l, j);
-        } else {
-          const T K = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
-          dk = k1[l] * ratio(K, fmadd(wj, K, T(1)));
-        }
+        const T K = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
+        const T f = fmadd(wj, K, T(1));
+        const T dk = f == T(0) ? dk_explicit<T, FAM, ALPHA, L>(job, tb, wT, bi[l], l, j) : k1[l] * ratio(K, f);
         su = fmadd(uget(l), dk, su);
         s1 += dk;
       }

@@ -631,7 +631,7 @@ __device__ __forceinline__ void fused_C_item(const FTask &ft, uint32_t v, uint32
   }
   __syncthreads();
   // u itself stays in the transform tile (sm) after tile_wht; each thread reads its own
-  gradient_sweep<T, FAM, ALPHA, L>(job, tb, wT, bi, k1, uu, ok,
+  gradient_sweep<T, FAM, ALPHA, L, true>(job, tb, wT, bi, k1, uu, ok,
                                    [&](int l) { return sm[t + (l << kLOGNT)]; }, red);
   __syncthreads();
   double *dst = ft.gr + ((uint64_t)v * ft.tiles + tile) * 2 * d;
@@ -703,7 +703,7 @@ __global__ void __launch_bounds__(256) k_fused_final(FTask ft) { fused_final_ite
 // x <- H x * scale for vectors of n = 2^m with LOGT < m <= 2 LOGT - LOGL, in place, in two
 // tile passes: low LOGT bits on contiguous tiles, the high bits on column tiles.
 template <typename T>
-__global__ void __launch_bounds__(kFNT) k_wht_low(T *__restrict__ x) {
+__global__ void __launch_bounds__(kFNT, 5) k_wht_low(T *__restrict__ x) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L;
   extern __shared__ __align__(16) unsigned char smem[];
   T *sm = reinterpret_cast<T *>(smem);
@@ -771,7 +771,7 @@ __device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
 }
 
 template <typename T, int M>
-__global__ void __launch_bounds__(kFNT, 4) k_wht_persist(T *__restrict__ x, T scale, WhtSched sc,
+__global__ void __launch_bounds__(kFNT, 5) k_wht_persist(T *__restrict__ x, T scale, WhtSched sc,
                                                          uint32_t *__restrict__ ctr, uint32_t *status,
                                                          uint32_t spin_limit, uint32_t first_item) {
   constexpr int LOGT = FCfg<T>::LOGT, L = FCfg<T>::L, m = M, c = 2 * LOGT - M;
