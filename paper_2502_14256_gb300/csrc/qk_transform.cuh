@@ -83,6 +83,28 @@ __device__ __forceinline__ double2 twiddle(double2, uint64_t j, int b, double si
   return make_double2(cv, sv);
 }
 
+// e^{sign i pi k / 8} for k = 0..7: cos and sin of multiples of pi/8 (k is a compile-time
+// constant wherever this is called, so the switch folds away).
+template <typename E, typename S>
+__device__ __forceinline__ E root8(int k, S sign) {
+  constexpr double C1 = 0.92387953251128675613, S1 = 0.38268343236508977173, R2 = 0.70710678118654752440;
+  double c = 1.0, s = 0.0;
+  switch (k & 7) {
+    case 1: c = C1, s = S1; break;
+    case 2: c = R2, s = R2; break;
+    case 3: c = S1, s = C1; break;
+    case 4: c = 0.0, s = 1.0; break;
+    case 5: c = -S1, s = C1; break;
+    case 6: c = -R2, s = R2; break;
+    case 7: c = -C1, s = S1; break;
+    default: break;
+  }
+  E w;
+  w.x = (S)c;
+  w.y = (S)(sign * s);
+  return w;
+}
+
 template <typename E>
 __device__ __forceinline__ int pad_index(int e) { return e + (e >> ElemTraits<E>::PAD); }
 
@@ -160,14 +182,17 @@ __device__ __forceinline__ void radix_round(E (&v)[1 << R], uint64_t glow, int g
       }
     }
   } else if constexpr (KIND == XF_DIT) {
+    // the twiddle of stage bg for j = glow + (ql << gb0) factors into e^{-i pi glow / 2^bg}
+    // (one per stage and group) times e^{-i pi ql / 2^h}, an eighth root of -1 (constant)
 #pragma unroll
     for (int h = 0; h < R; ++h) {
       const int bg = gb0 + h;
+      const E base = twiddle(E(), glow, bg, S(-1));
 #pragma unroll
       for (int q = 0; q < (1 << R); ++q) {
         if (!(q & (1 << h))) {
-          const uint64_t j = glow + ((uint64_t)(q & ((1 << h) - 1)) << gb0);
-          const E w = twiddle(E(), j, bg, S(-1));
+          const int ql = q & ((1 << h) - 1);
+          const E w = ql == 0 ? base : cmul(base, root8<E>(ql << (3 - h), S(-1)));
           const E a = v[q], b = cmul(v[q | (1 << h)], w);
           v[q] = a + b;
           v[q | (1 << h)] = a - b;
@@ -178,11 +203,12 @@ __device__ __forceinline__ void radix_round(E (&v)[1 << R], uint64_t glow, int g
 #pragma unroll
     for (int h = R - 1; h >= 0; --h) {
       const int bg = gb0 + h;
+      const E base = twiddle(E(), glow, bg, S(1));
 #pragma unroll
       for (int q = 0; q < (1 << R); ++q) {
         if (!(q & (1 << h))) {
-          const uint64_t j = glow + ((uint64_t)(q & ((1 << h) - 1)) << gb0);
-          const E w = twiddle(E(), j, bg, S(1));
+          const int ql = q & ((1 << h) - 1);
+          const E w = ql == 0 ? base : cmul(base, root8<E>(ql << (3 - h), S(1)));
           const E a = v[q], b = v[q | (1 << h)];
           v[q] = a + b;
           v[q | (1 << h)] = cmul(a - b, w);
