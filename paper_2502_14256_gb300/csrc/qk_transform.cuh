@@ -270,16 +270,24 @@ __global__ void __launch_bounds__(NT) k_transform_pass(E *__restrict__ x, PassDe
   extern __shared__ __align__(16) unsigned char smem_raw[];
   E *sm = reinterpret_cast<E *>(smem_raw);
   const TileMap tm = make_tilemap(p, LOGE, blockIdx.x);
-  for (int e = threadIdx.x; e < E_; e += NT)
-    sm[pad_index<E>(e)] = tm.valid(e) ? x[tm.offset(e)] : zero_elem<E>();
+  constexpr int PER = E_ / NT;  // elements per thread; all loads issued before any is used
+  E r[PER];
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * NT;
+    r[i] = tm.valid(e) ? x[tm.offset(e)] : zero_elem<E>();
+  }
+#pragma unroll
+  for (int i = 0; i < PER; ++i) sm[pad_index<E>(threadIdx.x + i * NT)] = r[i];
   __syncthreads();
   tile_rounds<KIND, E, LOGE, NT>(sm, tm, p.k);
   const bool do_scale = p.scale != 1.0;
-  for (int e = threadIdx.x; e < E_; e += NT) {
-    if (!tm.valid(e)) continue;
+#pragma unroll
+  for (int i = 0; i < PER; ++i) {
+    const int e = threadIdx.x + i * NT;
     E v = sm[pad_index<E>(e)];
     if (do_scale) v = scale_elem(v, p.scale);
-    x[tm.offset(e)] = v;
+    if (tm.valid(e)) x[tm.offset(e)] = v;
   }
 }
 

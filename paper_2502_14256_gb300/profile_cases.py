@@ -2,6 +2,7 @@
 under a profiler (ncu -k <kernel> -c <n>) with inputs sized like the benchmark workload.
 
     python -m paper_2502_14256_gb300.profile_cases fwht  --m 20 --R 64 [--two-pass]
+    python -m paper_2502_14256_gb300.profile_cases fftbr --m 20 --R 64 [--fp64]
     python -m paper_2502_14256_gb300.profile_cases fused --m 20 --R 8  [--refine 0|1] [--fp64] [--persistent]
 
 `fwht` transforms R vectors of 2^m FP32 values in place (qk_fwht_ws, persistent plan with
@@ -27,6 +28,13 @@ def _fwht(args):
         qk.fwht_ws(args.m, x, ws, plan=plan, status=status)
     torch.cuda.synchronize()
     qk.read_status(status)
+
+
+def _fftbr(args):
+    x = torch.randn((args.R, 2 << args.m), dtype=torch.float64 if args.fp64 else torch.float32, device="cuda")
+    for _ in range(1 + args.reps):
+        qk.fftbr(args.m, x)
+    torch.cuda.synchronize()
 
 
 def _fused(args):
@@ -60,7 +68,7 @@ def _fused(args):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("case", choices=["fwht", "fused"])
+    ap.add_argument("case", choices=["fwht", "fftbr", "fused"])
     ap.add_argument("--m", type=int, default=20)
     ap.add_argument("--R", type=int, default=8)
     ap.add_argument("--reps", type=int, default=2)
@@ -69,7 +77,7 @@ def main(argv=None):
     ap.add_argument("--two-pass", action="store_true")
     ap.add_argument("--persistent", action="store_true", help="fused: one persistent launch")
     args = ap.parse_args(argv)
-    (_fwht if args.case == "fwht" else _fused)(args)
+    {"fwht": _fwht, "fftbr": _fftbr, "fused": _fused}[args.case](args)
     print("ok")
 
 
