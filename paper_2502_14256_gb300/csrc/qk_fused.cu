@@ -915,12 +915,12 @@ int persist_wht_max_ctas_per_sm(int dtype) {
 
 // Lag (in vectors) after which a vector's column tiles are queued: enough tickets between
 // a vector's last low tile and its first column tile that the low tile has finished when
-// the column tile is taken ((2 lag - 1) tiles >= resident CTAs), and at most 48 MB of
-// first-pass output waiting in L2.
+// the column tile is taken (lag tiles-per-vector >= resident CTAs), plus three vectors of
+// slack (measured), and at most 48 MB of first-pass output waiting in L2.
 uint32_t persist_wht_default_lag(uint32_t m, uint64_t nvec, int dtype, uint32_t ctas) {
   const int LOGT = dtype == QK_F64 ? FCfg<double>::LOGT : FCfg<float>::LOGT;
   const uint64_t T = 1ull << (m - LOGT), bytes = (dtype == QK_F64 ? 8ull : 4ull) << m;
-  uint64_t lag = (ctas / T + 2) / 2 + 1;
+  uint64_t lag = (ctas + T - 1) / T + 3;  // measured best for 64 x 2^20 FP32 at 4 CTAs/SM: 8
   const uint64_t cap = (48ull << 20) / bytes;
   if (lag > cap) lag = cap;
   if (lag < 1) lag = 1;
@@ -938,7 +938,10 @@ static int persist_wht_t(T *x, uint32_t m, uint64_t nvec, double scale, uint32_t
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint32_t cps = ctas_per_sm == 0 || (int)ctas_per_sm > occ ? (uint32_t)occ : ctas_per_sm;
+  // default: at most 4 CTAs per SM (measured: a fifth resident CTA gains nothing and
+  // lengthens the lag the queue needs)
+  const uint32_t cps = ctas_per_sm == 0 ? (occ < 4 ? (uint32_t)occ : 4u)
+                                        : ((int)ctas_per_sm > occ ? (uint32_t)occ : ctas_per_sm);
   const uint64_t items = (2ull * nvec) << (m - LOGT);
   if (items >= (1ull << 31)) return fail(QK_EINVAL, "persistent WHT: %llu work items exceed 2^31",
                                          (unsigned long long)items);

@@ -99,7 +99,8 @@ int qk_fwht_tune(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, si
   cand.push_back(two);
   const uint64_t bytes = (dtype == QK_F64 ? 8ull : 4ull) << m;
   for (int cps = 1; cps <= occ; ++cps) {
-    const uint32_t base = persist_wht_default_lag(m, nvec, dtype, (uint32_t)(sms * cps));
+    const uint32_t dl = persist_wht_default_lag(m, nvec, dtype, (uint32_t)(sms * cps));
+    const uint32_t base = dl > 1 ? dl / 2 : 1;  // candidates: half, once and twice the default
     uint32_t prev = 0;
     for (uint32_t mult : {1u, 2u, 4u}) {
       uint64_t lag = (uint64_t)base * mult;
