@@ -389,7 +389,7 @@ def main():
     # DRAM bytes (read + write) per launch from one ncu capture of the same kernels at
     # R = 64, n = 2^20, d = 16 (profiles/fused_pipeline_solve20.md); traffic is per
     # randomization, so it scales with R.  Only valid for that m and d.
-    ncu_traffic_r64 = {"k_fused_C": 806.0e6 + 248.0e6, "k_fused_A": 269.2e6 + 1010e6}
+    ncu_traffic_r64 = {"k_fused_C": 805.9e6 + 248.2e6, "k_fused_A": 268.7e6 + 1010e6}
     roof = None
     if top_name in flops_per_point:
         work = flops_per_point[top_name] * R_ * n_
@@ -433,7 +433,7 @@ def main():
                      "shape": f"{R} x 2^{m} fp32, in place", "plan": fw_plan,
                      # ncu: dram read + write of one persistent launch at 64 x 2^20
                      # (profiles/fwht_persistent_64x2p20_fp32.md)
-                     "traffic": (268.5e6 + 213.9e6) if (R, m) == (64, 20) else None,
+                     "traffic": (275.9e6 + 326.0e6) if (R, m) == (64, 20) else None,
                      "two_launch_ms": fw2_ms, "two_launch_gbs": fw_bytes / (fw2_ms * 1e-3) / 1e9},
             "fftbr": {"gbs": ff_bytes / (ff_ms * 1e-3) / 1e9, "ms": ff_ms, "bytes": ff_bytes,
                       "frac_of_hbm": ff_bytes / (ff_ms * 1e-3) / 1e9 / hbm_peak,
