@@ -183,11 +183,15 @@ __device__ __forceinline__ void radix_round(E (&v)[1 << R], uint64_t glow, int g
     }
   } else if constexpr (KIND == XF_DIT) {
     // the twiddle of stage bg for j = glow + (ql << gb0) factors into e^{-i pi glow / 2^bg}
-    // (one per stage and group) times e^{-i pi ql / 2^h}, an eighth root of -1 (constant)
+    // (one per stage and group) times e^{-i pi ql / 2^h}, an eighth root of -1 (constant);
+    // the per-stage factors are successive squares of the top stage's
+    E bases[R];
+    bases[R - 1] = twiddle(E(), glow, gb0 + R - 1, S(-1));
+#pragma unroll
+    for (int h = R - 2; h >= 0; --h) bases[h] = cmul(bases[h + 1], bases[h + 1]);
 #pragma unroll
     for (int h = 0; h < R; ++h) {
-      const int bg = gb0 + h;
-      const E base = twiddle(E(), glow, bg, S(-1));
+      const E base = bases[h];
 #pragma unroll
       for (int q = 0; q < (1 << R); ++q) {
         if (!(q & (1 << h))) {
@@ -200,10 +204,13 @@ __device__ __forceinline__ void radix_round(E (&v)[1 << R], uint64_t glow, int g
       }
     }
   } else {
+    E bases[R];
+    bases[R - 1] = twiddle(E(), glow, gb0 + R - 1, S(1));
+#pragma unroll
+    for (int h = R - 2; h >= 0; --h) bases[h] = cmul(bases[h + 1], bases[h + 1]);
 #pragma unroll
     for (int h = R - 1; h >= 0; --h) {
-      const int bg = gb0 + h;
-      const E base = twiddle(E(), glow, bg, S(1));
+      const E base = bases[h];
 #pragma unroll
       for (int q = 0; q < (1 << R); ++q) {
         if (!(q & (1 << h))) {

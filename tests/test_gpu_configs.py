@@ -159,7 +159,8 @@ def test_precision_workload_fp32_refined_against_fp64(qk):
 def test_mixed_workload_full_size(qk):
     """256 instances (half lattice + SI alpha = 1, half net + DSI order 2), m in 12..22,
     d in {8, 32, 128}: FP32-refined schedule captured in a CUDA graph, against the FP64 GPU
-    path on the eight smallest instances."""
+    path on the eight smallest instances (the 1e-5 target) and on the two largest of each
+    family (reported; their spectra reach the nugget, see the precision workload)."""
     wls = inputs.mixed_batch()
     t0 = time.time()
     insts = [W.build_instance(qk, wl, wl.ms[0], 1, 1, seed_shift=0, y_kind="product") for wl in wls]
@@ -169,8 +170,12 @@ def test_mixed_workload_full_size(qk):
     t2 = time.time()
     print(f"\nmixed workload: {sum(1 << i.m for i in insts)} points, inputs {t1 - t0:.1f} s, "
           f"schedule {t2 - t1:.2f} s, status word {word}")
-    order = np.argsort([(1 << i.m) * i.wl.d for i in insts])[:8]
-    for k in order:
+    size = [(1 << i.m) * i.wl.d for i in insts]
+    order = list(np.argsort(size)[:8])
+    for kind in ("net", "lattice"):
+        idx = [k for k in np.argsort(size)[::-1] if insts[k].wl.kind == kind][:2]
+        order += idx
+    for pos, k in enumerate(order):
         inst = insts[k]
         t64, b64 = W.outputs(qk, inst, F64, with_lam=False, y_via=F32)
         W.run_tasks(qk, [t64], F64)
@@ -179,6 +184,10 @@ def test_mixed_workload_full_size(qk):
         print(f"  {inst.wl.kind} m={inst.m} d={inst.wl.d}: mll {rel(b32['out'][..., 2], b64['out'][..., 2]):.2e} "
               f"quad {rel(b32['out'][..., 0], b64['out'][..., 0]):.2e} solve {rel(b32['c'], b64['c']):.2e} "
               f"grad {rel(b32['grad'][..., :inst.wl.d], b64['grad'][..., :inst.wl.d]):.2e}")
+        for key in ("out", "c", "grad"):
+            assert torch.isfinite(b32[key]).all(), (k, key)
+        if pos >= 8:
+            continue
         assert rel(b32["out"][..., 2], b64["out"][..., 2]) < 1e-5, (k, inst.wl.kind)
         assert rel(b32["out"][..., 0], b64["out"][..., 0]) < 1e-5, (k, inst.wl.kind)
         assert rel(b32["c"], b64["c"]) < 1e-5, (k, inst.wl.kind)
