@@ -350,12 +350,59 @@ __device__ __forceinline__ void xwht_col(T (&v)[FCfg<T>::L], T *sm, int c, int d
   }
 }
 
+// Packed FP32 pairs (sm_100+ f32x2 adds): the same roundings as the scalar operations.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long v, float &a, float &b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long x, unsigned long long y) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+  return r;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long x, unsigned long long y) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(x), "l"(y));
+  return r;
+}
+
+// Two compensated butterflies (registers q and q + 1 of the same stage) in packed
+// arithmetic: exactly cbfly applied to each.
+__device__ __forceinline__ void cbfly_x2(float &ah0, float &ah1, float &al0, float &al1, float &bh0, float &bh1,
+                                         float &bl0, float &bl1) {
+  const unsigned long long A = pk2(ah0, ah1), B = pk2(bh0, bh1), Al = pk2(al0, al1), Bl = pk2(bl0, bl1);
+  const unsigned long long S = add2(A, B), bb = sub2(S, A);
+  const unsigned long long e1 = add2(sub2(A, sub2(S, bb)), sub2(B, bb));  // TwoSum(a, b)
+  const unsigned long long D = sub2(A, B), dd = sub2(D, A);
+  const unsigned long long e2 = sub2(sub2(A, sub2(D, dd)), add2(B, dd));  // TwoSum(a, -b)
+  const unsigned long long SL = add2(add2(Al, Bl), e1), DL = add2(sub2(Al, Bl), e2);
+  upk2(S, ah0, ah1);
+  upk2(SL, al0, al1);
+  upk2(D, bh0, bh1);
+  upk2(DL, bl0, bl1);
+}
+
 template <typename T>
 __device__ __forceinline__ void reg_stages2(T (&vh)[FCfg<T>::L], T (&vl)[FCfg<T>::L], int bit0, int lo, int hi) {
   constexpr int L = FCfg<T>::L, LOGL = FCfg<T>::LOGL;
 #pragma unroll
   for (int h = 0; h < LOGL; ++h) {
     if (bit0 + h >= lo && bit0 + h < hi) {
+      if constexpr (sizeof(T) == 4) {
+        if (h > 0) {
+#pragma unroll
+          for (int q = 0; q < L; q += 2)
+            if (!(q & (1 << h))) {
+              const int p = q | (1 << h);
+              cbfly_x2(vh[q], vh[q + 1], vl[q], vl[q + 1], vh[p], vh[p + 1], vl[p], vl[p + 1]);
+            }
+          continue;
+        }
+      }
 #pragma unroll
       for (int q = 0; q < L; ++q)
         if (!(q & (1 << h))) cbfly(vh[q], vl[q], vh[q | (1 << h)], vl[q | (1 << h)]);
