@@ -47,8 +47,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--e2e-chunk", type=int, default=8, help="randomizations per host-copy chunk (e2e)")
-    ap.add_argument("--sched", default="launches", choices=["launches", "persistent"],
-                    help="batched schedule: per-phase launches or one persistent launch")
+    ap.add_argument("--sched", default="auto", choices=["auto", "launches", "persistent"],
+                    help="batched schedule: tuned (auto), per-phase launches or one persistent launch")
     ap.add_argument("--lag", type=int, default=1, help="persistent schedule: units between phases")
     return ap.parse_args()
 
@@ -266,6 +266,9 @@ def main():
     P32 = Pipeline(qk, torch, dev, W, torch.float32, refine=args.refine)
     if args.sched == "persistent":
         qk.batch_schedule(P32.ws, qk.QK_SCHED_PERSISTENT, args.lag)
+    sched = {"mode": args.sched, "lag": args.lag if args.sched == "persistent" else 0}
+    if args.sched == "auto":  # the library's schedule tuner picks launches vs one persistent launch
+        sched = qk.batch_tune(P32.ws)
     for _ in range(args.warmup):
         P32.step()
     qk.read_status(P32.status)
@@ -425,6 +428,7 @@ def main():
             "gpu_launches": launches,
             "gpu_launches_per_step": launches / max(1, args.steps),
             "fp64_plain": fp64,
+            "schedule": sched,
             "stages_ms": stage,
             "doubling": doubling,
             "kernels_ms_per_step": {k: v[1] / max(1, args.steps) for k, v in kernel_ms.items()},

@@ -337,6 +337,14 @@ QK_API int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream s
 #define QK_SCHED_PERSISTENT 1
 QK_API int qk_batch_schedule(void *ws, size_t ws_bytes, int32_t mode, uint32_t lag);
 
+/* Autotuner for a recorded plan (no counterpart in the paper): runs the plan as the
+ * launch sequence and, when eligible, as the persistent launch with each lag, times each
+ * with CUDA events on `stream` (the plan's outputs are overwritten), and keeps the
+ * fastest as the plan's schedule (as qk_batch_schedule would).  Returns the choice and
+ * its milliseconds per run (each out-pointer nullable).  Synchronises the stream; not
+ * for stream capture. */
+QK_API int qk_batch_tune(void *ws, size_t ws_bytes, int32_t *mode, uint32_t *lag, float *ms, qk_stream stream);
+
 /* Run a planned schedule with HOST inputs and outputs (the planned device buffers are
  * the staging area): every task's randomizations go in chunks of chunk_r; chunk k's
  * right-hand sides are copied in on a library stream while chunk k-1 computes on

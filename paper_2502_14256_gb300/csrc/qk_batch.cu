@@ -286,6 +286,62 @@ int qk_batch_schedule(void *ws, size_t ws_bytes, int32_t mode, uint32_t lag) {
   return QK_OK;
 }
 
+int qk_batch_tune(void *ws, size_t ws_bytes, int32_t *mode_out, uint32_t *lag_out, float *ms_out, qk_stream stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan base;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_plans.find(ws);
+    if (it == g_plans.end()) return fail(QK_EINVAL, "no plan recorded for this workspace (call qk_batch_plan)");
+    base = it->second;
+  }
+  if (ws_bytes < base.total) return fail(QK_EWORKSPACE, "batch workspace has %zu bytes, %zu needed", ws_bytes, base.total);
+  struct Cand {
+    int32_t mode;
+    uint32_t lag;
+    float ms;
+  };
+  std::vector<Cand> cand = {{QK_SCHED_LAUNCHES, 0, 0.f}};
+  if (base.persist_bytes)
+    for (uint32_t lag = 1; lag <= kMaxPersistLag; ++lag) cand.push_back({QK_SCHED_PERSISTENT, lag, 0.f});
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  int rc = QK_OK;
+  Cand best{QK_SCHED_LAUNCHES, 0, 1e30f};
+  for (Cand &c : cand) {
+    if ((rc = qk_batch_schedule(ws, ws_bytes, c.mode, c.lag))) break;
+    Plan p;
+    {
+      std::lock_guard<std::mutex> lk(g_mu);
+      p = g_plans[ws];
+    }
+    if ((rc = run_plan(p, (unsigned char *)ws, nullptr, st, nullptr))) break;  // warm-up
+    const int reps = 3;
+    cudaEventRecord(a, st);
+    for (int r = 0; r < reps && !rc; ++r) rc = run_plan(p, (unsigned char *)ws, nullptr, st, nullptr);
+    cudaEventRecord(b, st);
+    if (rc) break;
+    cudaError_t e = cudaEventSynchronize(b);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "qk_batch_tune");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    c.ms = ms / reps;
+    if (c.ms < best.ms) best = c;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (rc) return rc;
+  if ((rc = qk_batch_schedule(ws, ws_bytes, best.mode, best.lag))) return rc;
+  if (mode_out) *mode_out = best.mode;
+  if (lag_out) *lag_out = best.lag;
+  if (ms_out) *ms_out = best.ms;
+  return QK_OK;
+}
+
 int qk_batch_run_host(void *ws, size_t ws_bytes, const qk_host_io *io, uint32_t chunk_r, uint32_t *status,
                       qk_stream stream) {
   Plan p;

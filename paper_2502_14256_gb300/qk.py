@@ -34,7 +34,7 @@ EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_sol
             "qk_read_status", "qk_last_error", "qk_version", "qk_fwht", "qk_fftbr", "qk_ifftbr",
             "qk_launch_count", "qk_eigs_static", "qk_batch_timing", "qk_batch_kernel_ms", "qk_fwht_ws",
             "qk_fwht_tune", "qk_fwht_wait_selftest", "qk_batch_run_host", "qk_batch_schedule",
-            "qk_kernel_col_at", "qk_eigs_extend", "qk_fwht_extend", "qk_fftbr_extend"]
+            "qk_kernel_col_at", "qk_eigs_extend", "qk_fwht_extend", "qk_fftbr_extend", "qk_batch_tune"]
 
 
 class QKError(RuntimeError):
@@ -100,6 +100,7 @@ def _load():
         "qk_fwht_wait_selftest": [u32, u64, i32, P, P, sz, u32, P, P],
         "qk_batch_run_host": [P, sz, C.POINTER(HostIO), u32, P, P],
         "qk_batch_schedule": [P, sz, i32, u32],
+        "qk_batch_tune": [P, sz, C.POINTER(i32), C.POINTER(u32), C.POINTER(C.c_float), P],
         "qk_kernel_col_at": [C.POINTER(PointSet), C.POINTER(Kernel), u32, u32, u64, u32, i32, i32, P, P],
         "qk_eigs_extend": [i32, u32, u32, i32, i32, P, dbl, dbl, P, P, P, sz, P, P],
         "qk_fwht_extend": [u32, u64, i32, P, P, P, P],
@@ -366,6 +367,15 @@ def batch_run(ws, status=None, stream=None):
 def batch_schedule(ws, mode: int, lag: int = 0):
     """Choose how batch_run executes the recorded plan (QK_SCHED_LAUNCHES / QK_SCHED_PERSISTENT)."""
     _check(LIB.qk_batch_schedule(_ptr(ws), ws.numel(), mode, lag))
+
+
+def batch_tune(ws, stream=None) -> dict:
+    """Time the launch sequence and the persistent launch (each lag) of the recorded plan and
+    keep the fastest; returns {"mode": ..., "lag": ..., "ms": ...}."""
+    mode, lag, ms = C.c_int32(0), C.c_uint32(0), C.c_float(0.0)
+    _check(LIB.qk_batch_tune(_ptr(ws), ws.numel(), C.byref(mode), C.byref(lag), C.byref(ms), _stream(stream)))
+    return {"mode": "persistent" if mode.value == QK_SCHED_PERSISTENT else "launches", "lag": lag.value,
+            "ms": ms.value}
 
 
 def batch_run_host(ws, host_io, chunk_r: int, status=None, stream=None):

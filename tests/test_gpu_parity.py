@@ -640,3 +640,32 @@ def test_doubling_update_of_eigenvalues_and_transforms(qk, kind, family, alpha, 
         out = torch.empty_like(y)
         (qk.fftbr_extend if cplx else qk.fwht_extend)(m, xt_old, x_new, out)
         assert qc.rel_err(out.cpu().numpy(), ref.cpu().numpy()) < tol, dtype
+
+
+def test_schedule_tuner_keeps_results(qk):
+    """qk_batch_tune times the launch sequence and the persistent launch (each lag), keeps
+    the fastest, and the plan's results are unchanged bit for bit."""
+    from paper_2502_14256_gb300 import inputs
+    from tests import qkworkloads as W
+    wl = inputs.workload("batch")
+    insts = [W.build_instance(qk, wl, m, R, 2, seed_shift=i) for i, (m, R) in enumerate([(15, 4), (16, 2)])]
+    tasks, bufs = zip(*[W.outputs(qk, inst, torch.float32, with_lam=False) for inst in insts])
+    ws = qk.workspace(qk.batch_workspace_bytes(list(tasks), torch.float32))
+    qk.batch_plan(list(tasks), torch.float32, 1, ws)
+    status = torch.zeros(1, dtype=torch.int32, device=qc.dev())
+    qk.batch_run(ws, status)
+    torch.cuda.synchronize()
+    qk.read_status(status)
+    ref = [{k: v.clone() for k, v in b.items() if v is not None} for b in bufs]
+    choice = qk.batch_tune(ws)
+    assert choice["mode"] in ("launches", "persistent") and choice["ms"] > 0
+    for b in bufs:
+        for k, v in b.items():
+            if v is not None and k != "y":
+                v.zero_()
+    qk.batch_run(ws, status)
+    torch.cuda.synchronize()
+    qk.read_status(status)
+    for i, b in enumerate(bufs):
+        for k in ("c", "out", "grad"):
+            assert torch.equal(b[k], ref[i][k]), (i, k, choice)
