@@ -392,7 +392,7 @@ def main():
     # DRAM bytes (read + write) per launch from one ncu capture of the same kernels at
     # R = 64, n = 2^20, d = 16 (profiles/fused_pipeline_solve20.md); traffic is per
     # randomization, so it scales with R.  Only valid for that m and d.
-    ncu_traffic_r64 = {"k_fused_C": 805.9e6 + 248.2e6, "k_fused_A": 268.7e6 + 1010e6}
+    ncu_traffic_r64 = {"k_fused_C": 805.9e6 + 248.1e6, "k_fused_A": 268.7e6 + 1010e6}
     roof = None
     if top_name in flops_per_point:
         work = flops_per_point[top_name] * R_ * n_
