@@ -669,3 +669,23 @@ def test_schedule_tuner_keeps_results(qk):
     for i, b in enumerate(bufs):
         for k in ("c", "out", "grad"):
             assert torch.equal(b[k], ref[i][k]), (i, k, choice)
+
+
+def test_empty_inputs_are_no_ops(qk):
+    """Zero randomizations, vectors or tasks: every entry returns QK_OK and touches nothing."""
+    case = qc.make_case("net", "dsi", 2, 3, 1, seed=5)
+    kern = qc.kernel_of(case)
+    empty = torch.empty((0, 1 << 10), dtype=F64, device=qc.dev())
+    qk.kernel_col(case.ps, kern, 0, 0, 10, empty)
+    lam = torch.empty((0, 1 << 10), dtype=F64, device=qc.dev())
+    qk.eigs(qk.QK_DSI, 10, empty, lam, ws=qk.workspace(256))
+    qk.fwht(10, empty)
+    qk.fftbr(10, torch.empty((0, 2 << 10), dtype=F64, device=qc.dev()))
+    qk.fwht_ws(15, torch.empty((0, 1 << 15), dtype=torch.float32, device=qc.dev()), ws=qk.workspace(256))
+    ws = qk.workspace(256)
+    qk.batch_plan([], F64, 0, ws)
+    status = torch.zeros(1, dtype=torch.int32, device=qc.dev())
+    qk.batch_run(ws, status)
+    torch.cuda.synchronize()
+    qk.read_status(status)
+    assert int(status.item()) == 0
