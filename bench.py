@@ -353,11 +353,9 @@ def main():
     del xf, fw_ws
     # FFTBR (the lattice transform) on R complex FP32 vectors of the same length
     xc = torch.randn((R, 2 * n), dtype=torch.float32, device=dev)
-    ff_ws = q.fwht_workspace(R, dev)
-    ff_ms = time_steps(torch, lambda: q.fftbr_ws(m, xc, ff_ws), args.steps, 2, stream)  # one persistent launch
-    ff2_ms = time_steps(torch, lambda: q.fftbr(m, xc), args.steps, 2, stream)  # two launches
+    ff_ms = time_steps(torch, lambda: q.fftbr(m, xc), args.steps, 2, stream)
     ff_bytes = 2 * xc.numel() * 4
-    del xc, ff_ws
+    del xc
 
     # ---- plain FP64 pipeline beside it
     fp64 = None
@@ -443,8 +441,7 @@ def main():
                      "two_launch_ms": fw2_ms, "two_launch_gbs": fw_bytes / (fw2_ms * 1e-3) / 1e9},
             "fftbr": {"gbs": ff_bytes / (ff_ms * 1e-3) / 1e9, "ms": ff_ms, "bytes": ff_bytes,
                       "frac_of_hbm": ff_bytes / (ff_ms * 1e-3) / 1e9 / hbm_peak,
-                      "shape": f"{R} x 2^{m} complex fp32, in place, two tile passes in one persistent launch",
-                      "two_launch_ms": ff2_ms, "two_launch_gbs": ff_bytes / (ff2_ms * 1e-3) / 1e9},
+                      "shape": f"{R} x 2^{m} complex fp32, in place, two tile passes"},
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks,

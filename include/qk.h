@@ -267,17 +267,6 @@ typedef struct {
 QK_API int qk_fwht_ws(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes,
                       const qk_fwht_plan *plan, uint32_t *status, qk_stream stream);
 
-/* qk_fftbr / qk_ifftbr with a workspace: the same transforms (bit for bit).  Where the
- * length needs exactly two tile passes (2^12 < n <= 2^20 complex FP32, 2^11 < n <= 2^19
- * complex FP64) both run as ONE persistent launch, a vector's second pass queued behind
- * its first so that it reads the first pass's output from L2, with the bounded waits of
- * qk_fwht_ws (QK_STATUS_TIMEOUT in `status`, nullable); other lengths run the plain
- * transform.  ws: (1 + nvec) 32-bit counters, 256-byte aligned (qk_workspace_bytes op 4). */
-QK_API int qk_fftbr_ws(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes,
-                       uint32_t *status, qk_stream stream);
-QK_API int qk_ifftbr_ws(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes,
-                        uint32_t *status, qk_stream stream);
-
 /* Autotuner for qk_fwht_ws (the paper has no counterpart): times the two-launch form and
  * the persistent launch over CTAs per SM x lag on the caller's buffer x (its contents are
  * overwritten: used as scratch), records the fastest for (current device, m, dtype, nvec)
@@ -382,8 +371,7 @@ QK_API int qk_batch_kernel_ms(void *ws, uint32_t idx, char *name, size_t name_le
 /* ------------------------------------------------------------- utilities --- */
 
 /* Workspace bytes needed by qk_eigs / qk_solve / qk_matvec / qk_mll / qk_fwht_ws with
- * these sizes (op: 0 eigs, 1 solve, 2 matvec, 3 mll, 4 fwht_ws / fftbr_ws / ifftbr_ws with
- * batch = nvec). */
+ * these sizes (op: 0 eigs, 1 solve, 2 matvec, 3 mll, 4 fwht_ws with batch = nvec). */
 QK_API int qk_workspace_bytes(int32_t op, int32_t family, uint32_t m, uint32_t batch, uint32_t nrhs,
                        int32_t dtype, uint32_t d, size_t *bytes);
 

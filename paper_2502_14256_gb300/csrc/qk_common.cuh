@@ -190,33 +190,6 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
   return v;
 }
 
-__device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Ticket order of a two-pass batched transform run as one persistent launch: nvec
-// vectors of 2^lt tiles per pass; step s holds the first-pass tiles of vector s and then
-// the second-pass tiles of vector s - lag (1 <= lag <= nvec).
-struct WhtSched {
-  uint32_t nvec, lt, lag;  // lt = log2(tiles per vector); 1 <= lag <= nvec
-  __host__ __device__ uint32_t total() const { return (2u * nvec) << lt; }
-  __device__ void decode(uint32_t i, uint32_t &v, uint32_t &tile, bool &high) const {
-    const uint32_t T = 1u << lt, pre = lag << lt, mid = ((nvec - lag) << lt) * 2u;
-    if (i < pre) {
-      v = i >> lt, tile = i & (T - 1), high = false;
-    } else if (i - pre < mid) {
-      const uint32_t j = i - pre, s = j >> (lt + 1), k = j & (2 * T - 1);
-      high = k >= T;
-      v = high ? s : lag + s;
-      tile = k & (T - 1);
-    } else {
-      const uint32_t j = i - pre - mid;
-      v = (nvec - lag) + (j >> lt), tile = j & (T - 1), high = true;
-    }
-  }
-};
-
-
 // Spread the low 10 bits of v so that bit p lands on bit 3p (30-bit result).
 __device__ __forceinline__ uint32_t spread3_10(uint32_t v) {
   v &= 0x3FFu;

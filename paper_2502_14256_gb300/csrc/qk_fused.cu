@@ -794,6 +794,28 @@ __global__ void __launch_bounds__(kFNT) k_wht_high(T *__restrict__ x, T scale) {
 // were claimed by CTAs that are running, and wait on nothing, so the wait ends.  The
 // wait is bounded all the same: past the limit the item is skipped and
 // QK_STATUS_TIMEOUT is raised.
+struct WhtSched {
+  uint32_t nvec, lt, lag;  // lt = log2(tiles per vector); 1 <= lag <= nvec
+  __host__ __device__ uint32_t total() const { return (2u * nvec) << lt; }
+  __device__ void decode(uint32_t i, uint32_t &v, uint32_t &tile, bool &high) const {
+    const uint32_t T = 1u << lt, pre = lag << lt, mid = ((nvec - lag) << lt) * 2u;
+    if (i < pre) {
+      v = i >> lt, tile = i & (T - 1), high = false;
+    } else if (i - pre < mid) {
+      const uint32_t j = i - pre, s = j >> (lt + 1), k = j & (2 * T - 1);
+      high = k >= T;
+      v = high ? s : lag + s;
+      tile = k & (T - 1);
+    } else {
+      const uint32_t j = i - pre - mid;
+      v = (nvec - lag) + (j >> lt), tile = j & (T - 1), high = true;
+    }
+  }
+};
+
+__device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 template <typename T, int M>
 __global__ void __launch_bounds__(kFNT, 5) k_wht_persist(T *__restrict__ x, T scale, WhtSched sc,

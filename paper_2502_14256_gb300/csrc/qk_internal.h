@@ -93,8 +93,6 @@ int op_solve(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, c
 int op_matvec(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, const double *lam, const void *y,
               void *u, void *ws, cudaStream_t st);
 int op_transform(int kind, uint32_t m, uint64_t nvec, int dtype, void *x, cudaStream_t st);
-int op_transform_persist(int kind, uint32_t m, uint64_t nvec, int dtype, void *x, void *ws, uint32_t *status,
-                         cudaStream_t st);
 int op_eigs_extend(int family, uint32_t m, uint32_t batch, int dtype, int form, const void *col_new, double zeta,
                    double eta, const double *lam_old, double *lam, void *ws, uint32_t *status, cudaStream_t st);
 int op_transform_extend(int kind, uint32_t m, uint64_t nvec, int dtype, const void *xt_old, void *x_new, void *out,

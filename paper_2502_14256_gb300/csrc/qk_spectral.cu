@@ -554,24 +554,6 @@ int op_mll(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const
                          : mll_t<float, float2>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype);
 }
 
-int op_transform_persist(int kind, uint32_t m, uint64_t nvec, int dtype, void *x, void *ws, uint32_t *status,
-                         cudaStream_t st) {
-  const double scale = 1.0 / std::sqrt((double)(1ull << m));
-  int rc = -1;
-  if (kind == XF_DIT)
-    rc = dtype == QK_F64 ? run_transform_persist<XF_DIT, double2>((double2 *)x, (int)m, nvec, scale, (uint32_t *)ws,
-                                                                  status, 0, st, kSpinLimit)
-                         : run_transform_persist<XF_DIT, float2>((float2 *)x, (int)m, nvec, scale, (uint32_t *)ws,
-                                                                 status, 0, st, kSpinLimit);
-  else if (kind == XF_DIF)
-    rc = dtype == QK_F64 ? run_transform_persist<XF_DIF, double2>((double2 *)x, (int)m, nvec, scale, (uint32_t *)ws,
-                                                                  status, 0, st, kSpinLimit)
-                         : run_transform_persist<XF_DIF, float2>((float2 *)x, (int)m, nvec, scale, (uint32_t *)ws,
-                                                                 status, 0, st, kSpinLimit);
-  if (rc == -1) return op_transform(kind, m, nvec, dtype, x, st);  // not a two-pass size
-  return rc;
-}
-
 int op_transform(int kind, uint32_t m, uint64_t nvec, int dtype, void *x, cudaStream_t st) {
   const double scale = 1.0 / std::sqrt((double)(1ull << m));
   if (kind == XF_WHT && tiled_wht_supported(m, dtype)) return tiled_wht(x, m, nvec, dtype, scale, st);

@@ -19,7 +19,6 @@
 // their stages in increasing (DIT) or decreasing (DIF) bit order, passes too.
 #pragma once
 
-#include <utility>
 #include <vector>
 
 #include "qk_common.cuh"
@@ -271,25 +270,19 @@ __device__ __forceinline__ void tile_rounds(E *sm, const TileMap &tm, int k) {
   }
 }
 
-template <bool CG, typename E>
-__device__ __forceinline__ E load_elem(const E *p) {
-  if constexpr (CG) return __ldcg(p);  // L2 only: data another CTA of this launch wrote
-  else return *p;
-}
-
-// One tile (block blk) of one pass; sm: the padded tile.  Shared memory is free again
-// only after a barrier that follows the call.
-template <int KIND, typename E, int NT, bool CG>
-__device__ __forceinline__ void transform_tile(E *__restrict__ x, const PassDesc &p, uint64_t blk, E *sm) {
+template <int KIND, typename E, int NT>
+__global__ void __launch_bounds__(NT) k_transform_pass(E *__restrict__ x, PassDesc p) {
   constexpr int LOGE = ElemTraits<E>::LOGE;
   constexpr int E_ = 1 << LOGE;
-  const TileMap tm = make_tilemap(p, LOGE, blk);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  E *sm = reinterpret_cast<E *>(smem_raw);
+  const TileMap tm = make_tilemap(p, LOGE, blockIdx.x);
   constexpr int PER = E_ / NT;  // elements per thread; all loads issued before any is used
   E r[PER];
 #pragma unroll
   for (int i = 0; i < PER; ++i) {
     const int e = threadIdx.x + i * NT;
-    r[i] = tm.valid(e) ? load_elem<CG>(&x[tm.offset(e)]) : zero_elem<E>();
+    r[i] = tm.valid(e) ? x[tm.offset(e)] : zero_elem<E>();
   }
 #pragma unroll
   for (int i = 0; i < PER; ++i) sm[pad_index<E>(threadIdx.x + i * NT)] = r[i];
@@ -302,62 +295,6 @@ __device__ __forceinline__ void transform_tile(E *__restrict__ x, const PassDesc
     E v = sm[pad_index<E>(e)];
     if (do_scale) v = scale_elem(v, p.scale);
     if (tm.valid(e)) x[tm.offset(e)] = v;
-  }
-}
-
-template <int KIND, typename E, int NT>
-__global__ void __launch_bounds__(NT) k_transform_pass(E *__restrict__ x, PassDesc p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  transform_tile<KIND, E, NT, false>(x, p, blockIdx.x, reinterpret_cast<E *>(smem_raw));
-}
-
-// Both passes of a two-pass transform in one persistent launch (the ticket order of
-// WhtSched): the second pass of a vector waits, bounded, until all its first-pass tiles
-// are published, reads them from L2, and past the bound skips the tile and raises
-// QK_STATUS_TIMEOUT.  Progress: a CTA claims its next ticket while processing the
-// current item but waits only at the start of an item, after publishing the previous
-// one, and waits only on smaller tickets.
-template <int KIND, typename E, int NT>
-__global__ void __launch_bounds__(NT) k_transform_persist(E *__restrict__ x, PassDesc p1, PassDesc p2,
-                                                          WhtSched sc, uint32_t *__restrict__ ctr, uint32_t *status,
-                                                          uint32_t spin_limit) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ uint32_t s_item[2], s_ok[2];
-  E *sm = reinterpret_cast<E *>(smem_raw);
-  uint32_t *ticket = ctr, *done = ctr + 1;
-  const int t = threadIdx.x;
-  const uint32_t total = sc.total(), T_ = 1u << sc.lt;
-  if (t == 0) s_item[0] = atomicAdd(ticket, 1u);
-  __syncthreads();
-  for (int k = 0;; ++k) {
-    const uint32_t it = s_item[k & 1];
-    if (it >= total) break;
-    if (t == 0) s_item[(k + 1) & 1] = atomicAdd(ticket, 1u);
-    uint32_t v, tile;
-    bool second;
-    sc.decode(it, v, tile, second);
-    const uint64_t blk = ((uint64_t)v << sc.lt) | tile;
-    if (!second) {
-      transform_tile<KIND, E, NT, false>(x, p1, blk, sm);
-      __syncthreads();  // every thread's stores precede thread 0's release below
-      if (t == 0) red_release_add_u32(&done[v], 1u);
-    } else {
-      if (t == 0) {
-        uint32_t tries = 0, ok = 1;
-        while (ld_acquire_u32(&done[v]) < T_) {
-          if (++tries > spin_limit) {
-            ok = 0;
-            if (status) atomicOr(status, (uint32_t)QK_STATUS_TIMEOUT);
-            break;
-          }
-          __nanosleep(128);
-        }
-        s_ok[k & 1] = ok;
-      }
-      __syncthreads();
-      if (s_ok[k & 1]) transform_tile<KIND, E, NT, true>(x, p2, blk, sm);
-      __syncthreads();  // shared memory is reused by the next item
-    }
   }
 }
 
@@ -421,42 +358,6 @@ int run_transform(E *x, int m, uint64_t vstride, uint64_t nvec, double scale, cu
     if (rc) return rc;
   }
   return QK_OK;
-}
-
-// The two passes of a transform of nvec vectors of 2^m (m in the two-pass range) as one
-// persistent launch; ctr: (1 + nvec) counters.  Returns -1, launching nothing, when m
-// needs another number of passes (callers then use run_transform).
-template <int KIND, typename E>
-int run_transform_persist(E *x, int m, uint64_t nvec, double scale, uint32_t *ctr, uint32_t *status, uint32_t lag,
-                          cudaStream_t st, uint32_t spin_limit) {
-  constexpr int NT = 256;
-  std::vector<PassDesc> passes = plan_passes<E>(m, 1ull << m, nvec);
-  if (passes.size() != 2) return -1;
-  if (KIND == XF_DIF) std::swap(passes[0], passes[1]);
-  passes.back().scale = scale;
-  const uint64_t b1 = pass_blocks<E>(passes[0]), b2 = pass_blocks<E>(passes[1]);
-  if (b1 != b2 || nvec == 0 || b1 % nvec) return -1;
-  const uint64_t T = b1 / nvec;
-  uint32_t lt = 0;
-  while ((1ull << lt) < T) ++lt;
-  if ((1ull << lt) != T || (2ull * nvec << lt) >= (1ull << 31)) return -1;
-  const size_t smem = pass_smem<E>();
-  smem_optin<k_transform_persist<KIND, E, NT>>(smem);
-  int occ = 0, dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_transform_persist<KIND, E, NT>, NT, smem) != cudaSuccess ||
-      occ < 1)
-    return fail(QK_ECUDA, "persistent transform: occupancy query failed");
-  const uint64_t grid = (uint64_t)sms * occ;
-  if (lag == 0) lag = (uint32_t)((grid + T - 1) / T + 3);
-  if (lag > nvec) lag = (uint32_t)nvec;
-  WhtSched sc{(uint32_t)nvec, lt, lag};
-  cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * (1 + nvec), st);
-  if (e != cudaSuccess) return cuda_fail(e, "persistent transform: counter reset");
-  k_transform_persist<KIND, E, NT><<<(unsigned)grid, NT, smem, st>>>(x, passes[0], passes[1], sc, ctr, status,
-                                                                     spin_limit);
-  return check_launch("transform persistent");
 }
 
 }  // namespace qk

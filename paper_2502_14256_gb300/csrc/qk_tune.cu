@@ -74,29 +74,6 @@ int qk_fwht_ws(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size
   return run_plan_wht(p, m, nvec, dtype, x, ws, status, (cudaStream_t)stream);
 }
 
-static int fft_ws_entry(int kind, uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes,
-                        uint32_t *status, qk_stream stream) {
-  set_error("%s", "");
-  if (dtype != QK_F64 && dtype != QK_F32) return fail(QK_EINVAL, "dtype must be QK_F64 or QK_F32");
-  if (m > QK_MAX_M) return fail(QK_EINVAL, "m = %u exceeds QK_MAX_M = %d", m, QK_MAX_M);
-  if (nvec == 0) return QK_OK;
-  if (!x) return fail(QK_EINVAL, "transform data is NULL");
-  const size_t need = persist_wht_ws_bytes(nvec);
-  if (!ws || ws_bytes < need) return fail(QK_EWORKSPACE, "workspace has %zu bytes, %zu needed", ws_bytes, need);
-  if (((uintptr_t)ws & 255u) != 0) return fail(QK_EINVAL, "workspace must be 256-byte aligned");
-  return op_transform_persist(kind, m, nvec, dtype, x, ws, status, (cudaStream_t)stream);
-}
-
-int qk_fftbr_ws(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes, uint32_t *status,
-                qk_stream stream) {
-  return fft_ws_entry(1, m, nvec, dtype, x, ws, ws_bytes, status, stream);
-}
-
-int qk_ifftbr_ws(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes, uint32_t *status,
-                 qk_stream stream) {
-  return fft_ws_entry(2, m, nvec, dtype, x, ws, ws_bytes, status, stream);
-}
-
 int qk_fwht_tune(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes, qk_fwht_plan *best,
                  qk_stream stream) {
   set_error("%s", "");

@@ -34,8 +34,7 @@ EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_sol
             "qk_read_status", "qk_last_error", "qk_version", "qk_fwht", "qk_fftbr", "qk_ifftbr",
             "qk_launch_count", "qk_eigs_static", "qk_batch_timing", "qk_batch_kernel_ms", "qk_fwht_ws",
             "qk_fwht_tune", "qk_fwht_wait_selftest", "qk_batch_run_host", "qk_batch_schedule",
-            "qk_kernel_col_at", "qk_eigs_extend", "qk_fwht_extend", "qk_fftbr_extend", "qk_batch_tune",
-            "qk_fftbr_ws", "qk_ifftbr_ws"]
+            "qk_kernel_col_at", "qk_eigs_extend", "qk_fwht_extend", "qk_fftbr_extend", "qk_batch_tune"]
 
 
 class QKError(RuntimeError):
@@ -98,8 +97,6 @@ def _load():
         "qk_batch_kernel_ms": [P, u32, C.c_char_p, sz, C.POINTER(u32), C.POINTER(dbl)],
         "qk_fwht_ws": [u32, u64, i32, P, P, sz, C.POINTER(FwhtPlan), P, P],
         "qk_fwht_tune": [u32, u64, i32, P, P, sz, C.POINTER(FwhtPlan), P],
-        "qk_fftbr_ws": [u32, u64, i32, P, P, sz, P, P],
-        "qk_ifftbr_ws": [u32, u64, i32, P, P, sz, P, P],
         "qk_fwht_wait_selftest": [u32, u64, i32, P, P, sz, u32, P, P],
         "qk_batch_run_host": [P, sz, C.POINTER(HostIO), u32, P, P],
         "qk_batch_schedule": [P, sz, i32, u32],
@@ -321,25 +318,6 @@ def fwht_ws(m: int, x, ws=None, plan=None, status=None, stream=None):
         pp = C.byref(FwhtPlan(plan["mode"], plan.get("lag", 0), plan.get("ctas_per_sm", 0), 0.0))
     _check(LIB.qk_fwht_ws(m, nvec, dtype_code(x.dtype), _ptr(x), _ptr(ws), ws.numel(), pp, _ptr(status),
                           _stream(stream)))
-    return x
-
-
-def fftbr_ws(m: int, x, ws=None, status=None, stream=None):
-    """qk_fftbr as one persistent launch where the length needs two tile passes."""
-    nvec = _nvec_m(x, m, True)
-    if ws is None:
-        ws = fwht_workspace(nvec, x.device)
-    _check(LIB.qk_fftbr_ws(m, nvec, dtype_code(x.dtype), _ptr(x), _ptr(ws), ws.numel(), _ptr(status),
-                           _stream(stream)))
-    return x
-
-
-def ifftbr_ws(m: int, x, ws=None, status=None, stream=None):
-    nvec = _nvec_m(x, m, True)
-    if ws is None:
-        ws = fwht_workspace(nvec, x.device)
-    _check(LIB.qk_ifftbr_ws(m, nvec, dtype_code(x.dtype), _ptr(x), _ptr(ws), ws.numel(), _ptr(status),
-                            _stream(stream)))
     return x
 
 

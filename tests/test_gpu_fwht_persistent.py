@@ -79,21 +79,3 @@ def test_wait_that_runs_out_returns_timeout_status(qk):
     assert int(status.item()) == 0
     ref = qk.fwht(m, x.clone())
     assert torch.equal(qk.fwht_ws(m, x.clone()), ref)
-
-
-@pytest.mark.parametrize("dtype,m,nvec", [(torch.float32, 13, 7), (torch.float32, 16, 5), (torch.float32, 20, 3),
-                                          (torch.float32, 22, 1), (torch.float32, 10, 4), (torch.float64, 12, 6),
-                                          (torch.float64, 15, 3), (torch.float64, 19, 2)])
-def test_fftbr_ws_is_bitwise_fftbr(qk, dtype, m, nvec):
-    """qk_fftbr_ws / qk_ifftbr_ws (one persistent launch for two-pass lengths, the plain
-    transform otherwise) equal qk_fftbr / qk_ifftbr bit for bit."""
-    x = _data(nvec, m + 1, dtype, seed=m * 7 + nvec)  # interleaved complex: 2^(m+1) reals per vector
-    status = torch.zeros(1, dtype=torch.int32, device="cuda:0")
-    ref = qk.fftbr(m, x.clone())
-    got = qk.fftbr_ws(m, x.clone(), status=status)
-    qk.read_status(status)
-    assert torch.equal(got, ref)
-    back_ref = qk.ifftbr(m, ref.clone())
-    back = qk.ifftbr_ws(m, got, status=status)
-    qk.read_status(status)
-    assert torch.equal(back, back_ref)
