@@ -400,7 +400,9 @@ def main():
         traffic = ncu_traffic_r64.get(top_name) if (W["m"], d_) == (20, 16) else None
         roof = {"kernel": top_name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": ach / fp32_peak, "traffic": traffic * R_ / 64 if traffic else None,
-                "ms_per_launch": top_ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
+                "ms_per_launch": top_ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "note": "instruction-issue bound (clz, conversions, table loads, reciprocal per factor): "
+                        "73% issue-active in ncu, profiles/fused_pipeline_solve20.md"}
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):
