@@ -262,10 +262,22 @@ __device__ __forceinline__ void column_sweep(const ColJob &job, const DiffTables
     const T wj = wT[j];
     uint32_t base = 0;
     if constexpr (FAM == 0) base = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * d + j];
+    if constexpr (sizeof(T) == 4 && L % 2 == 0) {
+      // two points per packed f32x2 multiply / add / fma: the same roundings as below
+      const unsigned long long W = pack_f2(wj, wj);
 #pragma unroll
-    for (int l = 0; l < L; ++l) {
-      const T a = wj * kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
-      p[l] = pm1_step(p[l], a);
+      for (int l = 0; l < L; l += 2) {
+        const T k0 = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
+        const T k1 = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l + 1], l + 1, j));
+        const unsigned long long A = mul_f2(W, pack_f2(k0, k1)), P = pack_f2(p[l], p[l + 1]);
+        unpack_f2(fma_f2(P, A, add_f2(P, A)), p[l], p[l + 1]);
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        const T a = wj * kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
+        p[l] = pm1_step(p[l], a);
+      }
     }
   }
 }
