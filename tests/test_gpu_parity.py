@@ -422,7 +422,7 @@ def _batch_outputs(qk, case, m, nrhs, dt, y_h, eta, refine=0):
 
 @pytest.mark.parametrize("dt", [F64, F32])
 @pytest.mark.parametrize("m,alpha,order,nrhs", [(13, 2, "gray", 2), (14, 1, "gray", 1), (16, 4, "natural", 3),
-                                                (20, 2, "gray", 1), (21, 2, "natural", 1)])
+                                                (17, 3, "gray", 2), (20, 2, "gray", 1), (21, 2, "natural", 1)])
 def test_fused_schedule_matches_oracle(qk, dt, m, alpha, order, nrhs):
     """The batched schedule (fused three-phase kernels where the size allows) against
     the oracle's spectral formulas: lambda, solve, quadratic form, log det, MLL,
