@@ -392,7 +392,14 @@ def main():
     # DRAM bytes (read + write) per launch from one ncu capture of the same kernels at
     # R = 64, n = 2^20, d = 16 (profiles/fused_pipeline_solve20.md); traffic is per
     # randomization, so it scales with R.  Only valid for that m and d.
-    ncu_traffic_r64 = {"k_fused_C": 805.9e6 + 248.1e6, "k_fused_A": 268.7e6 + 1010e6}
+    ncu_traffic_r64 = {"k_fused_C": 805.9e6 + 247.8e6, "k_fused_A": 268.7e6 + 1013.3e6}
+    bound_note = {
+        "k_fused_A": "instruction-issue bound: per point and dimension a difference word, clz, "
+                     "coefficient row load, conversion, FMA polynomial and the p update "
+                     "(profiles/fused_pipeline_solve20.md)",
+        "k_fused_C": "instruction-issue bound: per point and dimension a difference word, clz, "
+                     "coefficient row load, conversion, reciprocal and two accumulations "
+                     "(profiles/fused_pipeline_solve20.md)"}
     roof = None
     if top_name in flops_per_point:
         work = flops_per_point[top_name] * R_ * n_
@@ -401,8 +408,7 @@ def main():
         roof = {"kernel": top_name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": ach / fp32_peak, "traffic": traffic * R_ / 64 if traffic else None,
                 "ms_per_launch": top_ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "note": "instruction-issue bound (clz, conversions, table loads, reciprocal per factor): "
-                        "73% issue-active in ncu, profiles/fused_pipeline_solve20.md"}
+                "note": bound_note.get(top_name, "")}
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk_path):

@@ -297,35 +297,77 @@ __device__ T dk_explicit(const ColJob &job, const DiffTables &tb, const T *wT, u
 }
 
 __device__ __forceinline__ float ratio(float a, float b) { return __fdividef(a, b); }  // 2 ulp
+// Approximate reciprocal (PTX rcp.approx.ftz.f32, max 1 ulp; subnormals flush to 0): 1/0 = inf.
+__device__ __forceinline__ float rcp_approx(float a) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+  return r;
+}
 __device__ __forceinline__ double ratio(double a, double b) { return a / b; }
 
 // Gradient sweep: for each dimension j, warp-reduced sums over this warp's points of
 // u_i dk1_i/dc_j and dk1_i/dc_j (float-float pairs in FP32 sweeps, doubles in FP64
 // sweeps), written to red[warp][2d] and totalled by red_total, with
-// dk1_i/dc_j = k1_i K_ij / (1 + c_j K_ij).  wk[l] = u_l k1_l; uget(l) returns u_l and
-// is called only for the rare exact zero of 1 + c_j K_ij, handled after the loop by
-// the explicit product over the other dimensions.
+// dk1_i/dc_j = k1_i K_ij / (1 + c_j K_ij).  wk[l] = u_l k1_l, both zero for points with
+// !ok[l]; uget(l) returns u_l and is called only for the rare exact zero of
+// 1 + c_j K_ij, handled after the loop by the explicit product over the other dimensions.
 template <typename T, int FAM, int ALPHA, int L, bool ALL_OK = false, typename UF>
 __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTables &tb, const T *wT,
                                                const uint32_t (&bi)[L], const T (&k1)[L], const T (&wk)[L],
                                                const bool (&ok)[L], UF uget, double *red) {
   const uint32_t d = job.d;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr bool PACKED = sizeof(T) == 4 && L % 2 == 0;
+  // packed form: points (2h, 2h+1) share one f32x2 fma / mul, with the two halves summed
+  // separately; a zero 1 + c_j K gives an infinite reciprocal, so the sums come out
+  // non-finite and the exact fallback below runs instead of a per-point zero test.
+  // Points with !ok[l] carry wk[l] = k1[l] = 0 and add nothing (or a NaN, which again
+  // sends the thread to the fallback, where they are skipped).
+  unsigned long long WK[PACKED ? L / 2 : 1], K1[PACKED ? L / 2 : 1];
+  if constexpr (PACKED) {
+#pragma unroll
+    for (int h = 0; h < L / 2; ++h) {
+      WK[h] = pack_f2(wk[2 * h], wk[2 * h + 1]);
+      K1[h] = pack_f2(k1[2 * h], k1[2 * h + 1]);
+    }
+  }
   for (uint32_t j = 0; j < d; ++j) {
     const T wj = wT[j];
     T su = T(0), s1 = T(0);
     uint32_t base = 0;
     if constexpr (FAM == 0) base = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * d + j];
     bool anyzero = false;
+    if constexpr (PACKED) {
+      const unsigned long long W = pack_f2(wj, wj), ONE = pack_f2(1.f, 1.f);
+      unsigned long long SU = pack_f2(0.f, 0.f), S1 = SU;
 #pragma unroll
-    for (int l = 0; l < L; ++l) {
-      const T K = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
-      const T f = fmadd(wj, K, T(1));
-      anyzero |= f == T(0);
-      T q = ratio(K, f);
-      if constexpr (!ALL_OK) q = ok[l] ? q : T(0);
-      su = fmadd(wk[l], q, su);
-      s1 = fmadd(k1[l], q, s1);
+      for (int h = 0; h < L / 2; ++h) {
+        const T ka = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[2 * h], 2 * h, j));
+        const T kb = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[2 * h + 1], 2 * h + 1, j));
+        const unsigned long long KK = pack_f2(ka, kb);
+        float fa, fb;
+        unpack_f2(fma_f2(W, KK, ONE), fa, fb);
+        const unsigned long long Q = mul_f2(KK, pack_f2(rcp_approx(fa), rcp_approx(fb)));
+        SU = fma_f2(WK[h], Q, SU);
+        S1 = fma_f2(K1[h], Q, S1);
+      }
+      float a, b;
+      unpack_f2(SU, a, b);
+      su = a + b;
+      unpack_f2(S1, a, b);
+      s1 = a + b;
+      anyzero = !(isfinite(su) && isfinite(s1));
+    } else {
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        const T K = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
+        const T f = fmadd(wj, K, T(1));
+        anyzero |= f == T(0);
+        T q = ratio(K, f);
+        if constexpr (!ALL_OK) q = ok[l] ? q : T(0);
+        su = fmadd(wk[l], q, su);
+        s1 = fmadd(k1[l], q, s1);
+      }
     }
     if (anyzero) {  // exact zeros of 1 + c_j K: use prod_{j' != j} (1 + c_j' K_j') directly
       su = T(0), s1 = T(0);
