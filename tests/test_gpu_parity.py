@@ -479,6 +479,55 @@ def test_fused_schedule_matches_oracle(qk, dt, m, alpha, order, nrhs):
                 assert np.all(np.abs(g_[d + 1:2 * d + 1] - gr["dmean_dc"]) < bound)
 
 
+@pytest.mark.parametrize("path,dt,m", [("standalone", F64, 8), ("standalone", F32, 8),
+                                       ("fused", F64, 14), ("fused", F32, 14)])
+def test_gradient_with_exact_zero_factors(qk, path, dt, m):
+    """DSI order 1 with c_1 = 2: K_1 = 1 - 3 2^-beta is -1/2 wherever the first coordinate of
+    the difference is >= 1/2 (beta = 1), so 1 + c_1 K_1 = 0 exactly and k_1 vanishes at half
+    the points.  dk_1/dc_1 there is the product of the other factors, which the sweeps reach
+    only through their exact fallback; the oracle multiplies the factors explicitly.  The
+    standalone case (2^8 points in a 2^11-point tile) also has padding points whose factors
+    vanish."""
+    d, R, alpha = 3, 2, 1
+    eta = 1e-4 if dt == F64 else 1e-3
+    c = np.array([2.0, 0.6, 0.4])
+    case = qc.make_case("net", "dsi", alpha, d, R, seed=4242 + m, c=c, zeta=1.0, order="gray")
+    n = 1 << m
+    y_h = np.empty((R, 1, n))
+    refs = []
+    for r in range(R):
+        k1, X = case.k1_ref(r, m)
+        assert np.count_nonzero(k1 == 0.0) >= n // 4  # the degenerate case is present
+        lam_ref = o.eigenvalues("dsi", k1, eta)
+        y_h[r, 0] = np.cos(X[:, 1] / 2 ** 31) + X[:, 0] / 2 ** 33
+        refs.append((X, float(lam_ref[0]),
+                     o.spectral_mll_grad("dsi", alpha, X, y_h[r, 0], lam_ref, case.c, case.zeta)))
+    if path == "fused":
+        grad = _batch_outputs(qk, case, m, 1, dt, y_h, eta)["grad"]
+    else:
+        kern, _, lam = _setup_spectrum(qk, case, m, dt, eta, R)
+        y = torch.tensor(y_h, dtype=dt, device=qc.dev())
+        out = torch.empty((R, 1, 5), dtype=F64, device=qc.dev())
+        g = torch.empty((R, 1, 2 * d + 2), dtype=F64, device=qc.dev())
+        status = torch.zeros(1, dtype=torch.int32, device=qc.dev())
+        qk.mll(case.ps, kern, 0, R, m, 1, eta, lam, y, out, g, status=status)
+        qk.read_status(status)
+        grad = g.cpu().numpy()
+    for r in range(R):
+        X, lam0, gr = refs[r]
+        assert np.all(np.isfinite(grad[r, 0]))
+        if dt == F64:
+            assert qc.rel_err(grad[r, 0, :d], gr["dc"]) < 1e-9, qc.rel_err(grad[r, 0, :d], gr["dc"])
+            assert qc.rel_err(grad[r, 0, d + 1:2 * d + 1], gr["dmean_dc"]) < 1e-8
+        else:
+            assert qc.rel_err(grad[r, 0, :d], gr["dc"]) < 2e-4, qc.rel_err(grad[r, 0, :d], gr["dc"])
+            # a sum of mean-zero terms: absolute bound from the FP32 rounding of the terms
+            absum = _abs_dk_sums("dsi", alpha, X, case.c, case.zeta)
+            scale = abs(case.zeta * float(np.sum(y_h[r, 0])) / lam0 ** 2) * absum
+            bound = 2e-4 * np.abs(gr["dmean_dc"]) + 8 * math.sqrt(32) * qc.EPS32 * scale
+            assert np.all(np.abs(grad[r, 0, d + 1:2 * d + 1] - gr["dmean_dc"]) < bound)
+
+
 @pytest.mark.parametrize("m,alpha,eta", [(15, 2, 1e-4), (18, 1, 1e-5), (20, 4, 1e-4)])
 def test_fused_refinement_solves_the_fp32_operator(qk, m, alpha, eta):
     """One refinement step (refine_steps = 1) with the residual carried exactly
