@@ -607,14 +607,19 @@ __device__ __forceinline__ void fused_B_item(const FTask &ft, uint32_t r, uint32
       y[l] = ch;
       gst[e] = gg;
     }
-    xwht_col<T>(y, sm, c, 1);  // L2 -> L0
+    // inverse high bits of c^, then of g: one copy of the transform's code for both (the
+    // kernel's time goes to instruction fetch more than to arithmetic)
+#pragma unroll 1
+    for (int k = 0; k < 2; ++k) {
+      if (k) {
 #pragma unroll
-    for (int l = 0; l < L; ++l) YT[wi0(l)] = y[l];
+        for (int l = 0; l < L; ++l) y[l] = gst[t + (l << kLOGNT)];
+      }
+      xwht_col<T>(y, sm, c, 1);  // L2 -> L0
+      T *dst = k ? GT : YT;
 #pragma unroll
-    for (int l = 0; l < L; ++l) y[l] = gst[t + (l << kLOGNT)];
-    xwht_col<T>(y, sm, c, 1);
-#pragma unroll
-    for (int l = 0; l < L; ++l) GT[wi0(l)] = y[l];
+      for (int l = 0; l < L; ++l) dst[wi0(l)] = y[l];
+    }
     const double sq = block_sum_c(quad, T(0), red);
     const double sg = block_sum_c(gs, T(0), red);
     if (t == 0) {
