@@ -26,8 +26,9 @@ def qk():
     return q
 
 
-def _oracle_check(inst, bufs, r, rhs_list, tol, check_grad=True):
-    """Compare randomization r (given right-hand sides) with the oracle's spectral formulas."""
+def _oracle_check(inst, bufs, r, rhs_list, tol, check_grad=True, y_fp32=False):
+    """Compare randomization r (given right-hand sides) with the oracle's spectral formulas;
+    y_fp32: the GPU ran on y rounded to FP32, so the oracle takes the same rounded y."""
     fam = inst.wl.family
     n = 1 << inst.m
     X = W.host_points(inst, r, np.arange(n))
@@ -35,6 +36,8 @@ def _oracle_check(inst, bufs, r, rhs_list, tol, check_grad=True):
     k1 = o.first_column(fam, inst.wl.alpha, X, c_w, inst.wl.zeta)
     lam = o.eigenvalues(fam, k1, inst.wl.eta)
     Y = W.host_rhs(inst, r, X)
+    if y_fp32:
+        Y = Y.astype(np.float32).astype(np.float64)
     got_lam = bufs["lam"][r].cpu().numpy() if bufs["lam"] is not None else None
     if got_lam is not None:
         assert qc.rel_err(got_lam, lam) < tol["lam"]
@@ -154,6 +157,32 @@ def test_precision_workload_fp32_refined_against_fp64(qk):
         if eta >= 100:
             for k in ("solve", "quad", "logdet", "mll", "grad"):
                 assert errs[k] < 1e-5, (k, errs[k])
+
+
+def test_solve20_workload_full_size(qk):
+    """The benchmark's workload at its full size and in the launch configuration it times:
+    net n = 2^20, d = 16, 64 randomizations, order-2 DSI, gamma_j = 0.9^j, eta = 1e-8, FP32
+    column and transforms with one refinement step (the fused launch sequence).  Every
+    randomization against the FP64 GPU path on the same FP32-rounded y (relative 1e-5 on the
+    MLL, quadratic form, solve and gradient); the last randomization against the oracle's
+    spectral formulas (~45 s of host work: the oracle's gradient is O(d^2 n))."""
+    wl = inputs.workload("solve20")
+    inst = W.build_instance(qk, wl, wl.ms[0], wl.R, wl.nrhs)
+    t32, b32 = W.outputs(qk, inst, F32)
+    W.run_tasks(qk, [t32], F32, refine=1, allow_floor=True)
+    t64, b64 = W.outputs(qk, inst, F64, with_lam=False, y_via=F32)
+    W.run_tasks(qk, [t64], F64, allow_floor=True)
+    rel = lambda a, b: float((a.double() - b.double()).abs().max() / b.double().abs().max())  # noqa: E731
+    d = wl.d
+    errs = {"mll": rel(b32["out"][..., 2], b64["out"][..., 2]), "quad": rel(b32["out"][..., 0], b64["out"][..., 0]),
+            "logdet": rel(b32["out"][..., 1], b64["out"][..., 1]), "solve": rel(b32["c"], b64["c"]),
+            "grad": rel(b32["grad"][..., :d], b64["grad"][..., :d])}
+    print("\nsolve20 FP32-refined vs FP64 GPU: " + " ".join(f"{k}={v:.2e}" for k, v in errs.items()))
+    for k, v in errs.items():
+        assert v < 1e-5, (k, v)
+    del b64
+    tol32 = dict(lam=1e-5, quad=1e-5, logdet=1e-5, mll=1e-5, mean=1e-5, c=1e-5, grad=1e-5)
+    _oracle_check(inst, b32, wl.R - 1, [0], tol32, y_fp32=True)
 
 
 def test_mixed_workload_full_size(qk):
