@@ -393,6 +393,9 @@ def main():
     # R = 64, n = 2^20, d = 16 (profiles/fused_pipeline_solve20.md); traffic is per
     # randomization, so it scales with R.  Only valid for that m and d.
     ncu_traffic_r64 = {"k_fused_C": 805.9e6 + 247.8e6, "k_fused_A": 268.7e6 + 1013.3e6}
+    # issue-slot utilisation of the same kernels from one ncu --set full capture at R = 8
+    # (profiles/fused_pipeline_solve20.md): the instruction-issue roofline these kernels sit on
+    ncu_issue_active = {"k_fused_A": 0.564, "k_fused_C": 0.596}
     bound_note = {
         "k_fused_A": "instruction-issue bound: per point and dimension a difference word, clz, "
                      "coefficient row load, conversion, FMA polynomial and the p update "
@@ -408,6 +411,7 @@ def main():
         roof = {"kernel": top_name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": ach / fp32_peak, "traffic": traffic * R_ / 64 if traffic else None,
                 "ms_per_launch": top_ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                "issue_active_ncu": ncu_issue_active.get(top_name) if (W["m"], d_) == (20, 16) else None,
                 "note": bound_note.get(top_name, "")}
     peaks = {}
     pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
