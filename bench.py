@@ -400,9 +400,9 @@ def main():
         "k_fused_A": "instruction-issue bound: per point and dimension a difference word, clz, "
                      "coefficient row load, conversion, FMA polynomial and the p update "
                      "(profiles/fused_pipeline_solve20.md)",
-        "k_fused_C": "instruction-issue bound: per point and dimension a difference word, clz, "
-                     "coefficient row load, conversion, reciprocal and two accumulations "
-                     "(profiles/fused_pipeline_solve20.md)"}
+        "k_fused_C": "issue and dependent-latency bound at 2 CTAs per SM: per point and dimension a "
+                     "difference word, clz, coefficient row load, conversion, reciprocal and two "
+                     "accumulations (profiles/fused_pipeline_solve20.md)"}
     roof = None
     if top_name in flops_per_point:
         work = flops_per_point[top_name] * R_ * n_
