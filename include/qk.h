@@ -237,7 +237,8 @@ QK_API int qk_ifftbr(uint32_t m, uint64_t nvec, int32_t dtype, void *x, qk_strea
  * next n values (raw; transformed in place here), out = the transform of all 2n values:
  *   out = [xt_old + w (.) xt_new, xt_old - w (.) xt_new] / sqrt(2),
  * w_k = 1 (qk_fwht_extend) or exp(-pi i k / n) (qk_fftbr_extend; interleaved complex).
- * xt_old, x_new: (nvec, n); out: (nvec, 2n); out must not overlap the inputs. */
+ * xt_old, x_new: (nvec, n); out: (nvec, 2n).  out must not overlap the inputs, nor
+ * x_new (transformed in place) xt_old: overlapping arrays return QK_EINVAL. */
 QK_API int qk_fwht_extend(uint32_t m, uint64_t nvec, int32_t dtype, const void *xt_old, void *x_new, void *out,
                           qk_stream stream);
 QK_API int qk_fftbr_extend(uint32_t m, uint64_t nvec, int32_t dtype, const void *xt_old, void *x_new, void *out,

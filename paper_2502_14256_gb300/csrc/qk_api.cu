@@ -216,6 +216,16 @@ static int transform_extend_entry(int kind, uint32_t m, uint64_t nvec, int32_t d
   if (m + 1 > QK_MAX_M) return fail(QK_EINVAL, "2^(m+1) exceeds 2^%d", QK_MAX_M);
   if (nvec == 0) return QK_OK;
   if (!xt_old || !x_new || !out) return fail(QK_EINVAL, "transform extension: NULL array");
+  // byte ranges: xt_old and x_new hold nvec x n elements, out nvec x 2n (complex for FFTBR)
+  const uint64_t half = elem_bytes(kind == 0 ? QK_DSI : QK_SI, dtype) * (nvec << m);
+  auto disjoint = [](const void *a, uint64_t na, const void *b, uint64_t nb) {
+    const uintptr_t pa = (uintptr_t)a, pb = (uintptr_t)b;
+    return pa + na <= pb || pb + nb <= pa;
+  };
+  if (!disjoint(out, 2 * half, xt_old, half) || !disjoint(out, 2 * half, x_new, half))
+    return fail(QK_EINVAL, "transform extension: out must not overlap xt_old or x_new");
+  if (!disjoint(x_new, half, xt_old, half))
+    return fail(QK_EINVAL, "transform extension: x_new (transformed in place) must not overlap xt_old");
   return op_transform_extend(kind, m, nvec, dtype, xt_old, x_new, out, (cudaStream_t)stream);
 }
 

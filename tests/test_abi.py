@@ -72,6 +72,41 @@ def test_invalid_arguments_are_rejected_before_any_launch(lib_path):
     assert lib.qk_batch_run(fake, 0, None, None) == qk.QK_EINVAL
 
 
+def test_documented_argument_errors_of_the_extension_and_scheduling_calls(lib_path):
+    """Errors include/qk.h documents for the doubling updates, the static-scratch
+    eigenvalues and the schedule / FWHT plans, all raised before any launch."""
+    from paper_2502_14256_gb300 import qk
+    lib = qk.LIB
+    a, b = C.c_void_p(0x100000), C.c_void_p(0x100000 + 64)  # overlapping ranges
+    fake = C.c_void_p(0x2000000)
+    ps = qk.PointSet(qk.QK_NET_B2, qk.QK_GRAY, 2, 1, fake, None, fake)
+    k = qk.Kernel(qk.QK_DSI, 2, 2, fake, 1.0)
+    # positions of an extended point set start at multiples of 2048
+    assert lib.qk_kernel_col_at(C.byref(ps), C.byref(k), 0, 1, C.c_uint64(100), 4, qk.QK_F64, 0, fake,
+                                None) == qk.QK_EINVAL
+    assert "2048" in qk.last_error()
+    # the extended eigenvalues must not overlap the old ones
+    assert lib.qk_eigs_extend(qk.QK_DSI, 10, 1, qk.QK_F64, 0, fake, C.c_double(1.0), C.c_double(0.0), a, b,
+                              fake, C.c_size_t(1 << 30), None, None) == qk.QK_EINVAL
+    # transform extensions: out must not overlap the inputs, nor x_new xt_old
+    for fn in (lib.qk_fwht_extend, lib.qk_fftbr_extend):
+        assert fn(10, C.c_uint64(1), qk.QK_F32, a, fake, b, None) == qk.QK_EINVAL
+        assert "out must not overlap" in qk.last_error()
+        assert fn(10, C.c_uint64(1), qk.QK_F32, a, b, fake, None) == qk.QK_EINVAL
+        assert "x_new" in qk.last_error()
+    # static scratch: a request beyond its size is refused
+    assert lib.qk_eigs_static(qk.QK_DSI, 20, 8, qk.QK_F64, 0, fake, C.c_double(1.0), C.c_double(0.0), fake,
+                              None, None) == qk.QK_EINVAL
+    # unknown schedule and FWHT plan modes
+    assert lib.qk_batch_schedule(fake, C.c_size_t(1 << 20), 7, 1) == qk.QK_EINVAL
+    plan = qk.FwhtPlan(7, 0, 0, 0.0)
+    assert lib.qk_fwht_ws(16, C.c_uint64(4), qk.QK_F32, fake, fake, C.c_size_t(1 << 20), C.byref(plan), None,
+                          None) == qk.QK_EINVAL
+    # the bounded-wait self-test needs a status word
+    assert lib.qk_fwht_wait_selftest(16, C.c_uint64(4), qk.QK_F32, fake, fake, C.c_size_t(1 << 20), 10, None,
+                                     None) == qk.QK_EINVAL
+
+
 def test_no_cpu_fallback_in_the_binding():
     """The product binding never imports the oracle and never computes on the host."""
     src = open(os.path.join(ROOT, "paper_2502_14256_gb300", "qk.py")).read()
