@@ -28,6 +28,7 @@ QK_MLL_QUAD, QK_MLL_LOGDET, QK_MLL_MLL, QK_MLL_MEAN, QK_MLL_VAR, QK_MLL_NOUT = r
 OP_EIGS, OP_SOLVE, OP_MATVEC, OP_MLL, OP_FWHT = 0, 1, 2, 3, 4
 QK_FWHT_TWO_PASS, QK_FWHT_PERSISTENT = 0, 1
 QK_SCHED_LAUNCHES, QK_SCHED_PERSISTENT = 0, 1
+QK_MAX_M, QK_MAX_D = 30, 256
 
 EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_solve", "qk_matvec", "qk_mll",
             "qk_batch_workspace_bytes", "qk_batch_plan", "qk_batch_run", "qk_workspace_bytes",

@@ -42,6 +42,9 @@ def test_binding_loads_and_names_match(lib_path):
     from paper_2502_14256_gb300 import qk
     assert sorted(qk.EXPORTED) == _declared()
     assert qk.version() >= 100
+    text = open(HEADER).read()
+    for name in ("QK_MAX_M", "QK_MAX_D"):
+        assert int(re.search(rf"#define {name} (\d+)", text).group(1)) == getattr(qk, name)
 
 
 def test_invalid_arguments_are_rejected_before_any_launch(lib_path):
@@ -105,6 +108,47 @@ def test_documented_argument_errors_of_the_extension_and_scheduling_calls(lib_pa
     # the bounded-wait self-test needs a status word
     assert lib.qk_fwht_wait_selftest(16, C.c_uint64(4), qk.QK_F32, fake, fake, C.c_size_t(1 << 20), 10, None,
                                      None) == qk.QK_EINVAL
+
+
+def test_point_set_kernel_and_spectrum_argument_errors(lib_path):
+    """Limits include/qk.h states for point sets, kernels and the spectrum: positions below
+    2^32, 1 <= d <= QK_MAX_D, randomizations within R, lattices in natural order, matching
+    kernel and point-set d, DSI orders 1-4 and SI 1-2, zeta > 0, m <= QK_MAX_M, known column
+    forms and families, 256-byte aligned workspaces.  Each returns QK_EINVAL before a launch."""
+    from paper_2502_14256_gb300 import qk
+    lib = qk.LIB
+    fake = C.c_void_p(0x2000000)
+
+    def ps(kind=qk.QK_NET_B2, order=qk.QK_GRAY, d=2, R=2):
+        net = kind == qk.QK_NET_B2
+        return C.byref(qk.PointSet(kind, order, d, R, fake if net else None, None if net else fake, fake))
+
+    def kern(fam=qk.QK_DSI, alpha=2, d=2, zeta=1.0):
+        return C.byref(qk.Kernel(fam, alpha, d, fake, zeta))
+
+    u64 = C.c_uint64
+    cases = [
+        lib.qk_gen_points(ps(), 0, 1, u64((1 << 32) - 4), u64(8), fake, None),
+        lib.qk_gen_points(ps(d=qk.QK_MAX_D + 1), 0, 1, u64(0), u64(8), fake, None),
+        lib.qk_gen_points(ps(R=2), 1, 2, u64(0), u64(8), fake, None),
+        lib.qk_gen_points(ps(kind=qk.QK_LATTICE, order=qk.QK_GRAY), 0, 1, u64(0), u64(8), fake, None),
+        lib.qk_kernel_col(ps(d=2), kern(d=3), 0, 1, 4, qk.QK_F64, 0, fake, None),
+        lib.qk_kernel_col(ps(), kern(alpha=5), 0, 1, 4, qk.QK_F64, 0, fake, None),
+        lib.qk_kernel_col(ps(kind=qk.QK_LATTICE, order=qk.QK_NATURAL), kern(fam=qk.QK_SI, alpha=3), 0, 1, 4,
+                          qk.QK_F64, 0, fake, None),
+        lib.qk_kernel_col(ps(), kern(zeta=0.0), 0, 1, 4, qk.QK_F64, 0, fake, None),
+        lib.qk_kernel_col(ps(), kern(), 0, 1, qk.QK_MAX_M + 1, qk.QK_F64, 0, fake, None),
+        lib.qk_kernel_col(ps(), kern(), 0, 1, 4, qk.QK_F64, 9, fake, None),
+        lib.qk_lms_setup(0, 1, fake, fake, fake, None),
+        lib.qk_lms_setup(2, 1, None, fake, fake, None),
+        lib.qk_eigs(qk.QK_DSI, 4, 1, qk.QK_F64, 0, fake, C.c_double(0.0), C.c_double(0.0), fake, fake,
+                    C.c_size_t(1 << 20), None, None),
+        lib.qk_eigs(7, 4, 1, qk.QK_F64, 0, fake, C.c_double(1.0), C.c_double(0.0), fake, fake,
+                    C.c_size_t(1 << 20), None, None),
+        lib.qk_eigs(qk.QK_DSI, 4, 1, qk.QK_F64, 0, fake, C.c_double(1.0), C.c_double(0.0), fake,
+                    C.c_void_p(0x2000010), C.c_size_t(1 << 20), None, None),
+    ]
+    assert cases == [qk.QK_EINVAL] * len(cases), cases
 
 
 def test_no_cpu_fallback_in_the_binding():
