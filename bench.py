@@ -214,6 +214,15 @@ def oracle_sample(W_host, m_sample, count=1, r_first=0):
                             f"(numpy FP64, single thread, {dt:.1f} s)")
 
 
+def workload_config(m, d, R, world):
+    """The `config` object of both arms' JSON lines (the same workload)."""
+    return {"workload": f"solve20: digital net (Gray, LMS+DS) n=2^{m}, d={d}, {R} randomizations/GPU, "
+                        "DSI order 2, gamma_j=0.9^j, eta=1e-8, 1 rhs; FP32 column+FWHT, FP64 "
+                        "division/logdet/variance, 1 refinement step",
+            "global_batch": world * R, "seq_len": 1 << m, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (y alone 256 MB)"}
+
+
 # ---------------------------------------------------------------- main
 def main():
     args = parse()
@@ -239,8 +248,7 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"solve20: net n=2^{args.m} d={wl.d} R={args.R} DSI order 2, 1 rhs",
-                           "l2": "inputs larger than L2"},
+                "config": workload_config(args.m, wl.d, args.R, args.gpus),
                 "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1, "sample": sample},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -430,11 +438,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"solve20: digital net (Gray, LMS+DS) n=2^{m}, d={d}, {R} randomizations/GPU, "
-                                   "DSI order 2, gamma_j=0.9^j, eta=1e-8, 1 rhs; FP32 column+FWHT, FP64 "
-                                   "division/logdet/variance, 1 refinement step",
-                       "global_batch": world * R, "seq_len": n, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (y alone 256 MB)"},
+            "config": workload_config(m, d, R, world),
             "e2e": {"value": points_step / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
