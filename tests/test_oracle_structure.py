@@ -202,6 +202,28 @@ def test_spectral_gradient_matches_dense(family, alpha, order):
     assert abs(sp["dmean_deta"] - dense["dmean_deta"]) < 1e-9 * max(1.0, abs(dense["dmean_deta"]))
 
 
+def test_gradient_with_exact_zero_factors_matches_dense_and_finite_differences():
+    """DSI order 1 with c_1 = 2: 1 + c_1 K_1 = 0 exactly wherever the first coordinate of
+    x_i (-) x_k is >= 1/2, so half of k_1 (and of every Gram row) vanishes.  The spectral
+    gradient (explicit products, no division by the factor) must still equal the dense
+    definition and central differences of the dense MLL in c_1 (K is polynomial in c)."""
+    m, d, eta = 6, 3, 1e-3
+    X = _net_points(m, d, "gray", seed=21)
+    y = inputs.rhs_product(X)
+    c = np.array([2.0, 0.6, 0.4])
+    k1 = o.first_column("dsi", 1, X, c)
+    assert np.count_nonzero(k1 == 0.0) == (1 << m) // 2
+    lam = o.eigenvalues("dsi", k1, eta)
+    sp = o.spectral_mll_grad("dsi", 1, X, y, lam, c)
+    dense = o.mll_grad_dense("dsi", 1, X, y, c, np.zeros(d), eta)
+    assert np.allclose(sp["dc"], dense["dc"], rtol=1e-9, atol=1e-9 * np.abs(dense["dc"]).max())
+    assert np.allclose(sp["dmean_dc"], dense["dmean_dc"], rtol=1e-9, atol=1e-12)
+    h = 1e-5
+    mll = lambda cc: o.mll_dense(o.gram_dense("dsi", 1, X, cc, 1.0, eta), y)[0]  # noqa: E731
+    fd = (mll(c + [h, 0, 0]) - mll(c - [h, 0, 0])) / (2 * h)
+    assert abs(fd - dense["dc"][0]) < 1e-5 * max(1.0, abs(fd))
+
+
 @pytest.mark.parametrize("family", ["dsi", "si"])
 def test_scale_zeta_enters_posterior_as_in_the_dense_definition(family):
     m, d, zeta, eta = 7, 3, 2.5, 1e-5
