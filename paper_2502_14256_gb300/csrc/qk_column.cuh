@@ -311,6 +311,7 @@ __device__ __forceinline__ double ratio(double a, double b) { return a / b; }
 // dk1_i/dc_j = k1_i K_ij / (1 + c_j K_ij).  wk[l] = u_l k1_l, both zero for points with
 // !ok[l]; uget(l) returns u_l and is called only for the rare exact zero of
 // 1 + c_j K_ij, handled after the loop by the explicit product over the other dimensions.
+// ALL_OK (unpacked sweeps): every point is valid, so no per-point validity select.
 template <typename T, int FAM, int ALPHA, int L, bool ALL_OK = false, typename UF>
 __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTables &tb, const T *wT,
                                                const uint32_t (&bi)[L], const T (&k1)[L], const T (&wk)[L],
