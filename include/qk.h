@@ -314,14 +314,6 @@ QK_API int qk_batch_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, i
  * captured into a CUDA graph. */
 QK_API int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream stream);
 
-/* Per-kernel timing of a planned schedule (no paper counterpart; used to report
- * rooflines).  After qk_batch_timing(ws, runs), each of the next `runs` calls of
- * qk_batch_run on that workspace records a CUDA event pair around every kernel it
- * launches, on the launching stream (events are host-side runtime objects; no device
- * memory is allocated).  qk_batch_kernel_ms(ws, idx, ...) waits for the recorded
- * events and returns, for the idx-th distinct kernel name, its launch count and
- * summed device milliseconds; QK_EINVAL once idx runs past the last name.
- * qk_batch_timing(ws, 0) stops recording and forgets the records. */
 /* How qk_batch_run executes a recorded plan.  QK_SCHED_LAUNCHES (the default after
  * qk_batch_plan): per task, a sequence of kernel launches (4 for fused tasks).
  * QK_SCHED_PERSISTENT: ONE launch of resident CTAs for the whole plan; every
@@ -365,6 +357,14 @@ typedef struct {
 QK_API int qk_batch_run_host(void *ws, size_t ws_bytes, const qk_host_io *io, uint32_t chunk_r, uint32_t *status,
                              qk_stream stream);
 
+/* Per-kernel timing of a planned schedule (no paper counterpart; used to report
+ * rooflines).  After qk_batch_timing(ws, runs), each of the next `runs` calls of
+ * qk_batch_run on that workspace records a CUDA event pair around every kernel it
+ * launches, on the launching stream (events are host-side runtime objects; no device
+ * memory is allocated).  qk_batch_kernel_ms(ws, idx, ...) waits for the recorded
+ * events and returns, for the idx-th distinct kernel name, its launch count and
+ * summed device milliseconds; QK_EINVAL once idx runs past the last name.
+ * qk_batch_timing(ws, 0) stops recording and forgets the records. */
 QK_API int qk_batch_timing(void *ws, uint32_t runs);
 QK_API int qk_batch_kernel_ms(void *ws, uint32_t idx, char *name, size_t name_len, uint32_t *launches,
                               double *ms);
