@@ -576,3 +576,136 @@ def spectral_mll_grad(family, alpha, X, y, lam, c_w, zeta=1.0):
         "dmean_dc": -zeta * ysum * dsum / lam0 ** 2,
         "dmean_deta": -zeta * ysum / lam0 ** 2,
     }
+
+
+# ------------------------------------------- test integrands and the baker transform
+
+
+def baker(x) -> np.ndarray:
+    """Baker (tent) transform x -> 1 - 2|x - 1/2| applied elementwise (Sec. 4.2): it maps the
+    uniform distribution to itself, so it does not change an integrand's mean."""
+    x = np.asarray(x, dtype=np.float64)
+    return 1.0 - 2.0 * np.abs(x - 0.5)
+
+
+def _genz_coefficients(kind: str, d: int) -> np.ndarray:
+    """Genz coefficients (Sec. 6): oscillatory c_j = 4.5 ct_j / sum ct with
+    ct_j = exp(j log(1e-8) / d) ("third kind"); corner peak c_j = 0.25 ct_j / sum ct with
+    ct_j = 1/j^2 ("second kind"); j = 1..d."""
+    j = np.arange(1, d + 1, dtype=np.float64)
+    if kind == "oscillatory":
+        ct = np.exp(j * math.log(1e-8) / d)
+        return 4.5 * ct / ct.sum()
+    ct = 1.0 / j ** 2
+    return 0.25 * ct / ct.sum()
+
+
+def integrand(name: str, x) -> np.ndarray:
+    """The six test integrands of the numerical experiments (Sec. 6), x of shape (..., n, d):
+
+    simple1   d = 1: x e^x - 1
+    simple2   d = 2: x_2 e^{x_1 x_2} / (e - 2) - 1
+    oakley    d = 2: g((x - 1/2)/50), g(t) = 5 + t_1 + t_2 + 2 cos t_1 + 2 cos t_2
+    gfun      any d: prod_j (|4 x_j - 2| - a_j) / (1 + a_j), a_j = (j - 2)/2
+    genz_osc  any d: cos(-sum_j c_j x_j), oscillatory coefficients
+    genz_cp   any d: (1 + sum_j c_j x_j)^-(d + 1), corner-peak coefficients
+    """
+    x = np.asarray(x, dtype=np.float64)
+    d = x.shape[-1]
+    if name == "simple1":
+        return x[..., 0] * np.exp(x[..., 0]) - 1.0
+    if name == "simple2":
+        return x[..., 1] * np.exp(x[..., 0] * x[..., 1]) / (math.e - 2.0) - 1.0
+    if name == "oakley":
+        t = (x - 0.5) / 50.0
+        return 5.0 + t[..., 0] + t[..., 1] + 2.0 * np.cos(t[..., 0]) + 2.0 * np.cos(t[..., 1])
+    if name == "gfun":
+        a = (np.arange(1, d + 1, dtype=np.float64) - 2.0) / 2.0
+        return np.prod((np.abs(4.0 * x - 2.0) - a) / (1.0 + a), axis=-1)
+    if name == "genz_osc":
+        return np.cos(-(x @ _genz_coefficients("oscillatory", d)))
+    if name == "genz_cp":
+        return (1.0 + x @ _genz_coefficients("corner", d)) ** (-(d + 1))
+    raise KeyError(name)
+
+
+def integrand_mean(name: str, d: int) -> float:
+    """Exact means of the integrands over [0,1]^d (closed forms, for pinning):
+    simple1, simple2: 0 (int_0^1 x e^x dx = 1; int int x_2 e^{x_1 x_2} = e - 2);
+    oakley: 5 + 4 sin(1/100) / (1/100) (t uniform on [-1/100, 1/100]);
+    gfun: prod_j (1 - a_j)/(1 + a_j) (E|4x - 2| = 1);
+    genz_osc: Re prod_j (1 - e^{-i c_j}) / (i c_j);
+    genz_cp: sum_{v in {0,1}^d} (-1)^|v| / (1 + c.v), over d! prod_j c_j (iterated integration)."""
+    if name in ("simple1", "simple2"):
+        return 0.0
+    if name == "oakley":
+        return 5.0 + 4.0 * math.sin(0.01) / 0.01
+    if name == "gfun":
+        a = (np.arange(1, d + 1, dtype=np.float64) - 2.0) / 2.0
+        return float(np.prod((1.0 - a) / (1.0 + a)))
+    if name == "genz_osc":
+        c = _genz_coefficients("oscillatory", d)
+        return float(np.real(np.prod((1.0 - np.exp(-1j * c)) / (1j * c))))
+    if name == "genz_cp":
+        c = _genz_coefficients("corner", d)
+        total = Fraction(0)
+        for mask in range(1 << d):
+            v = [(mask >> j) & 1 for j in range(d)]
+            s = 1.0 + sum(cj for cj, vj in zip(c, v) if vj)
+            total += Fraction((-1) ** sum(v)) / Fraction(s)
+        return float(total / (math.factorial(d) * Fraction(float(np.prod(c)))))
+    raise KeyError(name)
+
+
+# ------------------------------------------------- RQMC estimate with a Student-t interval
+
+
+def rqmc_estimate(y, tau: float):
+    """RQMC estimate from R randomizations (Sec. 3.1, Eq. RQMC): mu_r = mean_i y[r, i],
+    mu = mean_r mu_r, sigma^2 = sum_r (mu_r - mu)^2 / (R - 1), and the 100(1 - tau)%
+    interval mu +- t_{R-1, tau/2} sigma / sqrt(R) with the Student-t quantile (scipy)."""
+    import scipy.stats
+    y = np.asarray(y, dtype=np.float64)
+    R = y.shape[0]
+    mu_r = y.mean(axis=1)
+    mu = float(mu_r.mean())
+    sigma = float(np.sqrt(np.sum((mu_r - mu) ** 2) / (R - 1)))
+    t_star = float(-scipy.stats.t.ppf(tau / 2.0, df=R - 1))
+    return {"mu_r": mu_r, "mu": mu, "sigma": sigma, "t": t_star, "half_width": t_star * sigma / math.sqrt(R)}
+
+
+# ---------------------------------- kernel discrepancy / worst-case error (Sec. 3.2)
+
+
+def kernel_mean_1d(family: str, alpha: int, x_word: int, grid_bits: int = 16) -> float:
+    """int_0^1 K_alpha(u, x) du for one 32-bit point x by the left-point rule on the 2^-grid
+    grid (the grid is closed under (-) x's top digits, so for DSI kernels the rule sums
+    K_alpha over a shifted grid); used to pin kappa_i = int K(u, x_i) du."""
+    u = (np.arange(1 << grid_bits, dtype=np.uint64) << np.uint64(32 - grid_bits)).astype(np.uint32)
+    diff = pair_difference(family, u, np.uint32(x_word))
+    return float(np.mean(factor_values(family, alpha, diff)))
+
+
+def discrepancy2_dense(family, alpha, X, c, zeta, w) -> float:
+    """Squared worst-case error of the cubature sum_i w_i f(x_i) in the RKHS of K (Sec. 3.2):
+    int int K - 2 sum_i w_i kappa_i + w^T K w, with the dense Gram matrix (no nugget),
+    kappa_i = int K(u, x_i) du = zeta and int int K = zeta (each one-dimensional K_alpha
+    integrates to zero, pinned by kernel_mean_1d)."""
+    K = gram_dense(family, alpha, X, c, zeta, 0.0)
+    w = np.asarray(w, dtype=np.float64)
+    kappa = np.full(X.shape[0], float(zeta))
+    return float(zeta - 2.0 * w @ kappa + w @ K @ w)
+
+
+def optimal_weights_dense(family, alpha, X, c, zeta, eta=0.0) -> np.ndarray:
+    """Weights minimising the squared worst-case error: w* = K^-1 kappa (Sec. 3.2), by Cholesky."""
+    K = gram_dense(family, alpha, X, c, zeta, eta)
+    sol, _ = cholesky_solve(K, np.full(X.shape[0], float(zeta)))
+    return sol
+
+
+def discrepancy2_spectral(family, lam, w, zeta) -> float:
+    """The same squared worst-case error through the spectrum (Sec. 5.4): w^T K w = w . K w with
+    K w = V(w~ lambda)."""
+    w = np.asarray(w, dtype=np.float64)
+    return float(zeta - 2.0 * zeta * np.sum(w) + w @ spectral_matvec(family, lam, w))
