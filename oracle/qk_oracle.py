@@ -206,7 +206,7 @@ def walsh_power_series(Z) -> np.ndarray:
 
 
 def dsi_kernel_walsh_series(alpha: int, Z: int, a_max: int = 160, base: float = 2.0,
-                            scale: float = 1.0, parts: bool = False):
+                            scale: float = 1.0, parts: bool = False, digits: int = 32):
     """Exact evaluation of the Walsh series of Eq. (DSI kernel), Sec. 5.3, for one word Z.
 
     K_alpha(x) = sum_{k>=1} wal_k(x) / base^{mu_alpha(k)} with mu_alpha(k) the sum of
@@ -218,10 +218,11 @@ def dsi_kernel_walsh_series(alpha: int, Z: int, a_max: int = 160, base: float = 
     a_max (every neglected term is below 2^-a_max * poly(a_max)).
     ``base=4, scale=2`` gives the first-order kernel reading.  With ``parts=True`` the
     result is (s_1, ..., s_{alpha-1}, tilde s_alpha): the sums over k with exactly nu
-    nonzero digits and with at least alpha (the decomposition of Appendix B).
+    nonzero digits and with at least alpha (the decomposition of Appendix B).  ``digits``
+    is the word length t_max (x = Z 2^-digits; 64 for interlaced higher-order nets).
     """
     Z = int(Z)
-    s = [(-1.0 if (a < 32 and (Z >> (31 - a)) & 1) else 1.0) for a in range(a_max)]
+    s = [(-1.0 if (a < digits and (Z >> (digits - 1 - a)) & 1) else 1.0) for a in range(a_max)]
     v = [s[a] * base ** (-(a + 1)) for a in range(a_max)]
     # sets with 1 <= |A| <= alpha - 1: elementary symmetric polynomials e_p(v)
     e = [1.0] + [0.0] * alpha
@@ -233,7 +234,7 @@ def dsi_kernel_walsh_series(alpha: int, Z: int, a_max: int = 160, base: float = 
     # P(a) = 2^a when digits x_1..x_a vanish, else 0.  Ascending a, a is the new largest.
     F = [0.0] * (alpha + 1)
     for a in range(a_max):
-        w = v[a] * 2.0 ** a if all_zero_below(a, Z) else 0.0
+        w = v[a] * 2.0 ** a if all_zero_below(a, Z, digits) else 0.0
         for q in range(alpha, 1, -1):
             F[q] += v[a] * F[q - 1]
         F[1] += w
@@ -253,13 +254,13 @@ def walsh_function(k: int, Z) -> np.ndarray:
     return 1.0 - 2.0 * parity.astype(np.float64)
 
 
-def all_zero_below(a: int, Z: int) -> bool:
-    """True when digits x_1..x_a of x = Z 2^-32 are all zero (free low bits sum to 2^a)."""
+def all_zero_below(a: int, Z: int, digits: int = 32) -> bool:
+    """True when digits x_1..x_a of x = Z 2^-digits are all zero (free low bits sum to 2^a)."""
     if a == 0:
         return True
-    if a >= 32:
+    if a >= digits:
         return Z == 0
-    return (Z >> (32 - a)) == 0
+    return (Z >> (digits - a)) == 0
 
 
 # -------------------------------------------------------- SI kernels (Sec. 5.2)
@@ -709,3 +710,112 @@ def discrepancy2_spectral(family, lam, w, zeta) -> float:
     K w = V(w~ lambda)."""
     w = np.asarray(w, dtype=np.float64)
     return float(zeta - 2.0 * zeta * np.sum(w) + w @ spectral_matvec(family, lam, w))
+
+
+# ------------------------------------------- higher-order digital nets (Sec. 4.3)
+
+
+def interlace(A, alpha: int, t_out: int = 64) -> np.ndarray:
+    """Digital interlacing of order alpha (Sec. 4.3, "Digital interlacing for higher-order
+    nets"): generator columns A (alpha d, 32) of 32-digit words (column k, bit 31 - t =
+    digit t) -> d interlaced matrices with alpha 32 digits, of which the first t_out are
+    kept (digits past t_out lie below 2^-t_out).  Entry (t, k) of the j-th interlaced matrix
+    (1-based j) is entry (floor(t / alpha), k) of matrix alpha (j - 1) + (t mod alpha) + 1.
+    Returns (d, 32) uint64 words, bit (63 - t) = digit t (t < t_out <= 64)."""
+    A = np.asarray(A, dtype=np.uint64)
+    d = A.shape[0] // alpha
+    t_max = min(t_out, 32 * alpha)
+    out = np.zeros((d, 32), dtype=np.uint64)
+    for j in range(1, d + 1):
+        for t in range(t_max):
+            src = alpha * (j - 1) + (t % alpha) + 1          # 1-based source matrix
+            t_src = t // alpha
+            bit = (A[src - 1] >> np.uint64(31 - t_src)) & np.uint64(1)
+            out[j - 1] |= bit << np.uint64(63 - t)
+    return out
+
+
+def ho_net_points(Chat, D, idx, m: int, order: str = "gray") -> np.ndarray:
+    """Higher-order digital net points as 64-digit words: z = Chat_j D_m(k) mod 2 with k = i
+    or its Gray code, digitally shifted by the 64-digit D_j (Sec. 4.3).  Chat: (d, 32) uint64
+    interlaced columns; D: (d,) uint64.  Returns (len(idx), d) uint64."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    k = gray_code(idx) if order == "gray" else idx
+    Chat = np.asarray(Chat, dtype=np.uint64)
+    d = Chat.shape[0]
+    X = np.zeros((idx.size, d), dtype=np.uint64)
+    for t in range(m):
+        digit = ((k >> np.uint64(t)) & np.uint64(1)).astype(bool)
+        for j in range(d):
+            X[digit, j] ^= Chat[j, t]
+    X ^= np.asarray(D, dtype=np.uint64)[None, :]
+    return X
+
+
+def deinterlace_point(Xhat, alpha: int, digits: int = 64) -> np.ndarray:
+    """The alpha d coordinates (as 32-digit words, digits beyond those kept set to 0) whose
+    interlacing gives the points Xhat (n, d) uint64: coordinate alpha j + u takes digits
+    u, u + alpha, u + 2 alpha, ... of Xhat_j (0-based)."""
+    Xhat = np.asarray(Xhat, dtype=np.uint64)
+    n, d = Xhat.shape
+    out = np.zeros((n, alpha * d), dtype=np.uint64)
+    for j in range(d):
+        for t in range(min(digits, 32 * alpha)):
+            bit = (Xhat[:, j] >> np.uint64(63 - t)) & np.uint64(1)
+            out[:, alpha * j + t % alpha] |= bit << np.uint64(31 - t // alpha)
+    return out.astype(np.uint32)
+
+
+def dsi_kernel_words(alpha: int, Z, digits: int = 64) -> np.ndarray:
+    """K_alpha(x) of the Theorem (Sec. 5.3) at x = Z 2^-digits for words of `digits` digits
+    (64 for interlaced nets): beta(x) = -floor(log2 x) is the position of the first nonzero
+    digit, t_nu = 2^(-nu beta), and K_4's series sum_a wal_{2^a}(x) 8^-a runs over the
+    `digits` digits (later digits 0): 8/7 - 2 sum_{a < digits, x_{a+1} = 1} 8^-a."""
+    Zs = [int(z) for z in np.asarray(Z, dtype=np.uint64).ravel()]
+    out = np.empty(len(Zs))
+    for q, z in enumerate(Zs):
+        if z == 0:
+            beta, x, t1 = 0, 0.0, 0.0
+        else:
+            beta = digits - z.bit_length() + 1
+            x = float(Fraction(z, 1 << digits))
+            t1 = 2.0 ** -beta
+        b = float(beta)
+        t2, t3 = t1 * t1, t1 * t1 * t1
+        if alpha == 1:
+            out[q] = 1.0 - 3.0 * t1 if z else 1.0
+        elif alpha == 2:
+            out[q] = -1.0 - b * x + 2.5 * (1.0 - t1)
+        elif alpha == 3:
+            out[q] = -1.0 + b * x ** 2 - 5.0 * (1.0 - t1) * x + (43.0 / 18.0) * (1.0 - t2)
+        elif alpha == 4:
+            S = Fraction(8, 7)
+            for a in range(digits):
+                if (z >> (digits - 1 - a)) & 1:
+                    S -= 2 * Fraction(1, 8 ** a)
+            out[q] = (-1.0 - (2.0 / 3.0) * b * x ** 3 + 5.0 * (1.0 - t1) * x ** 2
+                      - (43.0 / 9.0) * (1.0 - t2) * x + (701.0 / 294.0) * (1.0 - t3)
+                      + b * (float(S) / 48.0 - 1.0 / 42.0))
+        else:
+            raise ValueError(f"DSI order {alpha} not supported")
+    return out.reshape(np.shape(Z))
+
+
+def ho_first_column(alpha_k: int, Xhat, c, zeta=1.0) -> np.ndarray:
+    """k_1[i] = zeta prod_j (1 + c_j K_alpha(x_ij (-) x_0j)) for 64-digit points (Sec. 5.3-5.4)."""
+    Xhat = np.asarray(Xhat, dtype=np.uint64)
+    out = np.full(Xhat.shape[0], float(zeta))
+    for j in range(Xhat.shape[1]):
+        out *= 1.0 + c[j] * dsi_kernel_words(alpha_k, Xhat[:, j] ^ Xhat[0, j])
+    return out
+
+
+def ho_gram_dense(alpha_k: int, Xhat, c, zeta=1.0, eta=0.0) -> np.ndarray:
+    """Dense Gram matrix of the product DSI kernel on 64-digit points, plus eta I."""
+    Xhat = np.asarray(Xhat, dtype=np.uint64)
+    n = Xhat.shape[0]
+    K = np.full((n, n), float(zeta))
+    for j in range(Xhat.shape[1]):
+        Z = Xhat[:, j][:, None] ^ Xhat[None, :, j]
+        K *= 1.0 + c[j] * dsi_kernel_words(alpha_k, Z)
+    return K + eta * np.eye(n)

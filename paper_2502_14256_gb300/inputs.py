@@ -126,6 +126,29 @@ def make_net(seed: int, d: int, R: int, order: str = "gray") -> NetInputs:
 
 
 @dataclass
+class HONetInputs:
+    d: int                    # dimensions of the interlaced (higher-order) net
+    alpha: int                # interlacing order
+    R: int
+    C: np.ndarray             # (alpha d, 32) u32 generator columns of the underlying net
+    S: np.ndarray             # (R, alpha d, 32) u32 LMS row masks
+    D: np.ndarray             # (R, d) u64 digital shifts with 64 digits
+    order: str
+
+
+def make_ho_net(seed: int, d: int, alpha: int, R: int, order: str = "gray") -> HONetInputs:
+    """Inputs of an order-alpha interlaced net in d dimensions: the alpha d generator matrices
+    (the first the identity, the others random upper unit-triangular), an LMS scramble per
+    randomization and matrix, and a 64-digit digital shift per randomization and dimension."""
+    base = make_net(seed, alpha * d, R, order)
+    rng = SplitMix64(seed + 0x5EED)
+    hi = rng.u32(R * d).astype(np.uint64)
+    lo = rng.u32(R * d).astype(np.uint64)
+    D = ((hi << np.uint64(32)) | lo).reshape(R, d)
+    return HONetInputs(d=d, alpha=alpha, R=R, C=base.C, S=base.S, D=D, order=order)
+
+
+@dataclass
 class LatticeInputs:
     d: int
     R: int
