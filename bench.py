@@ -10,13 +10,19 @@ mean/variance), MLL gradient back-transform and reduction, and the solve with on
 refinement step.  Inputs are resident in HBM (y alone is 256 MB, twice the L2).
 
 The headline `value` is points/s (randomizations x n / step time) of the FP32 path
-(FP32 column and transforms, FP64 division / log det / variance, one refinement
-step); the plain FP64 path is timed beside it.  `--impl reference` times the FP64
-CPU oracle on a bounded sample of the same workload.
+(FP32 column and transforms, FP64 / float-float reductions, one refinement step); beside
+it the same step with the float-float first column (QK_F32W), the plain FP64 path, point
+generation, and the FWHT / FFTBR transforms alone.  `--impl reference` times the FP64 CPU
+oracle on a bounded sample of the same workload.
+
+`--profile CASE` runs one small self-contained invocation of a hot kernel instead (for a
+profiler: ncu -k <kernel> -c <n> python bench.py --profile fused --R 8); it prints "ok".
 """
 from __future__ import annotations
 
 import argparse
+import glob
+import hashlib
 import json
 import math
 import os
@@ -34,6 +40,18 @@ sys.path.insert(0, ROOT)
 METRIC = "structured-Gram solve+grad points/s at n=2^20 (FP32-refined vs plain FP64), FWHT HBM GB/s"
 UNIT = "points/s"
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes per launch) of the fused
+# kernels at 64 randomizations of n = 2^20, d = 16, from one ncu capture, and the hash of the
+# CUDA sources that capture ran (kernel_source_hash()).  A run whose sources differ reports
+# traffic null: the counters belong to another version of the kernels.
+NCU_TRAFFIC = {
+    "src_hash": None,
+    "bytes_r64": {},
+    "fwht_bytes": None,
+}
+# Nominal FP64 rate of GB300 (profiling recipe's table; FP64 is not a tensor-core path here).
+FP64_PEAK_TFLOPS = 1.25
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -50,7 +68,24 @@ def parse():
     ap.add_argument("--sched", default="auto", choices=["auto", "launches", "persistent"],
                     help="batched schedule: tuned (auto), per-phase launches or one persistent launch")
     ap.add_argument("--lag", type=int, default=1, help="persistent schedule: units between phases")
+    ap.add_argument("--profile", default=None, choices=["fused", "fwht", "fftbr", "points", "col"],
+                    help="run one small case of a hot kernel (for a profiler) instead of the benchmark")
+    ap.add_argument("--reps", type=int, default=2, help="--profile: runs after one warm-up")
+    ap.add_argument("--fp64", action="store_true", help="--profile fused/fftbr/col: FP64")
+    ap.add_argument("--wide", action="store_true", help="--profile fused/col: float-float first column")
+    ap.add_argument("--two-pass", action="store_true", help="--profile fwht: two-launch form")
+    ap.add_argument("--persistent", action="store_true", help="--profile fused: one persistent launch")
+    ap.add_argument("--d", type=int, default=16, help="--profile points/col: dimensions")
     return ap.parse_args()
+
+
+def kernel_source_hash() -> str:
+    """Hash of the library's CUDA sources (which kernel version a measurement belongs to)."""
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2502_14256_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(os.path.basename(f).encode() + fh.read())
+    return h.hexdigest()[:12]
 
 
 # ------------------------------------------------------------------ clocks
@@ -147,13 +182,13 @@ def build_workload(qk, torch, dev, R, m, seed_offset=0):
 
 
 class Pipeline:
-    """One batched schedule (all randomizations) in a given precision."""
+    """One batched schedule (all randomizations) in a given precision (torch dtype or qk.F32W)."""
 
     def __init__(self, qk, torch, dev, W, dtype, refine, keep_lam=False):
         self.qk, self.torch = qk, torch
         R, n, d = W["R"], W["n"], W["d"]
-        # both precisions see the same inputs: y rounded to FP32 once
-        self.y = W["y64"].to(torch.float32).to(dtype).contiguous()
+        # every precision sees the same inputs: y rounded to FP32 once
+        self.y = W["y64"].to(torch.float32).to(qk.data_dtype(dtype)).contiguous()
         self.c = torch.empty_like(self.y)
         self.lam = torch.empty((R, n), dtype=torch.float64, device=dev)
         self.out = torch.empty((R, 1, qk.QK_MLL_NOUT), dtype=torch.float64, device=dev)
@@ -169,6 +204,15 @@ class Pipeline:
 
     def step(self, stream=None):
         self.qk.batch_run(self.ws, self.status, stream=stream)
+
+    def kernel_ms(self, torch, steps, stream):
+        """Per-kernel device milliseconds per step: a separate pass of `steps` steps with a CUDA
+        event pair around every kernel (on the launching stream)."""
+        self.qk.batch_timing(self.ws, steps)
+        time_steps(torch, self.step, steps, 0, stream)
+        out = self.qk.batch_kernel_ms(self.ws)
+        self.qk.batch_timing(self.ws, 0)
+        return {k: (v[0] / steps, v[1] / steps) for k, v in out.items()}
 
 
 def time_steps(torch, fn, steps, warmup, stream):
@@ -223,9 +267,69 @@ def workload_config(m, d, R, world):
             "l2": "inputs larger than L2 (y alone 256 MB)"}
 
 
+# ------------------------------------------------------------- profile cases
+def profile_case(args):
+    """One small invocation of a hot kernel (1 warm-up + reps runs), for ncu -k ... -c ..."""
+    import torch
+    from paper_2502_14256_gb300 import build
+    build.build()
+    from paper_2502_14256_gb300 import inputs, qk
+    dev = torch.device("cuda:0")
+    R, m = args.R, args.m
+    n = 1 << m
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    if args.profile == "fwht":
+        x = torch.randn((R, n), dtype=torch.float32, device=dev)
+        ws = qk.fwht_workspace(R, dev)
+        plan = dict(mode=qk.QK_FWHT_TWO_PASS if args.two_pass else qk.QK_FWHT_PERSISTENT)
+        run = lambda: qk.fwht_ws(m, x, ws, plan=plan, status=status)  # noqa: E731
+    elif args.profile == "fftbr":
+        x = torch.randn((R, 2 * n), dtype=torch.float64 if args.fp64 else torch.float32, device=dev)
+        run = lambda: qk.fftbr(m, x)  # noqa: E731
+    else:
+        wl = inputs.workload("solve20")
+        d = args.d if args.profile in ("points", "col") else wl.d
+        net = inputs.make_net(wl.seed, d, R, wl.order)
+        u32 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)  # noqa: E731
+        C, S, D = u32(net.C), u32(net.S), u32(net.D)
+        Ct = torch.empty((R, d, 32), dtype=torch.int32, device=dev)
+        qk.lms_setup(C, S, Ct)
+        ps = qk.pointset(qk.QK_NET_B2, d, R, Ct=Ct, D=D, order=qk.QK_GRAY)
+        w = torch.tensor(0.9 ** np.arange(1, d + 1), dtype=torch.float64, device=dev)
+        kern = qk.kernel(qk.QK_DSI, wl.alpha, w, wl.zeta)
+        if args.profile == "points":
+            X = torch.empty((R, n, d), dtype=torch.int32, device=dev)
+            run = lambda: qk.gen_points(ps, 0, R, 0, n, X)  # noqa: E731
+        elif args.profile == "col":
+            col = torch.empty((R, n), dtype=torch.float64 if (args.fp64 or args.wide) else torch.float32, device=dev)
+            run = lambda: qk.kernel_col(ps, kern, 0, R, m, col, form=qk.QK_COL_P, wide=args.wide)  # noqa: E731
+        else:
+            dt = torch.float64 if args.fp64 else (qk.F32W if args.wide else torch.float32)
+            g = torch.Generator(device=dev).manual_seed(wl.seed)
+            y = torch.randn((R, 1, n), dtype=qk.data_dtype(dt), device=dev, generator=g)
+            c = torch.empty_like(y)
+            out = torch.empty((R, 1, qk.QK_MLL_NOUT), dtype=torch.float64, device=dev)
+            grad = torch.empty((R, 1, 2 * d + 2), dtype=torch.float64, device=dev)
+            task = qk.Task(ps, kern, m, 1, wl.eta, y.data_ptr(), c.data_ptr(), None, out.data_ptr(),
+                           grad.data_ptr())
+            ws = qk.workspace(qk.batch_workspace_bytes([task], dt))
+            qk.batch_plan([task], dt, args.refine, ws)
+            if args.persistent:
+                qk.batch_schedule(ws, qk.QK_SCHED_PERSISTENT, 1)
+            run = lambda: qk.batch_run(ws, status)  # noqa: E731
+    for _ in range(1 + args.reps):
+        run()
+    torch.cuda.synchronize()
+    qk.read_status(status)
+    print("ok")
+    return 0
+
+
 # ---------------------------------------------------------------- main
 def main():
     args = parse()
+    if args.profile:
+        return profile_case(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -249,7 +353,8 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": workload_config(args.m, wl.d, args.R, args.gpus),
-                "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1, "sample": sample},
+                "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
+                                 "host_cores": os.cpu_count(), "sample": sample},
                 "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return 0
@@ -269,6 +374,7 @@ def main():
 
     W = build_workload(qk, torch, dev, args.R, args.m, seed_offset=replica_seed_offset(rank))
     stream = torch.cuda.current_stream()
+    R, n, m, d = W["R"], W["n"], W["m"], W["d"]
 
     # ---- the headline: FP32-refined pipeline, device-resident inputs
     P32 = Pipeline(qk, torch, dev, W, torch.float32, refine=args.refine)
@@ -286,24 +392,22 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     launches0 = qk.launch_count()
-    qk.batch_timing(P32.ws, args.steps)  # CUDA events around each kernel of the timed steps
     ms = time_steps(torch, P32.step, args.steps, 0, stream)
     launches = qk.launch_count() - launches0
     clocks = sampler.stop()
-    kernel_ms = qk.batch_kernel_ms(P32.ws)
-    qk.batch_timing(P32.ws, 0)
     if world > 1:
         dist.barrier()
     ms = max_over_ranks(ms, torch, dist, world, dev)
-    points_step = world * W["R"] * W["n"]
-    value = job_throughput(W["R"] * W["n"], world, ms)
+    points_step = world * R * n
+    value = job_throughput(R * n, world, ms)
+    # per-kernel times of the same step, in a separate pass with CUDA events around each kernel
+    kernel_ms = P32.kernel_ms(torch, args.steps, stream)
 
     # ---- end to end through the public API with host buffers (pinned)
     y_host = P32.y.cpu().pin_memory()
     c_host = torch.empty_like(P32.c, device="cpu").pin_memory()
     o_host = torch.empty_like(P32.out, device="cpu").pin_memory()
     g_host = torch.empty_like(P32.grad, device="cpu").pin_memory()
-
     host_io = [dict(y=y_host, c=c_host, out=o_host, grad=g_host)]
 
     def e2e_step():
@@ -315,55 +419,77 @@ def main():
     e2e_ms = max_over_ranks(e2e_ms, torch, dist, world, dev)
     h2d = y_host.numel() * y_host.element_size()
     d2h = sum(t.numel() * t.element_size() for t in (c_host, o_host, g_host))
+    del y_host, c_host, o_host, g_host, host_io
 
     # ---- stage timing of the FP32 path (which stage dominates)
-    from paper_2502_14256_gb300 import qk as q
-    R, n, m, d = W["R"], W["n"], W["m"], W["d"]
     col = torch.empty((R, n), dtype=torch.float32, device=dev)
-    kern = q.kernel(q.QK_DSI, W["wl"].alpha, W["w"], W["wl"].zeta)
-    stage = {}
-    stage["kernel_col"] = time_steps(torch, lambda: q.kernel_col(W["ps"], kern, 0, R, m, col, form=q.QK_COL_P),
-                                     3, 1, stream)
+    kern = qk.kernel(qk.QK_DSI, W["wl"].alpha, W["w"], W["wl"].zeta)
+    stage = {"kernel_col": time_steps(torch, lambda: qk.kernel_col(W["ps"], kern, 0, R, m, col, form=qk.QK_COL_P),
+                                      3, 1, stream)}
     # doubling update (extensible n): eigenvalues of the 2^m-point sets from those of their
     # first 2^(m-1) points plus the new half's column and one half-length transform,
     # against computing the full column and transform
     lam_full = torch.empty((R, n), dtype=torch.float64, device=dev)
     lam_half = torch.empty((R, n // 2), dtype=torch.float64, device=dev)
     col_half = torch.empty((R, n // 2), dtype=torch.float32, device=dev)
-    ws_e = q.workspace(q.workspace_bytes(q.OP_EIGS, q.QK_DSI, m, R, 1, torch.float32), dev)
+    ws_e = qk.workspace(qk.workspace_bytes(qk.OP_EIGS, qk.QK_DSI, m, R, 1, torch.float32), dev)
     eta_ = W["wl"].eta
 
     def eig_full():
-        q.kernel_col(W["ps"], kern, 0, R, m, col, form=q.QK_COL_P)
-        q.eigs(q.QK_DSI, m, col, lam_full, zeta=W["wl"].zeta, eta=eta_, form=q.QK_COL_P, ws=ws_e)
+        qk.kernel_col(W["ps"], kern, 0, R, m, col, form=qk.QK_COL_P)
+        qk.eigs(qk.QK_DSI, m, col, lam_full, zeta=W["wl"].zeta, eta=eta_, form=qk.QK_COL_P, ws=ws_e)
 
-    q.kernel_col(W["ps"], kern, 0, R, m - 1, col_half, form=q.QK_COL_P)
-    q.eigs(q.QK_DSI, m - 1, col_half, lam_half, zeta=W["wl"].zeta, eta=eta_, form=q.QK_COL_P, ws=ws_e)
+    qk.kernel_col(W["ps"], kern, 0, R, m - 1, col_half, form=qk.QK_COL_P)
+    qk.eigs(qk.QK_DSI, m - 1, col_half, lam_half, zeta=W["wl"].zeta, eta=eta_, form=qk.QK_COL_P, ws=ws_e)
 
     def eig_extend():
-        q.kernel_col_at(W["ps"], kern, 0, R, n // 2, m - 1, col_half, form=q.QK_COL_P)
-        q.eigs_extend(q.QK_DSI, m - 1, col_half, lam_half, lam_full, zeta=W["wl"].zeta, eta=eta_,
-                      form=q.QK_COL_P, ws=ws_e)
+        qk.kernel_col_at(W["ps"], kern, 0, R, n // 2, m - 1, col_half, form=qk.QK_COL_P)
+        qk.eigs_extend(qk.QK_DSI, m - 1, col_half, lam_half, lam_full, zeta=W["wl"].zeta, eta=eta_,
+                       form=qk.QK_COL_P, ws=ws_e)
 
     doubling = {"eigs_full_ms": time_steps(torch, eig_full, 3, 1, stream),
                 "eigs_extend_ms": time_steps(torch, eig_extend, 3, 1, stream),
                 "what": f"{R} x 2^{m} FP32 column + eigenvalues: from scratch vs from the first 2^{m - 1} points"}
-    del lam_full, lam_half, col_half, ws_e
+    del lam_full, lam_half, col_half, ws_e, col
+
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    src_hash = kernel_source_hash()
+    ncu_ok = NCU_TRAFFIC["src_hash"] == src_hash and (R, m, d) == (64, 20, 16)
+
+    # ---- point generation (a2): 32-bit words of every point, stored (R, n, d)
+    Xp = torch.empty((R, n, d), dtype=torch.int32, device=dev)
+    gen_ms = time_steps(torch, lambda: qk.gen_points(W["ps"], 0, R, 0, n, Xp), max(3, args.steps // 2), 1, stream)
+    gen_bytes = 4 * R * n * d
+    points = {"gbs": gen_bytes / (gen_ms * 1e-3) / 1e9, "ms": gen_ms, "bytes": gen_bytes,
+              "frac_of_hbm": gen_bytes / (gen_ms * 1e-3) / 1e9 / hbm_peak, "peak": hbm_peak, "peak_source": peak_src,
+              "shape": f"{R} x 2^{m} x {d} u32 (Gray order, LMS + digital shift), store-bound: 4 n d R bytes"}
+    del Xp
 
     # FWHT alone on the same data volume (in place, FP32): HBM roofline of the transform
     xf = torch.randn((R, n), dtype=torch.float32, device=dev)
-    fw_ws = q.fwht_workspace(R, dev)
-    fw_plan = q.fwht_tune(m, xf, fw_ws)  # autotuned plan (xf is scratch here)
-    fw_ms = time_steps(torch, lambda: q.fwht_ws(m, xf, fw_ws), args.steps, 2, stream)
-    fw2_ms = time_steps(torch, lambda: q.fwht(m, xf), args.steps, 2, stream)
+    fw_ws = qk.fwht_workspace(R, dev)
+    fw_plan = qk.fwht_tune(m, xf, fw_ws)  # autotuned plan (xf is scratch here)
+    fw_ms = time_steps(torch, lambda: qk.fwht_ws(m, xf, fw_ws), args.steps, 2, stream)
+    fw2_ms = time_steps(torch, lambda: qk.fwht(m, xf), args.steps, 2, stream)
     fw_bytes = 2 * xf.numel() * 4  # one read + one write per element (the algorithmic minimum)
     fw_gbs = fw_bytes / (fw_ms * 1e-3) / 1e9
     del xf, fw_ws
     # FFTBR (the lattice transform) on R complex FP32 vectors of the same length
     xc = torch.randn((R, 2 * n), dtype=torch.float32, device=dev)
-    ff_ms = time_steps(torch, lambda: q.fftbr(m, xc), args.steps, 2, stream)
+    ff_ms = time_steps(torch, lambda: qk.fftbr(m, xc), args.steps, 2, stream)
     ff_bytes = 2 * xc.numel() * 4
     del xc
+
+    # ---- the same step with the float-float first column (QK_F32W): its cost beside the headline
+    PW = Pipeline(qk, torch, dev, W, qk.F32W, refine=args.refine, keep_lam=True)
+    wide_ms = time_steps(torch, PW.step, max(3, args.steps // 2), 1, stream)
+    wide = {"value": points_step / (wide_ms * 1e-3), "ms_per_step": wide_ms, "cost_vs_headline": wide_ms / ms,
+            "kernels_ms_per_step": {k: v[1] for k, v in PW.kernel_ms(torch, 2, stream).items()}}
 
     # ---- plain FP64 pipeline beside it
     fp64 = None
@@ -371,67 +497,67 @@ def main():
         P64 = Pipeline(qk, torch, dev, W, torch.float64, refine=0, keep_lam=True)
         ms64 = time_steps(torch, P64.step, max(1, min(3, args.steps)), 1, stream)
         fp64 = {"value": points_step / (ms64 * 1e-3), "ms_per_step": ms64}
-        # accuracy of the FP32 path against the FP64 GPU path, per output (one untimed
+        k64 = P64.kernel_ms(torch, 1, stream)
+        top64, (l64, t64) = max(k64.items(), key=lambda kv: kv[1][1])
+        # FP64 FMA-pipe roofline of the FP64 path's longest kernel (algorithmic flops per
+        # point below; 12-bit tile transforms in FP64)
+        fl64 = {"k_fused_A": 8 * d + 2 * 12 + 2, "k_fused_C": 10 * d + 2 * 12 + 3}.get(top64)
+        if fl64:
+            ach = fl64 * R * n / (t64 / max(1.0, l64) * 1e-3) / 1e12
+            fp64["roofline"] = {"kernel": top64, "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)", "ms_per_launch": t64 / max(1.0, l64)}
+        fp64["kernels_ms_per_step"] = {k: v[1] for k, v in k64.items()}
+        # accuracy of the FP32 paths against the FP64 GPU path, per output (one untimed
         # FP32 run that also writes its eigenvalues)
         P32L = Pipeline(qk, torch, dev, W, torch.float32, refine=args.refine, keep_lam=True)
         P32L.step()
-        P32 = P32L
+        PW.step()
         torch.cuda.synchronize()
         rel = lambda a, b: float((a.double() - b.double()).abs().max() / b.double().abs().max())  # noqa: E731
-        fp64["fp32_rel_err"] = {
-            "solve_c": rel(P32.c, P64.c), "lambda": rel(P32.lam, P64.lam),
-            "quad": rel(P32.out[..., 0], P64.out[..., 0]), "logdet": rel(P32.out[..., 1], P64.out[..., 1]),
-            "mll": rel(P32.out[..., 2], P64.out[..., 2]), "post_mean": rel(P32.out[..., 3], P64.out[..., 3]),
-            "grad_dc": rel(P32.grad[..., :d], P64.grad[..., :d])}
-        del P64
+        for name, P in (("fp32_rel_err", P32L), ("wide_rel_err", PW)):
+            errs = {"solve_c": rel(P.c, P64.c), "lambda": rel(P.lam, P64.lam),
+                    "lambda_elementwise": float(((P.lam - P64.lam).abs() / P64.lam).max()),
+                    "quad": rel(P.out[..., 0], P64.out[..., 0]), "logdet": rel(P.out[..., 1], P64.out[..., 1]),
+                    "mll": rel(P.out[..., 2], P64.out[..., 2]), "post_mean": rel(P.out[..., 3], P64.out[..., 3]),
+                    "post_var": rel(P.out[..., 4], P64.out[..., 4]), "grad_dc": rel(P.grad[..., :d], P64.grad[..., :d])}
+            if name == "wide_rel_err":
+                wide["rel_err_vs_fp64"] = errs
+            else:
+                fp64[name] = errs
+        del P64, P32L
+    del PW
 
     # ---- roofline of the dominant kernel of the timed step
-    R_, n_, d_ = W["R"], W["n"], W["d"]
-    top = max(kernel_ms.items(), key=lambda kv: kv[1][1])
-    top_name, (top_launches, top_ms_total) = top
-    top_ms = top_ms_total / max(1, top_launches)
-    # FP32 peak from unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flop/FMA x clock
-    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    top_name, (top_launches, top_ms_step) = max(kernel_ms.items(), key=lambda kv: kv[1][1])
+    top_ms = top_ms_step / max(1.0, top_launches)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = (clocks.get("sm_max_mhz") or 2070.0) * 1e6
+    # FP32 non-tensor peak from unit counts and clock: SMs x 128 FP32 lanes x 2 flop/FMA x clock
+    fp32_peak = sms * 128 * 2 * clk / 1e12
     # algorithmic work per launch (per point and right-hand side, DSI order 2):
     #   gradient sweep 10 flops per dimension (K, f = 1 + c K, K/f, two accumulations),
     #   column sweep 8 flops per dimension (K, a = c K, p update),
     #   13-bit tile transforms 13 adds per vector.
-    flops_per_point = {"k_fused_C": 10 * d_ + 2 * 13 + 3, "k_fused_A": 8 * d_ + 2 * 13 + 2}
-    # DRAM bytes (read + write) per launch from one ncu capture of the same kernels at
-    # R = 64, n = 2^20, d = 16 (profiles/fused_pipeline_solve20.md); traffic is per
-    # randomization, so it scales with R.  Only valid for that m and d.
-    ncu_traffic_r64 = {"k_fused_C": 805.9e6 + 247.8e6, "k_fused_A": 268.7e6 + 1013.3e6}
-    # issue-slot utilisation of the same kernels from one ncu --set full capture at R = 8
-    # (profiles/fused_pipeline_solve20.md): the instruction-issue roofline these kernels sit on
-    ncu_issue_active = {"k_fused_A": 0.564, "k_fused_C": 0.596}
-    bound_note = {
-        "k_fused_A": "instruction-issue bound: per point and dimension a difference word, clz, "
-                     "coefficient row load, conversion, FMA polynomial and the p update "
-                     "(profiles/fused_pipeline_solve20.md)",
-        "k_fused_C": "issue and dependent-latency bound at 2 CTAs per SM: per point and dimension a "
-                     "difference word, clz, coefficient row load, conversion, reciprocal and two "
-                     "accumulations (profiles/fused_pipeline_solve20.md)"}
+    flops_per_point = {"k_fused_C": 10 * d + 2 * 13 + 3, "k_fused_A": 8 * d + 2 * 13 + 2}
     roof = None
     if top_name in flops_per_point:
-        work = flops_per_point[top_name] * R_ * n_
+        work = flops_per_point[top_name] * R * n
         ach = work / (top_ms * 1e-3) / 1e12
-        traffic = ncu_traffic_r64.get(top_name) if (W["m"], d_) == (20, 16) else None
+        tr = NCU_TRAFFIC["bytes_r64"].get(top_name) if ncu_ok else None
         roof = {"kernel": top_name, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": ach / fp32_peak, "traffic": traffic * R_ / 64 if traffic else None,
-                "ms_per_launch": top_ms, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                "issue_active_ncu": ncu_issue_active.get(top_name) if (W["m"], d_) == (20, 16) else None,
-                "note": bound_note.get(top_name, "")}
-    peaks = {}
-    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pk_path):
-        peaks = json.load(open(pk_path))
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+                "frac": ach / fp32_peak, "traffic": tr,
+                "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum of this kernel, "
+                                   f"sources {NCU_TRAFFIC['src_hash']}") if tr else "null: no capture of these sources",
+                "ms_per_launch": top_ms,
+                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x 2 flop x {clk / 1e9:.2f} GHz (sampled max clock)",
+                "algorithmic_bytes": 20 * R * n if top_name == "k_fused_A" else 16 * R * n}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
         v, sample = oracle_sample(W, min(18, m), 2, 0)  # ~10 s of host work
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(), "kind": "oracle",
+               "sample": sample}
 
     if rank == 0:
         line = {
@@ -444,21 +570,22 @@ def main():
             "gpu_launches": launches,
             "gpu_launches_per_step": launches / max(1, args.steps),
             "fp64_plain": fp64,
+            "wide": wide,
             "schedule": sched,
             "stages_ms": stage,
             "doubling": doubling,
-            "kernels_ms_per_step": {k: v[1] / max(1, args.steps) for k, v in kernel_ms.items()},
+            "kernels_ms_per_step": {k: v[1] for k, v in kernel_ms.items()},
+            "points": points,
             "fwht": {"gbs": fw_gbs, "ms": fw_ms, "frac_of_hbm": fw_gbs / hbm_peak, "bytes": fw_bytes,
                      "peak": hbm_peak, "peak_source": peak_src,
                      "shape": f"{R} x 2^{m} fp32, in place", "plan": fw_plan,
-                     # ncu: dram read + write of one persistent launch at 64 x 2^20
-                     # (profiles/fwht_persistent_64x2p20_fp32.md)
-                     "traffic": (275.9e6 + 326.0e6) if (R, m) == (64, 20) else None,
+                     "traffic": NCU_TRAFFIC["fwht_bytes"] if ncu_ok else None,
                      "two_launch_ms": fw2_ms, "two_launch_gbs": fw_bytes / (fw2_ms * 1e-3) / 1e9},
             "fftbr": {"gbs": ff_bytes / (ff_ms * 1e-3) / 1e9, "ms": ff_ms, "bytes": ff_bytes,
                       "frac_of_hbm": ff_bytes / (ff_ms * 1e-3) / 1e9 / hbm_peak,
                       "shape": f"{R} x 2^{m} complex fp32, in place, two tile passes"},
             "roofline": roof,
+            "kernel_sources": src_hash,
             "cpu_baseline": cpu,
             "clocks": clocks,
         }

@@ -71,7 +71,17 @@ enum qk_status_bits { QK_STATUS_NOTPD = 1u, QK_STATUS_TIMEOUT = 2u, QK_STATUS_FL
 enum qk_kind { QK_NET_B2 = 0, QK_LATTICE = 1 };
 enum qk_order { QK_NATURAL = 0, QK_GRAY = 1 };
 enum qk_family { QK_DSI = 0, QK_SI = 1 };
-enum qk_dtype { QK_F64 = 0, QK_F32 = 1 };
+/* QK_F32W: FP32 data and FP32 arithmetic, except that the first column is carried as
+ * float-float pairs (about 2^-46 relative per kernel factor, still on the FP32 pipes) and
+ * transformed with compensated (float-float) butterflies, so that every eigenvalue is
+ * accurate to about 2^-44 lambda_max before it is rounded, instead of eps32 ||k_1||.  Use
+ * it when the spectrum reaches far below eps32 lambda_max (a small nugget, many
+ * dimensions, large n): there an FP32 column moves the small eigenvalues by more than
+ * themselves, and every 1/lambda-weighted output (solve, quadratic form, log det,
+ * gradient) inherits that.  Accepted by qk_kernel_col / qk_kernel_col_at (which then
+ * write FP64 values) and by the batched schedule (FP32 y and c; the refinement of the
+ * FP32 schedule is always on).  Other entry points take QK_F64 or QK_F32 only. */
+enum qk_dtype { QK_F64 = 0, QK_F32 = 1, QK_F32W = 2 };
 /* Form of a stored first column: the column itself, or p = k_1/zeta - 1
  * (computed by a product-minus-one recurrence, so that the variation of the
  * kernel around its constant part keeps full relative precision). */
@@ -137,7 +147,8 @@ QK_API int qk_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64
 /* First Gram column k_1[i] = K(x_i, x_0) for n = 2^m points of randomizations
  * r0 .. r0+nr-1 (Sec. 5.4, "k1 = kernel(x, x[0])").  The shift cancels in
  * x_i (-) x_0, so only Ct (nets) or g (lattices) is read.  col: (nr, n) in
- * dtype, in the requested form (QK_COL_K1 or QK_COL_P). */
+ * dtype, in the requested form (QK_COL_K1 or QK_COL_P); with QK_F32W, (nr, n) doubles
+ * computed in float-float arithmetic. */
 QK_API int qk_kernel_col(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr,
                   uint32_t m, int32_t dtype, int32_t form, void *col, qk_stream stream);
 
@@ -282,6 +293,114 @@ QK_API int qk_fwht_tune(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void 
 QK_API int qk_fwht_wait_selftest(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes,
                                  uint32_t spin_limit, uint32_t *status, qk_stream stream);
 
+/* --------------------------------------------------- higher-order nets --- */
+
+/* Digital interlacing of order alpha (Sec. 4.3, "Digital interlacing for higher-order
+ * nets"): from the generator columns Ct (R, alpha d, 32) of an alpha d-dimensional net (for
+ * higher-order LMS: the qk_lms_setup output on the alpha d matrices), the d interlaced
+ * matrices Chat (R, d, 32) of 64-bit columns, bit 63 - t = digit t, where digit t of matrix j
+ * (0-based) is digit floor(t / alpha) of matrix alpha j + (t mod alpha).  The interlaced
+ * matrices have 32 alpha digits; the first min(64, 32 alpha) are kept (later digits lie
+ * below 2^-64).  alpha in 1..4. */
+QK_API int qk_interlace(uint32_t d, uint32_t R, uint32_t alpha, const uint32_t *Ct, uint64_t *Chat,
+                        qk_stream stream);
+
+/* A randomized higher-order (interlaced) net: points are 64-digit words, x = X 2^-64. */
+typedef struct {
+  int32_t order;         /* QK_NATURAL or QK_GRAY */
+  uint32_t d;            /* dimensions of the interlaced net */
+  uint32_t R;            /* randomizations stored in Chat / D */
+  const uint64_t *Chat;  /* (R, d, 32) interlaced columns (qk_interlace output) */
+  const uint64_t *D;     /* (R, d) 64-digit digital shifts; NULL means no shift */
+} qk_hopointset;
+
+/* Points of a higher-order net, as qk_gen_points: X (nr, n, d) uint64 row-major,
+ * X = D (+) XOR_{bit k of g(i)} Chat[:, k] (g(i) = i or its Gray code); i0 + n <= 2^32. */
+QK_API int qk_gen_points_ho(const qk_hopointset *ps, uint32_t r0, uint32_t nr, uint64_t i0, uint64_t n,
+                            uint64_t *X, qk_stream stream);
+
+/* First Gram column of a product DSI kernel (k->family QK_DSI, order k->alpha 1..4, Sec. 5.3)
+ * on the points of a higher-order net, as qk_kernel_col: the Theorem's closed forms at
+ * x = Z 2^-64 for the 64-digit difference words Z = X_i (+) X_0 (beta = clz64(Z) + 1; the
+ * order-4 digit series over 64 digits).  col: (nr, 2^m) in dtype (QK_F64 / QK_F32) and form.
+ * The column feeds qk_eigs, qk_solve, qk_matvec, qk_discrepancy and qk_mll_spectrum
+ * unchanged (the Gram matrix of an interlaced net is RSBT). */
+QK_API int qk_kernel_col_ho(const qk_hopointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr, uint32_t m,
+                            int32_t dtype, int32_t form, void *col, qk_stream stream);
+
+/* qk_mll for a higher-order net: the MLL pieces and (grad non-NULL) the gradient block of
+ * qk_mll, the factors recomputed from the 64-digit words.  lam: (nr, 2^m) from qk_eigs on
+ * qk_kernel_col_ho's column (nugget included); y: (nr, nrhs, 2^m) in dtype; out:
+ * (nr, nrhs, QK_MLL_NOUT); grad: (nr, nrhs, 2d + 2), nr nrhs <= 65535.  Workspace:
+ * qk_workspace_bytes op 3 with (QK_DSI, m, nr, nrhs, dtype, d). */
+QK_API int qk_mll_ho(const qk_hopointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr, uint32_t m, uint32_t nrhs,
+                     int32_t dtype, const double *lam, const void *y, double *out, double *grad, void *ws,
+                     size_t ws_bytes, qk_stream stream);
+
+/* The MLL pieces of qk_mll (quadratic form, log det, MLL, posterior mean and variance) from
+ * the eigenvalues alone, without the point set (and so without the gradient): for callers
+ * that hold only a spectrum.  lam: (nr, 2^m) from qk_eigs;
+ * y: (nr, nrhs, 2^m) in dtype; out: (nr, nrhs, QK_MLL_NOUT).  Workspace: qk_workspace_bytes
+ * op 3 with d = 0. */
+QK_API int qk_mll_spectrum(int32_t family, uint32_t m, uint32_t nr, uint32_t nrhs, int32_t dtype, double zeta,
+                           const double *lam, const void *y, double *out, void *ws, size_t ws_bytes,
+                           qk_stream stream);
+
+/* ---------------------------------------------------- RQMC integration --- */
+
+/* The test integrands of the numerical experiments (Sec. 6):
+ *   QK_F_SIMPLE1   d = 1:  x e^x - 1
+ *   QK_F_SIMPLE2   d = 2:  x_2 e^{x_1 x_2} / (e - 2) - 1
+ *   QK_F_OAKLEY    d = 2:  g((x - 1/2)/50), g(t) = 5 + t_1 + t_2 + 2 cos t_1 + 2 cos t_2
+ *   QK_F_GFUN      any d:  prod_j (|4 x_j - 2| - a_j) / (1 + a_j), a_j = (j - 2)/2
+ *   QK_F_GENZ_OSC  any d:  cos(-sum_j c_j x_j), c_j = 4.5 ct_j / sum ct, ct_j = e^{j log(1e-8)/d}
+ *   QK_F_GENZ_CP   any d:  (1 + sum_j c_j x_j)^-(d+1), c_j = 0.25 ct_j / sum ct, ct_j = 1/j^2 */
+enum qk_integrand_id { QK_F_SIMPLE1 = 0, QK_F_SIMPLE2 = 1, QK_F_OAKLEY = 2, QK_F_GFUN = 3, QK_F_GENZ_OSC = 4,
+                       QK_F_GENZ_CP = 5 };
+
+/* y[r][i] = f(x_i) at the points of randomizations r0 .. r0+nr-1, positions i0 .. i0+n-1
+ * (the points of qk_gen_points, not materialised), with baker != 0 at the baker-transformed
+ * point 1 - 2|x - 1/2| instead (Sec. 4.2: periodises the integrand for lattices, mean
+ * unchanged).  y: (nr, n) in dtype (QK_F64 or QK_F32; the arithmetic runs in dtype).
+ * The integrand's dimension must match ps->d where it is fixed (QK_EINVAL otherwise). */
+QK_API int qk_integrand(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64_t i0, uint64_t n, int32_t f,
+                        int32_t baker, int32_t dtype, void *y, qk_stream stream);
+
+/* RQMC estimate with its Student-t interval (Sec. 3.1, Eq. RQMC): from y (R, n) in dtype
+ * (one row of f values per randomization), mu_r = mean_i y[r][i], mu = mean_r mu_r,
+ * sigma^2 = sum_r (mu_r - mu)^2 / (R - 1), and the 100(1 - tau)% half width
+ * t_{R-1, tau/2} sigma / sqrt(R) (t quantile: qk_student_t_quantile).  out: device doubles
+ * (4 + R) = [mu, sigma, half width, t, mu_1 .. mu_R].  R >= 2, 0 < tau < 1. */
+QK_API int qk_rqmc(uint32_t R, uint64_t n, int32_t dtype, const void *y, double tau, double *out,
+                   qk_stream stream);
+
+/* Host: the p-quantile q of Student's t distribution with df > 0 degrees of freedom
+ * (P(T <= q) = p, 0 < p < 1; bisection on the CDF through the regularised incomplete
+ * beta function).  *q is a host double. */
+QK_API int qk_student_t_quantile(double df, double p, double *q);
+
+/* Squared worst-case error (the generalized kernel discrepancy, Sec. 3.2) of cubature rules
+ * on the points of `batch` point sets, for the kernel without nugget: with
+ * kappa_i = int K(u, x_i) du = zeta and int int K = zeta (each one-dimensional K_alpha
+ * integrates to zero), from the first columns col (batch, n) in dtype and form (QK_COL_P
+ * keeps full precision; QK_COL_K1 cancels in k_1/zeta - 1):
+ *   out[b][0] = equal weights 1/n:          zeta S / n
+ *   out[b][1] = optimal weights K^-1 kappa: zeta - zeta^2 n / lambda_0 = zeta S / (n + S)
+ *   out[b][2] = the optimal weight, the same for every point: zeta / lambda_0 = 1 / (n + S)
+ * with S = sum_i p_i and lambda_0 = zeta (n + S).  out: (batch, 3) device doubles. */
+QK_API int qk_discrepancy(int32_t family, uint32_t m, uint32_t batch, int32_t dtype, int32_t form, const void *col,
+                          double zeta, double *out, qk_stream stream);
+
+/* The same for given weights w (batch, nw, n) in dtype:
+ *   out[b][q] = zeta - 2 zeta sum_i w_i + w^T K w,  w^T K w = sum_w lambda_w |W_w|^2 / n,
+ * W the unnormalised transform of the weights (Sec. 5.4) and lam (batch, n) the eigenvalues
+ * of K from qk_eigs with eta = 0.  The difference cancels for near-optimal weights: its
+ * absolute error is about eps zeta.  out: (batch, nw) device doubles.  Workspace:
+ * qk_workspace_bytes op 5 with (family, m, batch, nrhs = nw, dtype). */
+QK_API int qk_discrepancy_weights(int32_t family, uint32_t m, uint32_t batch, uint32_t nw, int32_t dtype,
+                                  const double *lam, const void *w, double zeta, double *out, void *ws,
+                                  size_t ws_bytes, qk_stream stream);
+
 /* --------------------------------------------------------------- batching --- */
 
 /* One task of a batched schedule: R randomizations of one point set and kernel,
@@ -371,8 +490,9 @@ QK_API int qk_batch_kernel_ms(void *ws, uint32_t idx, char *name, size_t name_le
 
 /* ------------------------------------------------------------- utilities --- */
 
-/* Workspace bytes needed by qk_eigs / qk_solve / qk_matvec / qk_mll / qk_fwht_ws with
- * these sizes (op: 0 eigs, 1 solve, 2 matvec, 3 mll, 4 fwht_ws with batch = nvec). */
+/* Workspace bytes needed by qk_eigs / qk_solve / qk_matvec / qk_mll / qk_fwht_ws /
+ * qk_discrepancy_weights with these sizes (op: 0 eigs, 1 solve, 2 matvec, 3 mll, 4 fwht_ws
+ * with batch = nvec, 5 discrepancy_weights with nrhs = nw). */
 QK_API int qk_workspace_bytes(int32_t op, int32_t family, uint32_t m, uint32_t batch, uint32_t nrhs,
                        int32_t dtype, uint32_t d, size_t *bytes);
 

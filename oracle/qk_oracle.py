@@ -819,3 +819,30 @@ def ho_gram_dense(alpha_k: int, Xhat, c, zeta=1.0, eta=0.0) -> np.ndarray:
         Z = Xhat[:, j][:, None] ^ Xhat[None, :, j]
         K *= 1.0 + c[j] * dsi_kernel_words(alpha_k, Z)
     return K + eta * np.eye(n)
+
+
+def ho_gram_weight_derivative(alpha_k: int, Xhat, c, j: int, zeta=1.0) -> np.ndarray:
+    """dK/dc_j for the product DSI kernel on 64-digit points (dense)."""
+    Xhat = np.asarray(Xhat, dtype=np.uint64)
+    n = Xhat.shape[0]
+    out = np.full((n, n), float(zeta))
+    for jj in range(Xhat.shape[1]):
+        Kv = dsi_kernel_words(alpha_k, Xhat[:, jj][:, None] ^ Xhat[None, :, jj])
+        out *= Kv if jj == j else (1.0 + c[jj] * Kv)
+    return out
+
+
+def ho_mll_grad_dense(alpha_k: int, Xhat, y, c, eta, zeta=1.0):
+    """dMLL/dc_j = c^T dK c / 2 - tr(K^-1 dK) / 2 and dMLL/deta for 64-digit points (dense,
+    the textbook GP gradient as in mll_grad_dense)."""
+    K = ho_gram_dense(alpha_k, Xhat, c, zeta, eta)
+    n, d = Xhat.shape
+    L = np.linalg.cholesky(K)
+    cvec = scipy.linalg.cho_solve((L, True), y)
+    Kinv = scipy.linalg.cho_solve((L, True), np.eye(n))
+    dc = np.empty(d)
+    for j in range(d):
+        dK = ho_gram_weight_derivative(alpha_k, Xhat, c, j, zeta)
+        dc[j] = 0.5 * cvec @ dK @ cvec - 0.5 * float(np.sum(Kinv * dK.T))
+    deta = 0.5 * cvec @ cvec - 0.5 * float(np.trace(Kinv))
+    return {"dc": dc, "deta": deta}

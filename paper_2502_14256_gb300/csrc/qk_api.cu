@@ -17,6 +17,19 @@ static std::atomic<uint64_t> g_launches{0};
 
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+int sm_count() {
+  constexpr int kMaxDev = 64;
+  static std::atomic<int> cache[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) dev = 0;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v <= 0) {
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 1;
+    cache[dev].store(v, std::memory_order_relaxed);
+  }
+  return v;
+}
+
 void set_error(const char *fmt, ...) {
   va_list ap;
   va_start(ap, fmt);
@@ -40,13 +53,19 @@ int cuda_fail(cudaError_t e, const char *what) {
 static int check_dtype(int32_t dtype) {
   return (dtype == QK_F64 || dtype == QK_F32) ? QK_OK : fail(QK_EINVAL, "dtype must be QK_F64 or QK_F32");
 }
+// Column entry points also take QK_F32W (float-float arithmetic, FP64 output).
+static int check_col_dtype(int32_t dtype) {
+  return (dtype == QK_F64 || dtype == QK_F32 || dtype == QK_F32W)
+             ? QK_OK
+             : fail(QK_EINVAL, "dtype must be QK_F64, QK_F32 or QK_F32W");
+}
 static int check_family(int32_t family) {
   return (family == QK_DSI || family == QK_SI) ? QK_OK : fail(QK_EINVAL, "family must be QK_DSI or QK_SI");
 }
 static int check_m(uint32_t m) {
   return m <= QK_MAX_M ? QK_OK : fail(QK_EINVAL, "m = %u exceeds QK_MAX_M = %d", m, QK_MAX_M);
 }
-static int check_ws(const void *ws, size_t have, size_t need) {
+int check_ws(const void *ws, size_t have, size_t need) {
   if (need == 0) return QK_OK;
   if (!ws) return fail(QK_EWORKSPACE, "workspace is NULL (%zu bytes needed)", need);
   if (have < need) return fail(QK_EWORKSPACE, "workspace has %zu bytes, %zu needed", have, need);
@@ -164,7 +183,7 @@ int qk_kernel_col(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32
   g_err[0] = 0;
   QK_TRY(check_pointset(ps, r0, nr));
   QK_TRY(check_kernel(k, ps));
-  QK_TRY(check_dtype(dtype));
+  QK_TRY(check_col_dtype(dtype));
   QK_TRY(check_m(m));
   if (form != QK_COL_K1 && form != QK_COL_P) return fail(QK_EINVAL, "form must be QK_COL_K1 or QK_COL_P");
   if (!col && nr) return fail(QK_EINVAL, "qk_kernel_col: output is NULL");
@@ -176,7 +195,7 @@ int qk_kernel_col_at(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uin
   g_err[0] = 0;
   QK_TRY(check_pointset(ps, r0, nr));
   QK_TRY(check_kernel(k, ps));
-  QK_TRY(check_dtype(dtype));
+  QK_TRY(check_col_dtype(dtype));
   QK_TRY(check_m(m));
   if (form != QK_COL_K1 && form != QK_COL_P) return fail(QK_EINVAL, "form must be QK_COL_K1 or QK_COL_P");
   if (i0 % 2048 != 0) return fail(QK_EINVAL, "qk_kernel_col_at: i0 = %llu is not a multiple of 2048", (unsigned long long)i0);
@@ -249,9 +268,10 @@ int qk_workspace_bytes(int32_t op, int32_t family, uint32_t m, uint32_t batch, u
   switch (op) {
     case 0: *bytes = ws_eigs(family, m, batch, dtype); break;
     case 1: *bytes = ws_solve(family, m, batch, nrhs, dtype); break;
-    case 2: *bytes = align256(elem_bytes(family, dtype) * (((uint64_t)batch * nrhs) << m)); break;
+    case 2: *bytes = ws_matvec(family, m, batch, nrhs, dtype); break;
     case 3: *bytes = ws_mll(family, m, batch, nrhs, dtype, d); break;
     case 4: *bytes = persist_wht_ws_bytes(batch); break;
+    case 5: *bytes = ws_discrepancy(family, m, batch, nrhs, dtype); break;
     default: return fail(QK_EINVAL, "unknown op %d", op);
   }
   return QK_OK;
@@ -292,7 +312,7 @@ int qk_matvec(int32_t family, uint32_t m, uint32_t batch, uint32_t nrhs, int32_t
   QK_TRY(check_m(m));
   if (batch == 0 || nrhs == 0) return QK_OK;
   if (!lam || !y || !u) return fail(QK_EINVAL, "qk_matvec: NULL array");
-  QK_TRY(check_ws(ws, ws_bytes, align256(elem_bytes(family, dtype) * (((uint64_t)batch * nrhs) << m))));
+  QK_TRY(check_ws(ws, ws_bytes, ws_matvec(family, m, batch, nrhs, dtype)));
   return op_matvec(family, m, batch, nrhs, dtype, lam, y, u, ws, (cudaStream_t)stream);
 }
 

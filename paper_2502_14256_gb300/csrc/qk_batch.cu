@@ -15,9 +15,6 @@
 
 namespace qk {
 
-int check_pointset(const qk_pointset *ps, uint32_t r0, uint32_t nr);
-int check_kernel(const qk_kernel *k, const qk_pointset *ps);
-ColJob make_job(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr, uint32_t m);
 
 // Event pairs recorded around launches when timing is on (qk_batch_timing).
 struct EventTimer : LaunchTimer {
@@ -75,6 +72,19 @@ static bool use_fused(const qk_task &t, int dtype, int refine) {
 static size_t task_scratch(const qk_task &t, int dtype, int refine) {
   if (use_fused(t, dtype, refine)) return fused_ws_bytes(t, dtype, refine);
   const uint32_t R = t.ps.R;
+  if (dtype == QK_F32W) {
+    // float-float column stored as FP64, FP64 eigenvalues and spectral sums, FP32 solve
+    // with refinement and FP32 gradient sweep
+    const size_t col = align256(8 * ((uint64_t)R << t.m));
+    size_t s = ws_eigs(t.k.family, t.m, R, QK_F64);
+    const size_t mw = ws_mll(t.k.family, t.m, R, t.nrhs, QK_F32W, t.ps.d);
+    if (mw > s) s = mw;
+    if (t.c) {
+      const size_t sw = ws_solve(t.k.family, t.m, R, t.nrhs, QK_F32);
+      if (sw > s) s = sw;
+    }
+    return col + s;
+  }
   const size_t tb = dtype == QK_F64 ? 8 : 4;
   const size_t col = align256(tb * ((uint64_t)R << t.m));
   size_t s = ws_eigs(t.k.family, t.m, R, dtype);
@@ -89,7 +99,8 @@ static size_t task_scratch(const qk_task &t, int dtype, int refine) {
 
 static int make_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, int32_t refine, Plan &p) {
   if (!tasks && ntasks) return fail(QK_EINVAL, "task list is NULL");
-  if (dtype != QK_F64 && dtype != QK_F32) return fail(QK_EINVAL, "dtype must be QK_F64 or QK_F32");
+  if (dtype != QK_F64 && dtype != QK_F32 && dtype != QK_F32W)
+    return fail(QK_EINVAL, "dtype must be QK_F64, QK_F32 or QK_F32W");
   p.tasks.assign(tasks, tasks + ntasks);
   p.dtype = dtype;
   p.refine = refine;
@@ -140,13 +151,34 @@ static int run_task(const Plan &p, const qk_task &t, unsigned char *ws, uint32_t
                     LaunchTimer *tm) {
   {
     const uint32_t R = t.ps.R;
-    const size_t tb = p.dtype == QK_F64 ? 8 : 4;
+    const size_t tb = p.dtype == QK_F32 ? 4 : 8;  // stored column (QK_F32W: FP64 from float-float)
     unsigned char *col = ws;
     unsigned char *scr = ws + align256(tb * ((uint64_t)R << t.m));
     double *lam = t.lam ? t.lam : (double *)(ws + p.lam_off);
     const ColJob job = make_job(&t.ps, &t.k, 0, R, t.m);
     if (use_fused(t, p.dtype, p.refine)) return run_fused(t, job, p.dtype, p.refine, ws, status, st, tm);
     int rc;
+    if (p.dtype == QK_F32W) {
+      {
+        OpScope s(tm, "op_kernel_col_ff", st);
+        if ((rc = launch_kernel_col(job, QK_F32W, QK_COL_P, col, st))) return rc;
+      }
+      {
+        OpScope s(tm, "op_eigs", st);
+        if ((rc = op_eigs(t.k.family, t.m, R, QK_F64, QK_COL_P, col, t.k.zeta, t.eta, lam, scr, status, st)))
+          return rc;
+      }
+      {
+        OpScope s(tm, "op_mll", st);
+        if ((rc = op_mll(job, t.nrhs, QK_F32W, lam, t.y, t.out, t.grad, scr, st))) return rc;
+      }
+      if (t.c) {
+        OpScope s(tm, "op_solve", st);
+        const int refine = p.refine > 0 ? p.refine : 1;
+        if ((rc = op_solve(t.k.family, t.m, R, t.nrhs, QK_F32, lam, t.y, t.c, refine, scr, st))) return rc;
+      }
+      return QK_OK;
+    }
     {
       OpScope s(tm, "op_kernel_col", st);
       if ((rc = launch_kernel_col(job, p.dtype, QK_COL_P, col, st))) return rc;

@@ -140,6 +140,62 @@ static __device__ const DsiTable<float> g_dsi_f[4] = {make_dsi_table<float, 1>()
 static __device__ const DsiTable<double> g_dsi_d[4] = {make_dsi_table<double, 1>(), make_dsi_table<double, 2>(),
                                                        make_dsi_table<double, 3>(), make_dsi_table<double, 4>()};
 
+// Float-float rows of the same polynomials in fz (the float-float first column): per row the
+// pairs (h, l) of A, B, C, D, E (orders 2 and 3 use a prefix), padded to 12 floats so that
+// a row loads as three 128-bit vectors, then the octal byte table (exact in FP32).
+constexpr int kFFStride = 12;
+constexpr int kDsiFFLen = kTabRows * kFFStride + kOctRows;
+struct DsiTableFF { float v[kDsiFFLen]; };
+static_assert(sizeof(DsiTableFF) <= kDsiTabLen * sizeof(double), "float-float rows fit the shared table region");
+
+template <int ALPHA>
+__host__ __device__ constexpr DsiTableFF make_dsi_table_ff() {
+  DsiTableFF tab{};
+  for (int q = 0; q < kTabRows; ++q) {
+    const int beta = q < 32 ? q + 1 : 0;
+    const double t1 = q < 32 ? pow2neg(beta) : 0.0, t2 = t1 * t1, t3 = t2 * t1;
+    const double b = (double)beta;
+    double co[5] = {0, 0, 0, 0, 0};
+    if (ALPHA == 1) {
+      co[0] = q < 32 ? 1.0 - 3.0 * t1 : 1.0;
+    } else if (ALPHA == 2) {
+      co[0] = 1.5 - 2.5 * t1;
+      co[1] = -b * pow2neg(32);
+    } else if (ALPHA == 3) {
+      co[0] = -1.0 + (43.0 / 18.0) * (1.0 - t2);
+      co[1] = -5.0 * (1.0 - t1) * pow2neg(32);
+      co[2] = b * pow2neg(64);
+    } else {
+      co[0] = -1.0 + (701.0 / 294.0) * (1.0 - t3);
+      co[1] = -(43.0 / 9.0) * (1.0 - t2) * pow2neg(32);
+      co[2] = 5.0 * (1.0 - t1) * pow2neg(64);
+      co[3] = -(2.0 / 3.0) * b * pow2neg(96);
+      co[4] = -b / 24.0;
+    }
+    for (int k = 0; k < 5; ++k) {
+      const float h = (float)co[k];
+      tab.v[q * kFFStride + 2 * k] = h;
+      tab.v[q * kFFStride + 2 * k + 1] = (float)(co[k] - (double)h);
+    }
+  }
+  for (int byte = 0; byte < kOctRows; ++byte) {
+    double sum = 0.0;
+    for (int a = 0; a < 8; ++a)
+      if ((byte >> (7 - a)) & 1) sum += pow2neg(3 * a);
+    tab.v[kTabRows * kFFStride + byte] = (float)sum;  // at most 22 significant bits: exact
+  }
+  return tab;
+}
+
+static __device__ const DsiTableFF g_dsi_ff[4] = {make_dsi_table_ff<1>(), make_dsi_table_ff<2>(),
+                                                  make_dsi_table_ff<3>(), make_dsi_table_ff<4>()};
+
+template <int ALPHA>
+__device__ void build_dsi_tab_ff(float *tab) {
+  const float *src = g_dsi_ff[ALPHA - 1].v;
+  for (int q = threadIdx.x; q < kDsiFFLen; q += kColNT) tab[q] = src[q];
+}
+
 // Copy the DSI coefficient rows of this order into shared memory.
 template <typename T, int ALPHA>
 __device__ void build_dsi_tab(T *tab) {
@@ -279,6 +335,123 @@ __device__ __forceinline__ void column_sweep(const ColJob &job, const DiffTables
         p[l] = pm1_step(p[l], a);
       }
     }
+  }
+}
+
+// --------------------------------------------- float-float first column (pairs of points)
+// The 32-bit word Z as a normalised float-float pair: Z & ~255 (at most 24 significant bits)
+// and Z & 255 convert exactly; one fast TwoSum normalises the pair.
+__device__ __forceinline__ FF<F2> word_ff2(uint32_t Z0, uint32_t Z1) {
+  const F2 zh = vpack(__uint2float_rn(Z0 & ~255u), __uint2float_rn(Z1 & ~255u));
+  const F2 zl = vpack(small_int_to(0.f, Z0 & 255u), small_int_to(0.f, Z1 & 255u));
+  return ff_fast_two_sum(zh, zl);
+}
+
+// K_alpha of two points in float-float from the float-float rows (the polynomial in fz of
+// the FP32 rows, Horner in float-float).  S'(Z) = T[b0] + 2^-24 T[b1] + 2^-48 T[b2] (the
+// bytes b of Z) enters as the pair (T[b0], 2^-24 T[b1] + 2^-48 T[b2]): T[b0] is 0 or at
+// least 2^-21, above the second part, so one fast TwoSum normalises it.
+template <int ALPHA>
+__device__ __forceinline__ FF<F2> dsi_ff2(const float *tab, uint32_t Z0, uint32_t Z1) {
+  const float *r0 = tab + __clz(Z0) * kFFStride, *r1 = tab + __clz(Z1) * kFFStride;
+  const float4 a0 = *reinterpret_cast<const float4 *>(r0), a1 = *reinterpret_cast<const float4 *>(r1);
+  const FF<F2> A = {vpack(a0.x, a1.x), vpack(a0.y, a1.y)};
+  if constexpr (ALPHA == 1) {
+    return A;
+  } else {
+    const FF<F2> B = {vpack(a0.z, a1.z), vpack(a0.w, a1.w)};
+    const FF<F2> fz = word_ff2(Z0, Z1);
+    if constexpr (ALPHA == 2) {
+      return ff_add(A, ff_mul(B, fz));
+    } else {
+      const float4 b0 = *reinterpret_cast<const float4 *>(r0 + 4), b1 = *reinterpret_cast<const float4 *>(r1 + 4);
+      const FF<F2> C = {vpack(b0.x, b1.x), vpack(b0.y, b1.y)};
+      if constexpr (ALPHA == 3) {
+        return ff_add(ff_mul(ff_add(ff_mul(C, fz), B), fz), A);
+      } else {
+        static_assert(ALPHA == 4, "DSI order 1..4");
+        const FF<F2> D = {vpack(b0.z, b1.z), vpack(b0.w, b1.w)};
+        const float2 e0 = *reinterpret_cast<const float2 *>(r0 + 8), e1 = *reinterpret_cast<const float2 *>(r1 + 8);
+        const FF<F2> E = {vpack(e0.x, e1.x), vpack(e0.y, e1.y)};
+        FF<F2> t = ff_add(ff_mul(D, fz), C);
+        t = ff_add(ff_mul(t, fz), B);
+        t = ff_add(ff_mul(t, fz), A);
+        const float *oct = tab + kTabRows * kFFStride;
+        const F2 sh = vpack(oct[Z0 >> 24], oct[Z1 >> 24]);
+        const F2 sl = vfma(vsplat(0x1p-48f), vpack(oct[(Z0 >> 8) & 255u], oct[(Z1 >> 8) & 255u]),
+                           vmul(vsplat(0x1p-24f), vpack(oct[(Z0 >> 16) & 255u], oct[(Z1 >> 16) & 255u])));
+        return ff_add(t, ff_mul(E, ff_fast_two_sum(sh, sl)));
+      }
+    }
+  }
+}
+
+// SI kernels in float-float: x = W 2^-32 (exact pair), q = x (1 - x),
+// K_1 = pi^2/3 - 2 pi^2 q, K_2 = pi^4/45 - 2 pi^4/3 q^2 (Sec. 5.2, Bernoulli B_2 and B_4);
+// the constants are the pairs of their FP64 values.
+template <int ALPHA>
+__device__ __forceinline__ FF<F2> si_ff2(uint32_t W0, uint32_t W1) {
+  FF<F2> x = word_ff2(W0, W1);
+  x.h = vmul(x.h, vsplat(0x1p-32f));
+  x.l = vmul(x.l, vsplat(0x1p-32f));
+  FF<F2> omx = ff_two_sum(vsplat(1.f), vneg(x.h));
+  omx.l = vsub(omx.l, x.l);
+  FF<F2> q = ff_mul(x, omx);
+  auto cst = [](double v) -> FF<F2> {
+    const float2 s = ff_split(v);
+    return {vsplat(s.x), vsplat(s.y)};
+  };
+  if constexpr (ALPHA == 1) {
+    return ff_add(cst(3.2898681336964528729), ff_mul(cst(-19.739208802178717238), q));
+  } else {
+    static_assert(ALPHA == 2, "SI smoothness 1..2");
+    return ff_add(cst(2.1646464674222763831), ff_mul(cst(-64.939394022668291491), ff_mul(q, q)));
+  }
+}
+
+template <int FAM, int ALPHA>
+__device__ __forceinline__ FF<F2> kfac_ff2(const DiffTables &tb, uint32_t w0, uint32_t w1) {
+  if constexpr (FAM == 0) return dsi_ff2<ALPHA>(reinterpret_cast<const float *>(tb.ktab), w0, w1);
+  else return si_ff2<ALPHA>(w0, w1);
+}
+
+// Tables of the float-float sweep: the index tables and, for DSI kernels, the float-float rows.
+template <int FAM, int ALPHA, int L>
+__device__ __forceinline__ void build_all_ff(const ColJob &job, const uint32_t *Cr, const uint32_t *g,
+                                             uint64_t tile_base, DiffTables &tb) {
+  build_tables<L>(job, Cr, g, tile_base, tb);
+  if constexpr (FAM == 0) build_dsi_tab_ff<ALPHA>(reinterpret_cast<float *>(tb.ktab));
+}
+
+// p = prod_j (1 + c_j K_j) - 1 for the L points of this thread as float-float pairs
+// (ph[l] + pl[l], about 2^-46 relative per factor), two points per packed f32x2 operation.
+// wff: the weights c_j as pairs (h, l).
+template <int FAM, int ALPHA, int L>
+__device__ __forceinline__ void column_sweep_ff(const ColJob &job, const DiffTables &tb, const float2 *wff,
+                                                const uint32_t (&bi)[L], float (&ph)[L], float (&pl)[L]) {
+  static_assert(L % 2 == 0, "pairs of points");
+  const uint32_t d = job.d;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  FF<F2> P[L / 2];
+  const F2 zero = vsplat(0.f), one = vsplat(1.f);
+#pragma unroll
+  for (int h = 0; h < L / 2; ++h) P[h] = {zero, zero};
+  for (uint32_t j = 0; j < d; ++j) {
+    const float2 w = wff[j];
+    const FF<F2> W = {vsplat(w.x), vsplat(w.y)};
+    uint32_t base = 0;
+    if constexpr (FAM == 0) base = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * d + j];
+#pragma unroll
+    for (int h = 0; h < L / 2; ++h) {
+      const uint32_t z0 = diff_word<FAM, L>(tb, d, base, bi[2 * h], 2 * h, j);
+      const uint32_t z1 = diff_word<FAM, L>(tb, d, base, bi[2 * h + 1], 2 * h + 1, j);
+      P[h] = ff_pm1_step(P[h], ff_mul(W, kfac_ff2<FAM, ALPHA>(tb, z0, z1)), one);
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < L / 2; ++h) {
+    vunpack(P[h].h, ph[2 * h], ph[2 * h + 1]);
+    vunpack(P[h].l, pl[2 * h], pl[2 * h + 1]);
   }
 }
 

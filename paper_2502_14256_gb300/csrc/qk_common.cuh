@@ -25,7 +25,8 @@ inline int check_launch(const char *what) {
 
 inline unsigned ceil_div_u(uint64_t a, uint64_t b) { return (unsigned)((a + b - 1) / b); }
 
-constexpr int kSMs = 152;  // GB300: 2 dies x 76 SMs
+// Multiprocessors of the current device (queried once per device, cached).
+int sm_count();
 
 // Opt a kernel into more than 48 KB of dynamic shared memory, once per process
 // and kernel (the call is skipped entirely below 48 KB, so launches that need
@@ -136,54 +137,6 @@ __device__ __forceinline__ double f2d_exact(float v) {
 }
 __device__ __forceinline__ double f2d_exact(double v) { return v; }
 
-// ---------------------------------------------- bulk asynchronous copies (TMA)
-// One-dimensional cp.async.bulk global -> shared copies completing on an mbarrier
-// (transaction bytes).  Addresses 16-byte aligned, sizes multiples of 16 bytes.
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-// Makes initialised mbarriers visible to the asynchronous proxy.
-__device__ __forceinline__ void mbar_init_fence() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Waits for the phase with the given parity to complete, at most `limit` tries.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t k = 0; k < limit; ++k)
-    if (mbar_try_wait(bar, parity)) return true;
-  return false;
-}
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-// Orders this thread's earlier generic-proxy view of global memory (e.g. data another
-// CTA published and this thread acquired) before its later bulk-copy reads.
-__device__ __forceinline__ void fence_proxy_async_global() {
-  asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-// Orders this thread's earlier generic accesses of shared memory before later bulk-copy
-// writes into it (a buffer reused as a copy destination).
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
   uint32_t v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -225,6 +178,82 @@ __device__ __forceinline__ uint32_t spread3_10(uint32_t v) {
   v = (v | (v << 4)) & 0x030C30C3u;
   v = (v | (v << 2)) & 0x09249249u;
   return v;
+}
+
+
+// ------------------------------------------------------- float-float arithmetic
+// Values carried as unevaluated pairs h + l of FP32 numbers (about 48 significant bits)
+// on the FP32 pipes, from error-free transformations: TwoSum for additions and the
+// product error fma(a, b, -a b) for multiplications (Dekker 1971; Knuth, TAOCP vol. 2).
+// On GB300 an FP64 operation costs tens of FP32 operations, so float-float is the cheap
+// way to more than FP32 precision.  Every operation is written for V = float (one value)
+// or F2 (two values in one packed f32x2 register: the same IEEE operations on both
+// halves), so that two points share each instruction.  The scalar forms use the _rn
+// intrinsics, which the compiler never contracts into a fused multiply-add.
+struct F2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float vneg(float a) { return -a; }
+__device__ __forceinline__ F2 vadd(F2 a, F2 b) { return {add_f2(a.v, b.v)}; }
+__device__ __forceinline__ F2 vsub(F2 a, F2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a.v), "l"(b.v));
+  return {r};
+}
+__device__ __forceinline__ F2 vmul(F2 a, F2 b) { return {mul_f2(a.v, b.v)}; }
+__device__ __forceinline__ F2 vfma(F2 a, F2 b, F2 c) { return {fma_f2(a.v, b.v, c.v)}; }
+__device__ __forceinline__ F2 vneg(F2 a) { return {a.v ^ 0x8000000080000000ull}; }
+__device__ __forceinline__ F2 vpack(float a, float b) { return {pack_f2(a, b)}; }
+__device__ __forceinline__ F2 vsplat(float a) { return {pack_f2(a, a)}; }
+__device__ __forceinline__ void vunpack(F2 x, float &a, float &b) { unpack_f2(x.v, a, b); }
+
+template <typename V>
+struct FF {
+  V h, l;
+};
+
+// s + e == a + b exactly (no ordering of |a|, |b| needed).
+template <typename V>
+__device__ __forceinline__ FF<V> ff_two_sum(V a, V b) {
+  const V s = vadd(a, b), bb = vsub(s, a);
+  return {s, vadd(vsub(a, vsub(s, bb)), vsub(b, bb))};
+}
+// The same when |a| >= |b| or a == 0 (three operations).
+template <typename V>
+__device__ __forceinline__ FF<V> ff_fast_two_sum(V a, V b) {
+  const V s = vadd(a, b);
+  return {s, vsub(b, vsub(s, a))};
+}
+// x y, relative error about 2^-46 for normalised pairs (|l| <= ulp(h)/2).
+template <typename V>
+__device__ __forceinline__ FF<V> ff_mul(FF<V> x, FF<V> y) {
+  const V p = vmul(x.h, y.h);
+  V e = vfma(x.h, y.h, vneg(p));
+  e = vfma(x.h, y.l, e);
+  e = vfma(x.l, y.h, e);
+  return ff_fast_two_sum(p, e);
+}
+// x + y, error about 2^-46 max(|x|, |y|).
+template <typename V>
+__device__ __forceinline__ FF<V> ff_add(FF<V> x, FF<V> y) {
+  FF<V> s = ff_two_sum(x.h, y.h);
+  return ff_fast_two_sum(s.h, vadd(s.l, vadd(x.l, y.l)));
+}
+// x (1 + a) + a = (1 + x)(1 + a) - 1: the product-minus-one recurrence of the first column.
+template <typename V>
+__device__ __forceinline__ FF<V> ff_pm1_step(FF<V> x, FF<V> a, V one) {
+  FF<V> q = ff_two_sum(one, x.h);  // 1 + x, exact up to the rounding of q.l below
+  q.l = vadd(q.l, x.l);
+  return ff_add(x, ff_mul(a, q));
+}
+// The pair of a double (host or device constant): h = fl32(v), l = fl32(v - h).
+__host__ __device__ inline float2 ff_split(double v) {
+  const float h = (float)v;
+  return make_float2(h, (float)(v - (double)h));
 }
 
 }  // namespace qk

@@ -28,7 +28,17 @@ struct ColJob {
   int32_t family, alpha;
   uint32_t nr;          // randomizations in this job
   uint64_t i0 = 0;      // first point position (kernel columns of a later block of points)
+  const uint64_t *Chat = nullptr;  // higher-order nets (kind kHONet): (R, d, 32) 64-digit columns
 };
+constexpr int32_t kHONet = 2;  // ColJob kind of an interlaced net (qk_honet.cu)
+// Gradient partial sums of a higher-order net job (same layout as launch_grad_partials).
+int launch_grad_partials_ho(const ColJob &job, uint32_t nrhs, int32_t dtype, const void *u, double *partial,
+                            cudaStream_t st);
+
+// Argument checks of the entry points (qk_api.cu): QK_OK or the error code, message set.
+int check_pointset(const qk_pointset *ps, uint32_t r0, uint32_t nr);
+int check_kernel(const qk_kernel *k, const qk_pointset *ps);
+int check_ws(const void *ws, size_t have, size_t need);
 
 // The job of randomizations r0 .. r0+nr-1 of a (validated) point set and kernel (qk_api.cu).
 ColJob make_job(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t nr, uint32_t m);
@@ -84,6 +94,7 @@ int run_fused(const qk_task &t, const ColJob &job, int dtype, int refine, void *
 namespace qk {
 size_t ws_eigs(int family, uint32_t m, uint32_t batch, int dtype);
 size_t ws_solve(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype);
+size_t ws_matvec(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype);
 size_t ws_mll(int family, uint32_t m, uint32_t nr, uint32_t nrhs, int dtype, uint32_t d);
 size_t elem_bytes(int family, int dtype);
 int op_eigs(int family, uint32_t m, uint32_t batch, int dtype, int form, const void *col, double zeta, double eta,
@@ -93,6 +104,8 @@ int op_solve(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, c
 int op_matvec(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, const double *lam, const void *y,
               void *u, void *ws, cudaStream_t st);
 int op_transform(int kind, uint32_t m, uint64_t nvec, int dtype, void *x, cudaStream_t st);
+int op_forward_real(int family, uint32_t m, uint64_t nvec, int dtype, const void *in, void *X, cudaStream_t st);
+size_t ws_discrepancy(int family, uint32_t m, uint32_t batch, uint32_t nw, int dtype);
 int op_eigs_extend(int family, uint32_t m, uint32_t batch, int dtype, int form, const void *col_new, double zeta,
                    double eta, const double *lam_old, double *lam, void *ws, uint32_t *status, cudaStream_t st);
 int op_transform_extend(int kind, uint32_t m, uint64_t nvec, int dtype, const void *xt_old, void *x_new, void *out,

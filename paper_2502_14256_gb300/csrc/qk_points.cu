@@ -48,57 +48,105 @@ int launch_lms(uint32_t d, uint32_t R, const uint32_t *C, const uint32_t *S, uin
 }
 
 // ---------------------------------------------------------- point generation
-__global__ void k_points_net(uint32_t d, int order, const uint32_t *__restrict__ Ct,
-                             const uint32_t *__restrict__ D, uint32_t r0, uint64_t i0, uint64_t n,
-                             uint32_t *__restrict__ X) {
-  extern __shared__ uint32_t sC[];
-  const uint32_t rl = blockIdx.y;
-  const uint32_t r = r0 + rl;
-  for (uint32_t q = threadIdx.x; q < d * 32; q += blockDim.x) sC[q] = Ct[(size_t)r * d * 32 + q];
-  __syncthreads();
-  const uint64_t total = n * d;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-    const uint64_t i = e / d;
-    const uint32_t j = (uint32_t)(e - i * d);
-    const uint32_t h = order_map(order, (uint32_t)(i0 + i));
-    uint32_t v = xor_columns(sC + j * 32, h);
-    if (D) v ^= D[(size_t)r * d + j];
-    X[(size_t)rl * total + e] = v;
-  }
+// By tiles: a CTA builds NP consecutive points (aligned to NP) of every dimension of one
+// randomization in shared memory, row-major as in the output, then writes the part inside
+// [i0, i0 + n) as one contiguous, coalesced run of words.  Inside the tile a thread makes a
+// run of kGenRL = 8 consecutive points of one dimension:
+//   nets: the index maps h(i) = i and i ^ (i >> 1) are linear over GF(2) and the tile, run
+//   and step bits of i are disjoint, so the run's first point is the XOR of a per-tile word,
+//   a per-run word (both tables built once per CTA) and the shift; each next point is one
+//   XOR with a column known at compile time: Gray order changes digit ctz(k + 1) (Sec. 4.3,
+//   Gray code), natural order all digits below it (the XOR of columns 0 .. ctz(k + 1));
+//   lattices: X_i = brev(i) g + D, one multiply-add per point.
+constexpr int kGenNT = 256, kGenRL = 8, kGenWords = 8192;
+
+// log2 of the tile's point count: the largest power of two with NP d <= kGenWords (NP >= RL).
+static uint32_t gen_lognp(uint32_t d) {
+  uint32_t l = 0;
+  while ((2u << l) * d <= (uint32_t)kGenWords) ++l;
+  return l < 3 ? 3 : l;
 }
 
-__global__ void k_points_lattice(uint32_t d, const uint32_t *__restrict__ g,
-                                 const uint32_t *__restrict__ D, uint32_t r0, uint64_t i0,
-                                 uint64_t n, uint32_t *__restrict__ X) {
-  const uint32_t rl = blockIdx.y;
-  const uint32_t r = r0 + rl;
-  const uint64_t total = n * d;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += stride) {
-    const uint64_t i = e / d;
-    const uint32_t j = (uint32_t)(e - i * d);
-    uint32_t v = __brev((uint32_t)(i0 + i)) * g[j];
-    if (D) v += D[(size_t)r * d + j];
-    X[(size_t)rl * total + e] = v;
+template <bool NET>
+__global__ void __launch_bounds__(kGenNT) k_points_tiled(uint32_t d, int order, const uint32_t *__restrict__ Ct,
+                                                         const uint32_t *__restrict__ g, const uint32_t *__restrict__ D,
+                                                         uint32_t r0, uint64_t i0, uint64_t n, uint32_t lognp,
+                                                         uint32_t *__restrict__ X) {
+  extern __shared__ uint32_t gsm[];
+  const uint32_t NP = 1u << lognp, runs = (NP / kGenRL) * d;
+  uint32_t *tile = gsm;             // NP x d
+  uint32_t *sC = tile + NP * d;     // nets: d x 32 columns; lattices: g
+  uint32_t *zrun = sC + 32 * d;     // nets: (NP / RL) x d run words
+  uint32_t *ztile = zrun + runs;    // nets: d tile words (shift included)
+  const uint32_t rl = blockIdx.y, r = r0 + rl;
+  const uint64_t base = ((i0 >> lognp) + blockIdx.x) << lognp;  // < 2^32 (i0 + n <= 2^32)
+  const int t = threadIdx.x;
+  if constexpr (NET) {
+    for (uint32_t q = t; q < 32 * d; q += kGenNT) sC[q] = Ct[(size_t)r * d * 32 + q];
+    __syncthreads();
+    for (uint32_t w = t; w < runs; w += kGenNT) {
+      const uint32_t q = w / d, j = w - q * d;
+      zrun[w] = xor_columns(sC + j * 32, order_map(order, q * kGenRL));
+    }
+    for (uint32_t j = t; j < d; j += kGenNT)
+      ztile[j] = xor_columns(sC + j * 32, order_map(order, (uint32_t)base)) ^ (D ? D[(size_t)r * d + j] : 0u);
+  } else {
+    for (uint32_t j = t; j < d; j += kGenNT) sC[j] = g[j];
+    for (uint32_t j = t; j < d; j += kGenNT) ztile[j] = D ? D[(size_t)r * d + j] : 0u;
   }
+  __syncthreads();
+  for (uint32_t w = t; w < runs; w += kGenNT) {
+    const uint32_t q = w / d, j = w - q * d;
+    uint32_t *dst = tile + q * kGenRL * d + j;
+    if constexpr (NET) {
+      const uint32_t *cj = sC + j * 32;
+      const uint32_t c0 = cj[0], c1 = cj[1], c2 = cj[2];
+      // step k -> k + 1 flips digit ctz(k + 1) of the Gray index, digits 0 .. ctz(k + 1) of i
+      const uint32_t s0 = c0, s1 = order == QK_GRAY ? c1 : (c0 ^ c1), s2 = order == QK_GRAY ? c2 : (c0 ^ c1 ^ c2);
+      uint32_t x = ztile[j] ^ zrun[w];
+      dst[0] = x;
+      x ^= s0, dst[1 * d] = x;
+      x ^= s1, dst[2 * d] = x;
+      x ^= s0, dst[3 * d] = x;
+      x ^= s2, dst[4 * d] = x;
+      x ^= s0, dst[5 * d] = x;
+      x ^= s1, dst[6 * d] = x;
+      x ^= s0, dst[7 * d] = x;
+    } else {
+      const uint32_t gj = sC[j], dj = ztile[j];
+      const uint32_t i = (uint32_t)base + q * kGenRL;
+#pragma unroll
+      for (int k = 0; k < kGenRL; ++k) dst[k * d] = __brev(i + k) * gj + dj;
+    }
+  }
+  __syncthreads();
+  const uint64_t lo = base > i0 ? base : i0, hi = (base + NP) < (i0 + n) ? (base + NP) : (i0 + n);
+  const uint64_t words = (hi - lo) * d;
+  const uint32_t *src = tile + (lo - base) * d;
+  uint32_t *out = X + ((uint64_t)rl * n + (lo - i0)) * d;
+  for (uint64_t e = t; e < words; e += kGenNT) out[e] = src[e];
 }
 
 int launch_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64_t i0, uint64_t n,
                       uint32_t *X, cudaStream_t st) {
   if (n == 0 || nr == 0) return QK_OK;
-  const uint64_t total = n * ps->d;
-  uint64_t blocks = (total + 255) / 256;
-  if (blocks > (uint64_t)kSMs * 64) blocks = (uint64_t)kSMs * 64;
-  dim3 grid((unsigned)blocks, nr);
-  if (ps->kind == QK_NET_B2) {
-    const size_t smem = (size_t)ps->d * 32 * sizeof(uint32_t);
-    smem_optin<k_points_net>(smem);
-    k_points_net<<<grid, 256, smem, st>>>(ps->d, ps->order, ps->Ct, ps->D, r0, i0, n, X);
-  } else {
-    k_points_lattice<<<grid, 256, 0, st>>>(ps->d, ps->g, ps->D, r0, i0, n, X);
+  const uint32_t d = ps->d, lognp = gen_lognp(d), NP = 1u << lognp;
+  const uint64_t tiles = ((i0 + n - 1) >> lognp) - (i0 >> lognp) + 1;
+  const size_t smem = sizeof(uint32_t) * ((size_t)NP * d + 32 * d + (NP / kGenRL) * d + d);
+  if (ps->kind == QK_NET_B2) smem_optin<k_points_tiled<true>>(smem);
+  else smem_optin<k_points_tiled<false>>(smem);
+  for (uint32_t rc = 0; rc < nr; rc += 65535) {  // grid.y limit
+    const uint32_t cnt = nr - rc < 65535 ? nr - rc : 65535;
+    dim3 grid((unsigned)tiles, cnt);
+    uint32_t *Xc = X + (size_t)rc * n * d;
+    if (ps->kind == QK_NET_B2)
+      k_points_tiled<true><<<grid, kGenNT, smem, st>>>(d, ps->order, ps->Ct, nullptr, ps->D, r0 + rc, i0, n, lognp, Xc);
+    else
+      k_points_tiled<false><<<grid, kGenNT, smem, st>>>(d, ps->order, nullptr, ps->g, ps->D, r0 + rc, i0, n, lognp, Xc);
+    int rc_ = check_launch("qk_gen_points");
+    if (rc_) return rc_;
   }
-  return check_launch("qk_gen_points");
+  return QK_OK;
 }
 
 template <typename T, int FAM, int ALPHA>
@@ -138,6 +186,63 @@ static void launch_col_t(const ColJob &job, int form, T *out, cudaStream_t st) {
   k_kernel_col<T, FAM, ALPHA><<<grid, kNT, smem, st>>>(job, form, out);
 }
 
+// The first column in float-float arithmetic on the FP32 pipes (about 2^-46 relative per
+// factor), written as FP64: for spectra that reach far below eps32 ||k_1||, where an FP32
+// column would perturb the small eigenvalues beyond the 1/lambda-weighted outputs' tolerance.
+template <int FAM, int ALPHA>
+__global__ void __launch_bounds__(kNT) k_kernel_col_ff(ColJob job, int form, double *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  double *wd;
+  DiffTables tb;
+  carve_tables<kL>(smem, job.d, &wd, tb);
+  float2 *wff = reinterpret_cast<float2 *>(wd);
+  const uint32_t rl = blockIdx.y;
+  const uint64_t n = 1ull << job.m;
+  const uint64_t tile_base = job.i0 + (uint64_t)blockIdx.x * kTile;
+  for (uint32_t q = threadIdx.x; q < job.d; q += kNT) wff[q] = ff_split(job.w[q]);
+  build_all_ff<FAM, ALPHA, kL>(job, job.Ct ? job.Ct + (size_t)rl * job.d * 32 : nullptr, job.g, tile_base, tb);
+  __syncthreads();
+  uint32_t bi[kL];
+#pragma unroll
+  for (int l = 0; l < kL; ++l) bi[l] = __brev((uint32_t)(tile_base + threadIdx.x + (l << 8)));
+  float ph[kL], pl[kL];
+  column_sweep_ff<FAM, ALPHA, kL>(job, tb, wff, bi, ph, pl);
+#pragma unroll
+  for (int l = 0; l < kL; ++l) {
+    const uint64_t i = tile_base - job.i0 + threadIdx.x + ((uint64_t)l << 8);
+    const double p = f2d_exact(ph[l]) + f2d_exact(pl[l]);
+    if (i < n) out[(size_t)rl * n + i] = form == QK_COL_P ? p : job.zeta + job.zeta * p;
+  }
+}
+
+template <int FAM, int ALPHA>
+static void launch_col_ff(const ColJob &job, int form, double *out, cudaStream_t st) {
+  const uint64_t n = 1ull << job.m;
+  dim3 grid(ceil_div_u(n, kTile), job.nr);
+  const size_t smem = col_smem_bytes<kL>(job.d);
+  smem_optin<k_kernel_col_ff<FAM, ALPHA>>(smem);
+  k_kernel_col_ff<FAM, ALPHA><<<grid, kNT, smem, st>>>(job, form, out);
+}
+
+static int dispatch_col_ff(const ColJob &job, int form, double *out, cudaStream_t st) {
+  if (job.family == QK_DSI) {
+    switch (job.alpha) {
+      case 1: launch_col_ff<0, 1>(job, form, out, st); break;
+      case 2: launch_col_ff<0, 2>(job, form, out, st); break;
+      case 3: launch_col_ff<0, 3>(job, form, out, st); break;
+      case 4: launch_col_ff<0, 4>(job, form, out, st); break;
+      default: return fail(QK_EINVAL, "DSI order must be 1..4");
+    }
+  } else {
+    switch (job.alpha) {
+      case 1: launch_col_ff<1, 1>(job, form, out, st); break;
+      case 2: launch_col_ff<1, 2>(job, form, out, st); break;
+      default: return fail(QK_EINVAL, "SI smoothness must be 1 or 2");
+    }
+  }
+  return check_launch("qk_kernel_col (float-float)");
+}
+
 template <typename T>
 static int dispatch_col(const ColJob &job, int form, T *out, cudaStream_t st) {
   if (job.family == QK_DSI) {
@@ -160,6 +265,7 @@ static int dispatch_col(const ColJob &job, int form, T *out, cudaStream_t st) {
 
 int launch_kernel_col(const ColJob &job, int32_t dtype, int32_t form, void *out, cudaStream_t st) {
   if (job.nr == 0) return QK_OK;
+  if (dtype == QK_F32W) return dispatch_col_ff(job, form, (double *)out, st);
   return dtype == QK_F64 ? dispatch_col<double>(job, form, (double *)out, st)
                          : dispatch_col<float>(job, form, (float *)out, st);
 }
@@ -242,6 +348,7 @@ static int dispatch_grad(const ColJob &job, uint32_t nrhs, const T *u, double *p
 int launch_grad_partials(const ColJob &job, uint32_t nrhs, int32_t dtype, const void *u, double *partial,
                          cudaStream_t st) {
   if (job.nr == 0 || nrhs == 0) return QK_OK;
+  if (job.kind == kHONet) return launch_grad_partials_ho(job, nrhs, dtype, u, partial, st);
   return dtype == QK_F64 ? dispatch_grad<double>(job, nrhs, (const double *)u, partial, st)
                          : dispatch_grad<float>(job, nrhs, (const float *)u, partial, st);
 }

@@ -13,6 +13,7 @@
 // kernel column is real and symmetric in linear order, so lambda and H g are real.
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "qk_common.cuh"
 #include "qk_internal.h"
@@ -204,7 +205,7 @@ __global__ void k_mll_final(FinalArgs a) {
 // ------------------------------------------------------------ host helpers
 static unsigned grid_for(uint64_t count) {
   uint64_t b = (count + 255) / 256;
-  const uint64_t cap = (uint64_t)kSMs * 32;
+  const uint64_t cap = (uint64_t)sm_count() * 32;
   return (unsigned)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
@@ -232,6 +233,15 @@ static int inv(int family, E *x, int m, uint64_t nvec, double scale, cudaStream_
   else return xform<E, XF_WHT>(x, m, nvec, scale, st);
 }
 
+// count * bytes, rounded up to 256, saturating at SIZE_MAX: a workspace size that does not
+// fit size_t must not wrap to a small number (callers compare it with what they hold).
+static size_t sized(uint64_t count_hi, uint32_t m, size_t bytes) {
+  const size_t cap = SIZE_MAX - 255;
+  if (count_hi != 0 && (bytes == 0 ? false : count_hi > ((cap / bytes) >> m))) return SIZE_MAX;
+  return align256(bytes * (count_hi << m));
+}
+static size_t add_sat(size_t a, size_t b) { return a > SIZE_MAX - b ? SIZE_MAX : a + b; }
+
 size_t elem_bytes(int family, int dtype) {
   const size_t s = dtype == QK_F64 ? 8 : 4;
   return family == QK_SI ? 2 * s : s;
@@ -239,26 +249,30 @@ size_t elem_bytes(int family, int dtype) {
 
 // Workspace sizes (bytes) per op; see qk_workspace_bytes.
 size_t ws_eigs(int family, uint32_t m, uint32_t batch, int dtype) {
-  return align256(elem_bytes(family, dtype) * ((uint64_t)batch << m));
+  return sized(batch, m, elem_bytes(family, dtype));
 }
 size_t ws_solve(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype) {
-  const uint64_t cnt = ((uint64_t)batch * nrhs) << m;
+  const uint64_t nv = (uint64_t)batch * nrhs;
   // X (E) + residual path: FP64 element buffer + T buffer
-  return align256(elem_bytes(family, dtype) * cnt) + align256(elem_bytes(family, QK_F64) * cnt) +
-         align256((dtype == QK_F64 ? 8 : 4) * cnt);
+  return add_sat(add_sat(sized(nv, m, elem_bytes(family, dtype)), sized(nv, m, elem_bytes(family, QK_F64))),
+                 sized(nv, m, dtype == QK_F64 ? 8 : 4));
+}
+size_t ws_matvec(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype) {
+  return sized((uint64_t)batch * nrhs, m, elem_bytes(family, dtype));
 }
 uint32_t spec_blocks(uint32_t m) {
   const uint64_t b = ((1ull << m) + 4095) / 4096;
   return (uint32_t)(b > 256 ? 256 : b);
 }
+// dtype QK_F32W: FP32 y and gradient sweep, FP64 transforms and spectral sums.
 size_t ws_mll(int family, uint32_t m, uint32_t nr, uint32_t nrhs, int dtype, uint32_t d) {
   const uint64_t nv = (uint64_t)nr * nrhs;
-  size_t s = align256(elem_bytes(family, dtype) * (nv << m));
-  if (family == QK_SI) s += align256((dtype == QK_F64 ? 8 : 4) * (nv << m));  // real u
-  s += align256(nv * spec_blocks(m) * 2 * sizeof(double));
-  s += align256((uint64_t)nr * spec_blocks(m) * sizeof(double));
-  s += align256(nv * sizeof(double));
-  s += align256(nv * grad_blocks(m) * 2 * (uint64_t)d * sizeof(double));
+  size_t s = sized(nv, m, elem_bytes(family, dtype == QK_F32W ? QK_F64 : dtype));
+  if (family == QK_SI || dtype == QK_F32W) s = add_sat(s, sized(nv, m, dtype == QK_F64 ? 8 : 4));  // real u
+  s = add_sat(s, align256(nv * spec_blocks(m) * 2 * sizeof(double)));
+  s = add_sat(s, align256((uint64_t)nr * spec_blocks(m) * sizeof(double)));
+  s = add_sat(s, align256(nv * sizeof(double)));
+  s = add_sat(s, align256(nv * grad_blocks(m) * 2 * (uint64_t)d * sizeof(double)));
   return s;
 }
 
@@ -470,6 +484,25 @@ int op_solve(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, c
   return solve_t<float, float2, double2>(family, m, batch, nrhs, lam, (const float *)y, (float *)c, refine, ws, st);
 }
 
+// X <- the unnormalised forward transform (H, or the DFT of the data in linear order) of
+// nvec real vectors `in` of dtype; X holds elements of the transform type (real for nets,
+// complex for lattices) in the same precision.
+int op_forward_real(int family, uint32_t m, uint64_t nvec, int dtype, const void *in, void *X, cudaStream_t st) {
+  const uint64_t cnt = nvec << m;
+  int rc;
+  if (family == QK_DSI) {
+    if (dtype == QK_F64) k_load_real<double, double><<<grid_for(cnt), 256, 0, st>>>((const double *)in, (double *)X, cnt);
+    else k_load_real<float, float><<<grid_for(cnt), 256, 0, st>>>((const float *)in, (float *)X, cnt);
+    if ((rc = check_launch("forward load"))) return rc;
+    return dtype == QK_F64 ? fwd<double>(family, (double *)X, (int)m, nvec, st) : fwd<float>(family, (float *)X, (int)m, nvec, st);
+  }
+  if (dtype == QK_F64) k_load_real<double, double2><<<grid_for(cnt), 256, 0, st>>>((const double *)in, (double2 *)X, cnt);
+  else k_load_real<float, float2><<<grid_for(cnt), 256, 0, st>>>((const float *)in, (float2 *)X, cnt);
+  if ((rc = check_launch("forward load"))) return rc;
+  return dtype == QK_F64 ? fwd<double2>(family, (double2 *)X, (int)m, nvec, st)
+                         : fwd<float2>(family, (float2 *)X, (int)m, nvec, st);
+}
+
 int op_matvec(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, const double *lam, const void *y,
               void *u, void *ws, cudaStream_t st) {
   const uint32_t nvec = batch * nrhs;
@@ -489,8 +522,11 @@ static int mll_t(const ColJob &job, uint32_t nrhs, const double *lam, const T *y
   unsigned char *p = (unsigned char *)ws;
   E *X = (E *)p;
   p += align256(sizeof(E) * cnt);
-  T *u = (T *)X;  // DSI: E == T, the transform output is u itself
-  if (job.family == QK_SI) {
+  // the transform output is u itself when E == T (nets in the data precision); otherwise
+  // (lattices: complex; FP64 transforms of FP32 data) its real part is stored as T
+  constexpr bool SEP_U = !std::is_same<E, T>::value;
+  T *u = (T *)X;
+  if (SEP_U) {
     u = (T *)p;
     p += align256(sizeof(T) * cnt);
   }
@@ -513,17 +549,17 @@ static int mll_t(const ColJob &job, uint32_t nrhs, const double *lam, const T *y
   if ((rc = check_launch("mll spectral"))) return rc;
   if (dtype == QK_F64)
     k_logdet<false><<<dim3(bs, job.nr), kRedNT, 0, st>>>(lam, (int)m, log_part);
-  else
+  else  // FP32 logs of FP32-rounded eigenvalues: each log is off by ~eps32 (absolute)
     k_logdet<true><<<dim3(bs, job.nr), kRedNT, 0, st>>>(lam, (int)m, log_part);
   if ((rc = check_launch("mll logdet"))) return rc;
   if (grad) {
     // u = H g (nets) or the DFT of g read back in natural order (lattices); real.
     if ((rc = inv<E>(job.family, X, (int)m, nvec, 1.0, st))) return rc;
-    if (job.family == QK_SI) {
+    if (SEP_U) {
       k_store_real<E, T><<<grid_for(cnt), 256, 0, st>>>(X, u, cnt, 1.0);
       if ((rc = check_launch("mll u"))) return rc;
     }
-    if ((rc = launch_grad_partials(job, nrhs, dtype, u, grad_part, st))) return rc;
+    if ((rc = launch_grad_partials(job, nrhs, sizeof(T) == 8 ? QK_F64 : QK_F32, u, grad_part, st))) return rc;
   }
   FinalArgs fa;
   fa.nvec = nvec;
@@ -547,6 +583,9 @@ static int mll_t(const ColJob &job, uint32_t nrhs, const double *lam, const T *y
 
 int op_mll(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const void *y, double *out, double *grad,
            void *ws, cudaStream_t st) {
+  if (dtype == QK_F32W)
+    return job.family == QK_DSI ? mll_t<float, double>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype)
+                                : mll_t<float, double2>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype);
   if (job.family == QK_DSI)
     return dtype == QK_F64 ? mll_t<double, double>(job, nrhs, lam, (const double *)y, out, grad, ws, st, dtype)
                            : mll_t<float, float>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype);

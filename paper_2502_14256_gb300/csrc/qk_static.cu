@@ -63,12 +63,14 @@ extern "C" int qk_eigs_static(int32_t family, uint32_t m, uint32_t batch, int32_
   if (batch == 0) return QK_OK;
   if (!col || !lam) return fail(QK_EINVAL, "qk_eigs_static: NULL array");
   if (!(zeta > 0.0)) return fail(QK_EINVAL, "zeta must be > 0");
-  const size_t need = ws_eigs(family, m, batch, dtype);
+  // bound the element count before any multiplication (batch << m can exceed 2^64 / 16)
+  const size_t eb = elem_bytes(family, dtype);
+  const size_t need = (uint64_t)batch > ((QK_EIGS_STATIC_MAX_BYTES / eb) >> m) ? SIZE_MAX : ws_eigs(family, m, batch, dtype);
   if (need > QK_EIGS_STATIC_MAX_BYTES)
     return fail(QK_EINVAL,
-                "qk_eigs_static: %u column(s) of 2^%u need %zu bytes of scratch, more than the %zu-byte "
-                "static array; call qk_eigs with a workspace instead",
-                batch, m, need, (size_t)QK_EIGS_STATIC_MAX_BYTES);
+                "qk_eigs_static: %u column(s) of 2^%u need more scratch than the %zu-byte static array; "
+                "call qk_eigs with a workspace instead",
+                batch, m, (size_t)QK_EIGS_STATIC_MAX_BYTES);
   void *ws = nullptr;
   int rc = static_scratch(&ws);
   if (rc) return rc;

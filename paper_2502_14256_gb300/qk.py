@@ -22,10 +22,13 @@ QK_STATUS_NOTPD, QK_STATUS_TIMEOUT, QK_STATUS_FLOOR = 1, 2, 4
 QK_NET_B2, QK_LATTICE = 0, 1
 QK_NATURAL, QK_GRAY = 0, 1
 QK_DSI, QK_SI = 0, 1
-QK_F64, QK_F32 = 0, 1
+QK_F64, QK_F32, QK_F32W = 0, 1, 2
+# Precision name for QK_F32W (FP32 data, float-float first column): pass it where a torch
+# dtype names the schedule's precision (batch_workspace_bytes, batch_plan; kernel_col(wide=True)).
+F32W = "float32w"
 QK_COL_K1, QK_COL_P = 0, 1
 QK_MLL_QUAD, QK_MLL_LOGDET, QK_MLL_MLL, QK_MLL_MEAN, QK_MLL_VAR, QK_MLL_NOUT = range(6)
-OP_EIGS, OP_SOLVE, OP_MATVEC, OP_MLL, OP_FWHT = 0, 1, 2, 3, 4
+OP_EIGS, OP_SOLVE, OP_MATVEC, OP_MLL, OP_FWHT, OP_DISCREPANCY = 0, 1, 2, 3, 4, 5
 QK_FWHT_TWO_PASS, QK_FWHT_PERSISTENT = 0, 1
 QK_SCHED_LAUNCHES, QK_SCHED_PERSISTENT = 0, 1
 QK_MAX_M, QK_MAX_D = 30, 256
@@ -35,7 +38,12 @@ EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_sol
             "qk_read_status", "qk_last_error", "qk_version", "qk_fwht", "qk_fftbr", "qk_ifftbr",
             "qk_launch_count", "qk_eigs_static", "qk_batch_timing", "qk_batch_kernel_ms", "qk_fwht_ws",
             "qk_fwht_tune", "qk_fwht_wait_selftest", "qk_batch_run_host", "qk_batch_schedule",
-            "qk_kernel_col_at", "qk_eigs_extend", "qk_fwht_extend", "qk_fftbr_extend", "qk_batch_tune"]
+            "qk_kernel_col_at", "qk_eigs_extend", "qk_fwht_extend", "qk_fftbr_extend", "qk_batch_tune",
+            "qk_integrand", "qk_rqmc", "qk_student_t_quantile", "qk_discrepancy", "qk_discrepancy_weights",
+            "qk_interlace", "qk_gen_points_ho", "qk_kernel_col_ho", "qk_mll_spectrum", "qk_mll_ho"]
+QK_F_SIMPLE1, QK_F_SIMPLE2, QK_F_OAKLEY, QK_F_GFUN, QK_F_GENZ_OSC, QK_F_GENZ_CP = range(6)
+INTEGRANDS = {"simple1": QK_F_SIMPLE1, "simple2": QK_F_SIMPLE2, "oakley": QK_F_OAKLEY, "gfun": QK_F_GFUN,
+              "genz_osc": QK_F_GENZ_OSC, "genz_cp": QK_F_GENZ_CP}
 
 
 class QKError(RuntimeError):
@@ -52,6 +60,10 @@ class PointSet(C.Structure):
 class Kernel(C.Structure):
     _fields_ = [("family", C.c_int32), ("alpha", C.c_int32), ("d", C.c_uint32), ("weights", C.c_void_p),
                 ("zeta", C.c_double)]
+
+
+class HOPointSet(C.Structure):
+    _fields_ = [("order", C.c_int32), ("d", C.c_uint32), ("R", C.c_uint32), ("Chat", C.c_void_p), ("D", C.c_void_p)]
 
 
 class FwhtPlan(C.Structure):
@@ -106,6 +118,16 @@ def _load():
         "qk_eigs_extend": [i32, u32, u32, i32, i32, P, dbl, dbl, P, P, P, sz, P, P],
         "qk_fwht_extend": [u32, u64, i32, P, P, P, P],
         "qk_fftbr_extend": [u32, u64, i32, P, P, P, P],
+        "qk_integrand": [C.POINTER(PointSet), u32, u32, u64, u64, i32, i32, i32, P, P],
+        "qk_rqmc": [u32, u64, i32, P, dbl, P, P],
+        "qk_student_t_quantile": [dbl, dbl, C.POINTER(dbl)],
+        "qk_discrepancy": [i32, u32, u32, i32, i32, P, dbl, P, P],
+        "qk_discrepancy_weights": [i32, u32, u32, u32, i32, P, P, dbl, P, P, sz, P],
+        "qk_interlace": [u32, u32, u32, P, P, P],
+        "qk_gen_points_ho": [C.POINTER(HOPointSet), u32, u32, u64, u64, P, P],
+        "qk_kernel_col_ho": [C.POINTER(HOPointSet), C.POINTER(Kernel), u32, u32, u32, i32, i32, P, P],
+        "qk_mll_spectrum": [i32, u32, u32, u32, i32, dbl, P, P, P, P, sz, P],
+        "qk_mll_ho": [C.POINTER(HOPointSet), C.POINTER(Kernel), u32, u32, u32, u32, i32, P, P, P, P, P, sz, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -143,12 +165,21 @@ def _stream(stream=None) -> int:
     return s.cuda_stream
 
 
-def dtype_code(dt: torch.dtype) -> int:
+def dtype_code(dt) -> int:
+    if isinstance(dt, str):
+        if dt == F32W:
+            return QK_F32W
+        raise ValueError(f"unsupported precision {dt!r}")
     if dt == torch.float64:
         return QK_F64
     if dt == torch.float32:
         return QK_F32
     raise ValueError(f"unsupported dtype {dt}")
+
+
+def data_dtype(dt) -> torch.dtype:
+    """The torch dtype of the y / c arrays of a schedule of precision dt."""
+    return torch.float32 if dt == F32W else dt
 
 
 # --------------------------------------------------------------- structures
@@ -173,16 +204,27 @@ def gen_points(ps: PointSet, r0: int, nr: int, i0: int, n: int, X, stream=None):
     return X
 
 
-def kernel_col(ps: PointSet, k: Kernel, r0: int, nr: int, m: int, col, form: int = QK_COL_K1, stream=None):
-    _check(LIB.qk_kernel_col(C.byref(ps), C.byref(k), r0, nr, m, dtype_code(col.dtype), form, _ptr(col),
+def _col_code(col, wide: bool) -> int:
+    if wide:
+        if col.dtype != torch.float64:
+            raise ValueError("the float-float column (wide=True) is written as float64")
+        return QK_F32W
+    return dtype_code(col.dtype)
+
+
+def kernel_col(ps: PointSet, k: Kernel, r0: int, nr: int, m: int, col, form: int = QK_COL_K1, stream=None,
+               wide: bool = False):
+    """First column; wide=True computes it in float-float arithmetic (FP32 pipes) into a
+    float64 tensor (QK_F32W)."""
+    _check(LIB.qk_kernel_col(C.byref(ps), C.byref(k), r0, nr, m, _col_code(col, wide), form, _ptr(col),
                              _stream(stream)))
     return col
 
 
 def kernel_col_at(ps: PointSet, k: Kernel, r0: int, nr: int, i0: int, m: int, col, form: int = QK_COL_K1,
-                  stream=None):
+                  stream=None, wide: bool = False):
     """First-column entries of the 2^m points at positions i0 .. i0 + 2^m - 1."""
-    _check(LIB.qk_kernel_col_at(C.byref(ps), C.byref(k), r0, nr, i0, m, dtype_code(col.dtype), form, _ptr(col),
+    _check(LIB.qk_kernel_col_at(C.byref(ps), C.byref(k), r0, nr, i0, m, _col_code(col, wide), form, _ptr(col),
                                 _stream(stream)))
     return col
 
@@ -223,7 +265,7 @@ def workspace(nbytes: int, device="cuda"):
 
 def eigs(family: int, m: int, col, lam, zeta: float = 1.0, eta: float = 0.0, form: int = QK_COL_K1,
          ws=None, status=None, stream=None):
-    batch = col.numel() >> m
+    batch = _check_spectrum_args(m, col, lam)
     if ws is None:
         ws = workspace(workspace_bytes(OP_EIGS, family, m, batch, 1, col.dtype), col.device)
     _check(LIB.qk_eigs(family, m, batch, dtype_code(col.dtype), form, _ptr(col), zeta, eta, _ptr(lam), _ptr(ws),
@@ -231,11 +273,26 @@ def eigs(family: int, m: int, col, lam, zeta: float = 1.0, eta: float = 0.0, for
     return lam
 
 
+def _check_spectrum_args(m: int, col, lam) -> int:
+    """Batch count of a (batch, 2^m) column and its (batch, 2^m) float64 eigenvalue output on
+    the current device; ValueError on a mismatch (the C side trusts these sizes)."""
+    n = 1 << m
+    if col.numel() % n != 0:
+        raise ValueError(f"column holds {col.numel()} elements, not a multiple of 2^{m}")
+    if lam.dtype != torch.float64 or lam.numel() != col.numel():
+        raise ValueError("lam must be a float64 tensor with as many elements as the column")
+    dev = torch.cuda.current_device()
+    for name, t in (("col", col), ("lam", lam)):
+        if not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must live on the current CUDA device (cuda:{dev})")
+    return col.numel() // n
+
+
 def eigs_static(family: int, m: int, col, lam, zeta: float = 1.0, eta: float = 0.0, form: int = QK_COL_K1,
                 status=None, stream=None):
     """qk_eigs without a workspace: the library's static device scratch is used
     (for callers that cannot allocate; see include/qk.h for its size limit)."""
-    batch = col.numel() >> m
+    batch = _check_spectrum_args(m, col, lam)
     _check(LIB.qk_eigs_static(family, m, batch, dtype_code(col.dtype), form, _ptr(col), zeta, eta, _ptr(lam),
                               _ptr(status), _stream(stream)))
     return lam
@@ -406,4 +463,100 @@ def batch_kernel_ms(ws):
             break
         out[name.value.decode()] = (cnt.value, ms.value)
         idx += 1
+    return out
+
+
+# ------------------------------------------------------------- RQMC integration
+def integrand(ps: PointSet, r0: int, nr: int, i0: int, n: int, f, y, baker: bool = False, stream=None):
+    """y (nr, n) <- f at the points (f: a name of INTEGRANDS or its QK_F_* code)."""
+    code = INTEGRANDS[f] if isinstance(f, str) else int(f)
+    _check(LIB.qk_integrand(C.byref(ps), r0, nr, i0, n, code, 1 if baker else 0, dtype_code(y.dtype), _ptr(y),
+                            _stream(stream)))
+    return y
+
+
+def rqmc(y, tau: float, out=None, stream=None):
+    """RQMC estimate of y (R, n): device doubles [mu, sigma, half width, t, mu_1 .. mu_R]."""
+    R, n = y.shape
+    if out is None:
+        out = torch.empty(4 + R, dtype=torch.float64, device=y.device)
+    _check(LIB.qk_rqmc(R, n, dtype_code(y.dtype), _ptr(y), float(tau), _ptr(out), _stream(stream)))
+    return out
+
+
+def student_t_quantile(df: float, p: float) -> float:
+    q = C.c_double(0.0)
+    _check(LIB.qk_student_t_quantile(float(df), float(p), C.byref(q)))
+    return q.value
+
+
+def discrepancy(family: int, m: int, col, zeta: float = 1.0, form: int = QK_COL_P, out=None, stream=None):
+    """Squared worst-case error for equal and optimal weights from first columns (batch, 2^m):
+    (batch, 3) doubles [equal, optimal, optimal weight]."""
+    batch = col.numel() >> m
+    if col.numel() != batch << m:
+        raise ValueError(f"column holds {col.numel()} elements, not a multiple of 2^{m}")
+    if out is None:
+        out = torch.empty((batch, 3), dtype=torch.float64, device=col.device)
+    _check(LIB.qk_discrepancy(family, m, batch, dtype_code(col.dtype), form, _ptr(col), float(zeta), _ptr(out),
+                              _stream(stream)))
+    return out
+
+
+def discrepancy_weights(family: int, m: int, lam, w, zeta: float = 1.0, out=None, ws=None, stream=None):
+    """Squared worst-case error of weights w (batch, nw, 2^m) given eigenvalues lam (batch, 2^m)."""
+    batch = lam.numel() >> m
+    nw = (w.numel() >> m) // batch
+    if out is None:
+        out = torch.empty((batch, nw), dtype=torch.float64, device=w.device)
+    if ws is None:
+        ws = workspace(workspace_bytes(OP_DISCREPANCY, family, m, batch, nw, w.dtype), w.device)
+    _check(LIB.qk_discrepancy_weights(family, m, batch, nw, dtype_code(w.dtype), _ptr(lam), _ptr(w), float(zeta),
+                                      _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+# ------------------------------------------------------------ higher-order nets
+def interlace(alpha: int, Ct, Chat, stream=None):
+    """Chat (R, d, 32) int64 <- interlacing of order alpha of Ct (R, alpha d, 32) int32."""
+    R, ad = Ct.shape[0], Ct.shape[1]
+    if ad % alpha != 0:
+        raise ValueError("Ct holds alpha d matrices per randomization")
+    _check(LIB.qk_interlace(ad // alpha, R, alpha, _ptr(Ct), _ptr(Chat), _stream(stream)))
+    return Chat
+
+
+def ho_pointset(d: int, R: int, Chat, D=None, order: int = QK_GRAY) -> HOPointSet:
+    return HOPointSet(order, d, R, _ptr(Chat), _ptr(D))
+
+
+def gen_points_ho(ps: HOPointSet, r0: int, nr: int, i0: int, n: int, X, stream=None):
+    _check(LIB.qk_gen_points_ho(C.byref(ps), r0, nr, i0, n, _ptr(X), _stream(stream)))
+    return X
+
+
+def kernel_col_ho(ps: HOPointSet, k: Kernel, r0: int, nr: int, m: int, col, form: int = QK_COL_K1, stream=None):
+    _check(LIB.qk_kernel_col_ho(C.byref(ps), C.byref(k), r0, nr, m, dtype_code(col.dtype), form, _ptr(col),
+                                _stream(stream)))
+    return col
+
+
+def mll_spectrum(family: int, m: int, lam, y, out, zeta: float = 1.0, ws=None, stream=None):
+    """MLL pieces from eigenvalues lam (nr, 2^m) and y (nr, nrhs, 2^m), without a point set."""
+    nr = lam.numel() >> m
+    nrhs = (y.numel() >> m) // nr
+    if ws is None:
+        ws = workspace(workspace_bytes(OP_MLL, family, m, nr, nrhs, y.dtype, 0), y.device)
+    _check(LIB.qk_mll_spectrum(family, m, nr, nrhs, dtype_code(y.dtype), float(zeta), _ptr(lam), _ptr(y), _ptr(out),
+                               _ptr(ws), ws.numel(), _stream(stream)))
+    return out
+
+
+def mll_ho(ps: HOPointSet, k: Kernel, r0: int, nr: int, m: int, nrhs: int, lam, y, out, grad=None, ws=None,
+           stream=None):
+    """qk_mll for a higher-order net (MLL pieces and, with grad, the gradient block)."""
+    if ws is None:
+        ws = workspace(workspace_bytes(OP_MLL, QK_DSI, m, nr, nrhs, y.dtype, ps.d), y.device)
+    _check(LIB.qk_mll_ho(C.byref(ps), C.byref(k), r0, nr, m, nrhs, dtype_code(y.dtype), _ptr(lam), _ptr(y), _ptr(out),
+                         _ptr(grad), _ptr(ws), ws.numel(), _stream(stream)))
     return out

@@ -2,6 +2,7 @@
 uploaded as raw 32-bit words, with the oracle's reference arrays beside them."""
 from __future__ import annotations
 
+import math
 from dataclasses import dataclass
 
 import numpy as np
@@ -83,6 +84,34 @@ def kernel_of(case):
     case.keep.append(w)
     fam = qk.QK_DSI if case.family == "dsi" else qk.QK_SI
     return qk.kernel(fam, case.alpha, w, case.zeta)
+
+
+def lam_elementwise_ok(got, want, rel, eps, m, factor=8.0):
+    """Every eigenvalue within rel of the reference, or within the absolute rounding floor of
+    an eps-precision transform of the first column, factor * sqrt(m + 1) * eps * max|lambda|
+    (the normwise check alone admits that much error on every eigenvalue, the smallest
+    included; this one bounds each by its own size first)."""
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    floor = factor * np.sqrt(m + 1) * eps * np.max(np.abs(want))
+    return bool(np.all(np.abs(got - want) <= rel * np.abs(want) + floor))
+
+
+def lam_elementwise_report(got, want):
+    err = np.abs(np.asarray(got) - np.asarray(want))
+    k = int(np.argmax(err / np.abs(want)))
+    return {"worst_rel": float(err[k] / abs(want[k])), "at_lambda": float(want[k]), "max_lambda": float(np.max(np.abs(want))),
+            "abs_err": float(err[k])}
+
+
+def ff_column_floor(lam, d):
+    """Absolute perturbation of every eigenvalue by a float-float first column: about 2^-46
+    per operation, ~5 operations per factor and d factors in a random walk, times ~6 for the
+    largest of n Gaussian-like errors, applied to each entry of p (rms ||lambda_{w>0}|| / n),
+    summed by the transform (sqrt(n)): 2^-46 sqrt(5 d) 6 ||lambda_{w>0}||_2 / sqrt(n)."""
+    lam = np.asarray(lam, dtype=np.float64)
+    n = lam.shape[-1]
+    return 2.0 ** -46 * math.sqrt(5 * d) * 6.0 * float(np.linalg.norm(lam[1:])) / math.sqrt(n)
 
 
 def cond_tol(lam, base, eps, factor=20.0):

@@ -111,11 +111,11 @@ def host_points(inst, r, idx):
 
 
 def outputs(qk, inst, dtype, with_c=True, with_lam=True, with_grad=True, y_via=None, eta=None):
-    """Output buffers and the task for one instance; y_via rounds y through another dtype
-    first (so that an FP64 run sees exactly the FP32 path's input); eta overrides the
-    workload's nugget."""
+    """Output buffers and the task for one instance; dtype is a torch dtype or qk.F32W (FP32
+    arrays); y_via rounds y through another dtype first (so that an FP64 run sees exactly the
+    FP32 path's input); eta overrides the workload's nugget."""
     R, n, d = inst.R, 1 << inst.m, inst.wl.d
-    y = (inst.y64.to(y_via) if y_via is not None else inst.y64).to(dtype).contiguous()
+    y = (inst.y64.to(y_via) if y_via is not None else inst.y64).to(qk.data_dtype(dtype)).contiguous()
     bufs = {
         "y": y,
         "c": torch.zeros_like(y) if with_c else None,
@@ -129,12 +129,15 @@ def outputs(qk, inst, dtype, with_c=True, with_lam=True, with_grad=True, y_via=N
     return task, bufs
 
 
-def run_tasks(qk, tasks, dtype, refine=0, graph=False, allow_floor=False):
-    """Plan and run one schedule over tasks; optionally capture it in a CUDA graph and replay.
+def run_tasks(qk, tasks, dtype, refine=0, graph=False, allow_floor=False, persistent=False):
+    """Plan and run one schedule over tasks; optionally as ONE persistent launch
+    (QK_SCHED_PERSISTENT), and optionally captured in a CUDA graph and replayed.
     Returns the workspace and the device status word (read and cleared here)."""
     ws = qk.workspace(qk.batch_workspace_bytes(tasks, dtype))
     status = torch.zeros(1, dtype=torch.int32, device=_dev())
     qk.batch_plan(tasks, dtype, refine, ws)
+    if persistent:
+        qk.batch_schedule(ws, qk.QK_SCHED_PERSISTENT, 1)
     if graph:
         qk.batch_run(ws, status)  # first call: module loading and shared-memory opt-ins
         torch.cuda.synchronize()

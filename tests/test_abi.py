@@ -156,3 +156,56 @@ def test_no_cpu_fallback_in_the_binding():
     src = open(os.path.join(ROOT, "paper_2502_14256_gb300", "qk.py")).read()
     assert "oracle" not in src
     assert "numpy" not in src
+
+
+def test_student_t_quantile_host_code_matches_scipy(lib_path):
+    """The library's host Student-t quantile (incomplete-beta CDF, bisection) against scipy."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    from paper_2502_14256_gb300 import qk
+    for df in (1, 2, 3, 5, 9, 14, 30, 63, 1000):
+        for p in (0.5, 0.6, 0.9, 0.95, 0.975, 0.995, 0.9995, 0.05, 0.005):
+            got = qk.student_t_quantile(df, p)
+            want = float(scipy_stats.t.ppf(p, df))
+            assert abs(got - want) <= 1e-12 * max(1.0, abs(want)), (df, p, got, want)
+    q = C.c_double(0.0)
+    assert qk.LIB.qk_student_t_quantile(0.0, 0.9, C.byref(q)) == qk.QK_EINVAL
+    assert qk.LIB.qk_student_t_quantile(5.0, 1.0, C.byref(q)) == qk.QK_EINVAL
+
+
+def test_rqmc_and_discrepancy_argument_errors(lib_path):
+    from paper_2502_14256_gb300 import qk
+    lib = qk.LIB
+    fake = C.c_void_p(0x2000000)
+    u64 = C.c_uint64
+    net1 = qk.PointSet(qk.QK_NET_B2, qk.QK_GRAY, 3, 1, fake, None, fake)
+    cases = [
+        lib.qk_integrand(C.byref(net1), 0, 1, u64(0), u64(16), qk.QK_F_SIMPLE1, 0, qk.QK_F64, fake, None),  # d != 1
+        lib.qk_integrand(C.byref(net1), 0, 1, u64(0), u64(16), qk.QK_F_OAKLEY, 0, qk.QK_F64, fake, None),   # d != 2
+        lib.qk_integrand(C.byref(net1), 0, 1, u64(0), u64(16), 9, 0, qk.QK_F64, fake, None),
+        lib.qk_integrand(C.byref(net1), 0, 1, u64((1 << 32) - 4), u64(8), qk.QK_F_GFUN, 0, qk.QK_F64, fake, None),
+        lib.qk_rqmc(1, u64(16), qk.QK_F64, fake, C.c_double(0.05), fake, None),
+        lib.qk_rqmc(4, u64(16), qk.QK_F64, fake, C.c_double(1.5), fake, None),
+        lib.qk_discrepancy(qk.QK_DSI, 4, 1, qk.QK_F64, 7, fake, C.c_double(1.0), fake, None),
+        lib.qk_discrepancy(qk.QK_DSI, 4, 1, qk.QK_F64, qk.QK_COL_P, fake, C.c_double(0.0), fake, None),
+    ]
+    assert cases == [qk.QK_EINVAL] * len(cases), cases
+    assert lib.qk_discrepancy_weights(qk.QK_SI, 10, 2, 3, qk.QK_F64, fake, fake, C.c_double(1.0), fake, None,
+                                      C.c_size_t(0), None) == qk.QK_EWORKSPACE
+
+
+def test_workspace_sizes_saturate_instead_of_wrapping(lib_path):
+    """batch 2^30 of 2^30-point lattice columns in FP64 (16-byte complex elements) needs 2^64
+    bytes: the size saturates, so the static-scratch call refuses it and qk_eigs refuses a NULL
+    or small workspace (a wrapped size of 0 would accept it)."""
+    from paper_2502_14256_gb300 import qk
+    lib = qk.LIB
+    fake = C.c_void_p(0x2000000)
+    size = C.c_size_t(0)
+    assert lib.qk_workspace_bytes(0, qk.QK_SI, 30, 1 << 30, 1, qk.QK_F64, 1, C.byref(size)) == qk.QK_OK
+    assert size.value == (1 << 64) - 1
+    assert lib.qk_eigs_static(qk.QK_SI, 30, 1 << 30, qk.QK_F64, 0, fake, C.c_double(1.0), C.c_double(0.0), fake,
+                              None, None) == qk.QK_EINVAL
+    assert lib.qk_eigs(qk.QK_SI, 30, 1 << 30, qk.QK_F64, 0, fake, C.c_double(1.0), C.c_double(0.0), fake, None,
+                       C.c_size_t(0), None, None) == qk.QK_EWORKSPACE
+    assert lib.qk_eigs(qk.QK_SI, 30, 1 << 30, qk.QK_F64, 0, fake, C.c_double(1.0), C.c_double(0.0), fake, fake,
+                       C.c_size_t(1 << 40), None, None) == qk.QK_EWORKSPACE

@@ -81,6 +81,19 @@ def test_kernel_col(qk, kind, family, alpha, m, d):
                 k1, _ = case.k1_ref(r, m)
                 g = got[r - 1] if form == qk.QK_COL_K1 else case.zeta * (1.0 + got[r - 1])
                 assert qc.rel_err(g, k1) < tol, (dt, form, r, qc.rel_err(g, k1))
+    # float-float arithmetic on the FP32 pipes (QK_F32W), written as FP64: about 2^-46 per
+    # factor, so the column agrees with the oracle to ~1e-13 where FP32 gives ~1e-6
+    for form in (qk.QK_COL_K1, qk.QK_COL_P):
+        col = torch.empty((2, n), dtype=F64, device=qc.dev())
+        qk.kernel_col(case.ps, kern, 1, 2, m, col, form=form, wide=True)
+        got = col.cpu().numpy()
+        for r in (1, 2):
+            k1, _ = case.k1_ref(r, m)
+            g = got[r - 1] if form == qk.QK_COL_K1 else case.zeta * (1.0 + got[r - 1])
+            assert qc.rel_err(g, k1) < 2e-13, ("wide", form, r, qc.rel_err(g, k1))
+            if form == qk.QK_COL_P:  # p itself keeps its relative precision
+                p_ref = k1 / case.zeta - 1.0
+                assert qc.rel_err(got[r - 1], p_ref) < 2e-12, ("wide p", r, qc.rel_err(got[r - 1], p_ref))
 
 
 # ---------------------------------------------------------------- spectrum
@@ -112,6 +125,19 @@ def test_eigs(qk, kind, family, alpha, m):
         for r in range(2):
             want, _, _ = _lam_ref(case, r, m, eta)
             assert qc.rel_err(got[r], want) < tol, (dt, r, qc.rel_err(got[r], want))
+            if dt == F64:
+                # element-wise: every eigenvalue, the small ones included, to the rounding floor
+                # of two FP64 transforms of k_1 (the library's and the oracle's)
+                assert qc.lam_elementwise_ok(got[r], want, 1e-10, qc.EPS64, m), qc.lam_elementwise_report(got[r], want)
+    # the float-float column (QK_F32W) then the FP64 transform: the same element-wise bound
+    col = torch.empty((2, 1 << m), dtype=F64, device=qc.dev())
+    qk.kernel_col(case.ps, kern, 0, 2, m, col, form=qk.QK_COL_P, wide=True)
+    lam = torch.empty((2, 1 << m), dtype=F64, device=qc.dev())
+    qk.eigs(fam, m, col, lam, zeta=case.zeta, eta=eta, form=qk.QK_COL_P)
+    got = lam.cpu().numpy()
+    for r in range(2):
+        want, _, _ = _lam_ref(case, r, m, eta)
+        assert qc.lam_elementwise_ok(got[r], want, 1e-10, qc.EPS64 * 4, m), qc.lam_elementwise_report(got[r], want)
 
 
 def test_eigs_reports_non_positive_definite(qk):
@@ -405,7 +431,7 @@ def _abs_dk_sums(family, alpha, X, c, zeta):
 def _batch_outputs(qk, case, m, nrhs, dt, y_h, eta, refine=0):
     kern = qc.kernel_of(case)
     R, n, d = case.R, 1 << m, case.d
-    y = torch.tensor(y_h, dtype=dt, device=qc.dev())
+    y = torch.tensor(y_h, dtype=qk.data_dtype(dt), device=qc.dev())
     c = torch.zeros_like(y)
     lam = torch.zeros((R, n), dtype=F64, device=qc.dev())
     out = torch.zeros((R, nrhs, 5), dtype=F64, device=qc.dev())
@@ -420,18 +446,30 @@ def _batch_outputs(qk, case, m, nrhs, dt, y_h, eta, refine=0):
     return {k: v.cpu().numpy().astype(np.float64) for k, v in dict(c=c, lam=lam, out=out, grad=grad).items()}
 
 
-@pytest.mark.parametrize("dt", [F64, F32])
+def _data(qk, dt):
+    return qk.data_dtype(dt)
+
+
+F32W = "float32w"  # qk.F32W: FP32 arrays, float-float first column
+
+
+@pytest.mark.parametrize("dt", [F64, F32, F32W])
 @pytest.mark.parametrize("m,alpha,order,nrhs", [(13, 2, "gray", 2), (14, 1, "gray", 1), (16, 4, "natural", 3),
-                                                (17, 3, "gray", 2), (20, 2, "gray", 1), (21, 2, "natural", 1)])
+                                                (17, 3, "gray", 2), (20, 2, "gray", 1), (21, 2, "natural", 1),
+                                                (22, 2, "gray", 1)])
 def test_fused_schedule_matches_oracle(qk, dt, m, alpha, order, nrhs):
-    """The batched schedule (fused three-phase kernels where the size allows) against
-    the oracle's spectral formulas: lambda, solve, quadratic form, log det, MLL,
-    posterior mean/variance and gradients, per randomization and right-hand side."""
+    """The batched schedule (fused three-phase kernels where the size allows, the standalone
+    ops beyond) against the oracle's spectral formulas: lambda, solve, quadratic form, log
+    det, MLL, posterior mean/variance and gradients, per randomization and right-hand side.
+    FP64 at nugget 1e-6; the FP32 precisions with one refinement step: QK_F32W (float-float
+    first column) at the workloads' nugget 1e-8 with 1e-5 tolerances; QK_F32 (FP32 column)
+    at nugget 1e-3, above the eps32 ||p||_2 perturbation an FP32 column gives every eigenvalue."""
     if dt == F64 and m > 20:
         pytest.skip("FP64 fused sizes end at 2^20; larger runs the standalone path, covered elsewhere")
-    # FP32 eigenvalues carry absolute errors ~ eps32 ||p||_2; the FP32 checks use a nugget
-    # that keeps the spectrum above that (FP64 uses 1e-6)
-    d, R, eta = 5, 2, (1e-6 if dt == F64 else 1e-3)
+    if dt == F32 and m > 21:
+        pytest.skip("m = 22 runs the standalone ops; covered for FP32 by the solve and MLL tests")
+    d, R = 5, 2
+    eta = {F64: 1e-6, F32: 1e-3, F32W: 1e-8}[dt]
     gamma = 0.8 ** np.arange(1, d + 1)
     case = qc.make_case("net", "dsi", alpha, d, R, seed=2000 + m, c=gamma, zeta=1.2, order=order)
     n = 1 << m
@@ -444,18 +482,27 @@ def test_fused_schedule_matches_oracle(qk, dt, m, alpha, order, nrhs):
         for q in range(nrhs):
             y_h[r, q] = np.cos((q + 1) * X[:, 0] / 2 ** 31) + 0.01 * rng.standard_normal(n)
         refs.append((X, lam_ref))
-    got = _batch_outputs(qk, case, m, nrhs, dt, y_h, eta)
-    tol = dict(lam=1e-12, c=1e-10, quad=1e-11, logdet=1e-12, mll=1e-11, mean=1e-10, var=1e-10, grad=1e-9) \
-        if dt == F64 else dict(lam=2e-6, c=2e-4, quad=2e-5, logdet=1e-5, mll=1e-5, mean=2e-4, var=1e-5, grad=2e-4)
+    got = _batch_outputs(qk, case, m, nrhs, dt, y_h, eta, refine=0 if dt == F64 else 1)
+    if dt == F64:
+        tol = dict(lam=1e-12, c=1e-10, quad=1e-11, logdet=1e-12, mll=1e-11, mean=1e-10, var=1e-10, grad=1e-9)
+    else:
+        # QK_F32 (FP32 column): its eigenvalues carry ~eps32 ||p||_2 absolute, which the
+        # 1/lambda-weighted quadratic form feels at the 1e-5 level (order 4 at 2^16: 1.8e-5)
+        tol = dict(lam=2e-6, c=1e-5, quad=1e-5 if dt == F32W else 3e-5, logdet=1e-5, mll=1e-5, mean=1e-5, var=1e-5,
+                   grad=1e-4)
     for r in range(R):
         X, lam_ref = refs[r]
         assert qc.rel_err(got["lam"][r], lam_ref) < tol["lam"], (r, qc.rel_err(got["lam"][r], lam_ref))
+        if dt == F32W:  # every eigenvalue to FP32 relative precision, down to the nugget
+            el = np.abs(got["lam"][r] - lam_ref) / lam_ref
+            assert el.max() < 1e-5, (r, float(el.max()), float(lam_ref.min()))
         for q in range(nrhs):
             y = y_h[r, q]
             c_ref = o.spectral_solve("dsi", lam_ref, y)
             sp = o.spectral_mll("dsi", lam_ref, y, case.zeta)
             gr = o.spectral_mll_grad("dsi", alpha, X, y, lam_ref, case.c, case.zeta)
-            ctol = max(tol["c"], 20 * float(lam_ref.max() / lam_ref.min()) * (qc.EPS64 if dt == F64 else qc.EPS32))
+            cond = float(lam_ref.max() / lam_ref.min())
+            ctol = max(tol["c"], 20 * cond * qc.EPS64) if dt != F32 else max(tol["c"], 20 * cond * qc.EPS32)
             assert qc.rel_err(got["c"][r, q], c_ref) < ctol, (r, q, qc.rel_err(got["c"][r, q], c_ref))
             o_ = got["out"][r, q]
             assert abs(o_[0] - sp["quad"]) < tol["quad"] * abs(sp["quad"])

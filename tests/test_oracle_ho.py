@@ -99,3 +99,27 @@ def test_higher_order_gram_is_rsbt_and_diagonalised_by_the_hadamard_transform(al
     lam = o.hadamard_apply(o.ho_first_column(alpha_k, X, c, 1.0))
     assert np.allclose(np.sort(lam), np.linalg.eigvalsh(K), rtol=1e-12, atol=1e-12 * lam.max())
     assert lam.min() > 0
+
+
+def test_higher_order_dense_gradient_matches_central_differences():
+    """The dense MLL gradient on an interlaced net against central differences (h = 1e-6) of
+    the dense MLL in each weight and in the nugget."""
+    d, m, alpha_k, eta = 2, 5, 4, 1e-3
+    n = 1 << m
+    net = inputs.make_ho_net(77, d, 2, 1, "gray")
+    X = o.ho_net_points(o.interlace(o.lms_scramble(net.C, net.S)[0], 2), net.D[0], np.arange(n), m, "gray")
+    x = X.astype(np.float64) / 2.0 ** 64
+    y = np.prod(1.0 + (x - 0.5) / np.arange(1, d + 1) ** 2, axis=1)
+    c = np.array([0.9, 0.4])
+    g = o.ho_mll_grad_dense(alpha_k, X, y, c, eta, 1.0)
+    h = 1e-6
+    for j in range(d):
+        cp, cm = c.copy(), c.copy()
+        cp[j] += h
+        cm[j] -= h
+        fd = (o.mll_dense(o.ho_gram_dense(alpha_k, X, cp, 1.0, eta), y)[0]
+              - o.mll_dense(o.ho_gram_dense(alpha_k, X, cm, 1.0, eta), y)[0]) / (2 * h)
+        assert abs(fd - g["dc"][j]) < 1e-6 * max(1.0, abs(fd)), (j, fd, g["dc"][j])
+    fd = (o.mll_dense(o.ho_gram_dense(alpha_k, X, c, 1.0, eta + h), y)[0]
+          - o.mll_dense(o.ho_gram_dense(alpha_k, X, c, 1.0, eta - h), y)[0]) / (2 * h)
+    assert abs(fd - g["deta"]) < 1e-5 * max(1.0, abs(fd))
