@@ -418,7 +418,9 @@ __device__ __forceinline__ void reg_stages2(T (&vh)[FCfg<T>::L], T (&vl)[FCfg<T>
   }
 }
 
-// Compensated (hi, lo) versions of xwht_full / xwht_col; sml: a second padded tile.
+// Compensated (hi, lo) versions of xwht_full / xwht_col; sml: the padded tile for the lo
+// parts (may be sm itself: each transpose ends with a barrier, so the lo parts then pass
+// through the same tile after the hi parts).
 template <typename T>
 __device__ __forceinline__ void xwht_full2(T (&vh)[FCfg<T>::L], T (&vl)[FCfg<T>::L], T *sm, T *sml, int dir) {
   constexpr int LOGL = Lay<T>::LOGL, LOGT = Lay<T>::LOGT;
@@ -464,9 +466,8 @@ __device__ __forceinline__ void fused_A_item(const FTask &ft, uint32_t r, uint32
   carve_tables<L>(smem, d, &wd, tb);
   T *wT = reinterpret_cast<T *>(wd);
   T *sm = reinterpret_cast<T *>(smem + align256(col_smem_bytes<L>(d)));
-  T *sml = reinterpret_cast<T *>(smem + align256(col_smem_bytes<L>(d)) + xtile_bytes<T>());
-  double *red = reinterpret_cast<double *>(smem + align256(col_smem_bytes<L>(d)) +
-                                           (COMP ? 2 : 1) * xtile_bytes<T>());
+  T *sml = sm;  // the compensated transforms pass the lo parts through the same tile
+  double *red = reinterpret_cast<double *>(smem + align256(col_smem_bytes<L>(d)) + xtile_bytes<T>());
   const uint64_t n = 1ull << job.m, base = (uint64_t)tile << LOGT;
   const int t = threadIdx.x;
   if constexpr (WIDE) {
@@ -542,7 +543,7 @@ __device__ __forceinline__ void fused_A_item(const FTask &ft, uint32_t r, uint32
 }
 
 template <typename T, int FAM, int ALPHA, bool COMP, bool WIDE>
-__global__ void __launch_bounds__(kFNT) k_fused_A(FTask ft) {
+__global__ void __launch_bounds__(kFNT, WIDE ? 1 : 3) k_fused_A(FTask ft) {
   extern __shared__ __align__(16) unsigned char smem[];
   fused_A_item<T, FAM, ALPHA, COMP, WIDE>(ft, blockIdx.y, blockIdx.x, smem);
 }
@@ -939,7 +940,7 @@ int launch_fused_t(const FTask &ft, cudaStream_t st, LaunchTimer *tm) {
   const uint32_t R = ft.job.nr, d = ft.job.d;
   const size_t colb = align256(col_smem_bytes<L>(d));
   // phase A keeps a second tile for the lo parts when compensating
-  const size_t smA = colb + (COMP ? 2 : 1) * xtile_bytes<T>() + 32 * sizeof(double);
+  const size_t smA = colb + xtile_bytes<T>() + 32 * sizeof(double);
   const size_t smB = 3 * xtile_bytes<T>() + 32 * sizeof(double);
   const size_t smC = colb + xtile_bytes<T>() + (size_t)(kFNT / 32) * 2 * d * sizeof(double);
   smem_optin<k_fused_A<T, FAM, ALPHA, COMP, WIDE>>(smA);
@@ -981,7 +982,7 @@ template <typename T, int FAM, int ALPHA, bool COMP, bool WIDE = false>
 int persist_launch_t(const PSched &ps, uint32_t dmax, cudaStream_t st) {
   constexpr int L = FCfg<T>::L;
   const size_t colb = align256(col_smem_bytes<L>(dmax));
-  const size_t smA = colb + (COMP ? 2 : 1) * xtile_bytes<T>() + 32 * sizeof(double);
+  const size_t smA = colb + xtile_bytes<T>() + 32 * sizeof(double);
   const size_t smB = 3 * xtile_bytes<T>() + 32 * sizeof(double);
   const size_t smC = colb + xtile_bytes<T>() + (size_t)(kFNT / 32) * 2 * dmax * sizeof(double);
   size_t sm = smA > smB ? smA : smB;

@@ -70,83 +70,109 @@ static uint32_t gen_lognp(uint32_t d) {
 template <bool NET>
 __global__ void __launch_bounds__(kGenNT) k_points_tiled(uint32_t d, int order, const uint32_t *__restrict__ Ct,
                                                          const uint32_t *__restrict__ g, const uint32_t *__restrict__ D,
-                                                         uint32_t r0, uint64_t i0, uint64_t n, uint32_t lognp,
-                                                         uint32_t *__restrict__ X) {
-  extern __shared__ uint32_t gsm[];
+                                                         uint32_t r0, uint32_t nr, uint64_t i0, uint64_t n,
+                                                         uint32_t lognp, uint32_t tiles, uint32_t *__restrict__ X) {
+  extern __shared__ __align__(16) uint32_t gsm[];
   const uint32_t NP = 1u << lognp, runs = (NP / kGenRL) * d;
   uint32_t *tile = gsm;             // NP x d
   uint32_t *sC = tile + NP * d;     // nets: d x 32 columns; lattices: g
   uint32_t *zrun = sC + 32 * d;     // nets: (NP / RL) x d run words
-  uint32_t *ztile = zrun + runs;    // nets: d tile words (shift included)
-  const uint32_t rl = blockIdx.y, r = r0 + rl;
-  const uint64_t base = ((i0 >> lognp) + blockIdx.x) << lognp;  // < 2^32 (i0 + n <= 2^32)
+  uint32_t *ztile = zrun + runs;    // d tile words (shift included)
   const int t = threadIdx.x;
-  if constexpr (NET) {
-    for (uint32_t q = t; q < 32 * d; q += kGenNT) sC[q] = Ct[(size_t)r * d * 32 + q];
+  // work items (randomization, tile) in order; each CTA takes one contiguous chunk, so the
+  // per-randomization set-up (columns, run words) is redone only where the chunk crosses
+  // into the next randomization
+  const uint64_t total = (uint64_t)nr * tiles, chunk = (total + gridDim.x - 1) / gridDim.x;
+  const uint64_t it0 = (uint64_t)blockIdx.x * chunk, it1 = it0 + chunk < total ? it0 + chunk : total;
+  uint32_t cur = 0xFFFFFFFFu;
+  for (uint64_t it = it0; it < it1; ++it) {
+    const uint32_t rl = (uint32_t)(it / tiles), tt = (uint32_t)(it - (uint64_t)rl * tiles), r = r0 + rl;
+    if (rl != cur) {  // the previous item's run phase ended at a barrier: sC / zrun are free
+      cur = rl;
+      if constexpr (NET) {
+        for (uint32_t q = t; q < 32 * d; q += kGenNT) sC[q] = Ct[(size_t)r * d * 32 + q];
+        __syncthreads();
+        for (uint32_t w = t; w < runs; w += kGenNT) {
+          const uint32_t q = w / d, j = w - q * d;
+          zrun[w] = xor_columns(sC + j * 32, order_map(order, q * kGenRL));
+        }
+      } else {
+        for (uint32_t j = t; j < d; j += kGenNT) sC[j] = g[j];
+      }
+    }
+    const uint64_t base = ((i0 >> lognp) + tt) << lognp;  // < 2^32 (i0 + n <= 2^32)
+    for (uint32_t j = t; j < d; j += kGenNT) {
+      const uint32_t dj = D ? D[(size_t)r * d + j] : 0u;
+      if constexpr (NET) ztile[j] = xor_columns(sC + j * 32, order_map(order, (uint32_t)base)) ^ dj;
+      else ztile[j] = dj;
+    }
+    // also separates the previous item's copy-out (reads of the tile) from this item's writes
     __syncthreads();
     for (uint32_t w = t; w < runs; w += kGenNT) {
       const uint32_t q = w / d, j = w - q * d;
-      zrun[w] = xor_columns(sC + j * 32, order_map(order, q * kGenRL));
-    }
-    for (uint32_t j = t; j < d; j += kGenNT)
-      ztile[j] = xor_columns(sC + j * 32, order_map(order, (uint32_t)base)) ^ (D ? D[(size_t)r * d + j] : 0u);
-  } else {
-    for (uint32_t j = t; j < d; j += kGenNT) sC[j] = g[j];
-    for (uint32_t j = t; j < d; j += kGenNT) ztile[j] = D ? D[(size_t)r * d + j] : 0u;
-  }
-  __syncthreads();
-  for (uint32_t w = t; w < runs; w += kGenNT) {
-    const uint32_t q = w / d, j = w - q * d;
-    uint32_t *dst = tile + q * kGenRL * d + j;
-    if constexpr (NET) {
-      const uint32_t *cj = sC + j * 32;
-      const uint32_t c0 = cj[0], c1 = cj[1], c2 = cj[2];
-      // step k -> k + 1 flips digit ctz(k + 1) of the Gray index, digits 0 .. ctz(k + 1) of i
-      const uint32_t s0 = c0, s1 = order == QK_GRAY ? c1 : (c0 ^ c1), s2 = order == QK_GRAY ? c2 : (c0 ^ c1 ^ c2);
-      uint32_t x = ztile[j] ^ zrun[w];
-      dst[0] = x;
-      x ^= s0, dst[1 * d] = x;
-      x ^= s1, dst[2 * d] = x;
-      x ^= s0, dst[3 * d] = x;
-      x ^= s2, dst[4 * d] = x;
-      x ^= s0, dst[5 * d] = x;
-      x ^= s1, dst[6 * d] = x;
-      x ^= s0, dst[7 * d] = x;
-    } else {
-      const uint32_t gj = sC[j], dj = ztile[j];
-      const uint32_t i = (uint32_t)base + q * kGenRL;
+      uint32_t *dst = tile + q * kGenRL * d + j;
+      if constexpr (NET) {
+        const uint32_t *cj = sC + j * 32;
+        const uint32_t c0 = cj[0], c1 = cj[1], c2 = cj[2];
+        // step k -> k + 1 flips digit ctz(k + 1) of the Gray index, digits 0 .. ctz(k + 1) of i
+        const uint32_t s0 = c0, s1 = order == QK_GRAY ? c1 : (c0 ^ c1), s2 = order == QK_GRAY ? c2 : (c0 ^ c1 ^ c2);
+        uint32_t x = ztile[j] ^ zrun[w];
+        dst[0] = x;
+        x ^= s0, dst[1 * d] = x;
+        x ^= s1, dst[2 * d] = x;
+        x ^= s0, dst[3 * d] = x;
+        x ^= s2, dst[4 * d] = x;
+        x ^= s0, dst[5 * d] = x;
+        x ^= s1, dst[6 * d] = x;
+        x ^= s0, dst[7 * d] = x;
+      } else {
+        const uint32_t gj = sC[j], dj = ztile[j];
+        const uint32_t i = (uint32_t)base + q * kGenRL;
 #pragma unroll
-      for (int k = 0; k < kGenRL; ++k) dst[k * d] = __brev(i + k) * gj + dj;
+        for (int k = 0; k < kGenRL; ++k) dst[k * d] = __brev(i + k) * gj + dj;
+      }
+    }
+    __syncthreads();
+    const uint64_t lo = base > i0 ? base : i0, hi = (base + NP) < (i0 + n) ? (base + NP) : (i0 + n);
+    const uint64_t words = (hi - lo) * d, soff = (lo - base) * d;
+    const uint32_t *src = tile + soff;
+    uint32_t *out = X + ((uint64_t)rl * n + (lo - i0)) * d;
+    if ((((uintptr_t)out | (uintptr_t)src) & 15u) == 0 && (words & 3u) == 0) {  // 16-byte rows
+      const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+      uint4 *o4 = reinterpret_cast<uint4 *>(out);
+      for (uint64_t e = t; e < (words >> 2); e += kGenNT) o4[e] = s4[e];
+    } else {
+      for (uint64_t e = t; e < words; e += kGenNT) out[e] = src[e];
     }
   }
-  __syncthreads();
-  const uint64_t lo = base > i0 ? base : i0, hi = (base + NP) < (i0 + n) ? (base + NP) : (i0 + n);
-  const uint64_t words = (hi - lo) * d;
-  const uint32_t *src = tile + (lo - base) * d;
-  uint32_t *out = X + ((uint64_t)rl * n + (lo - i0)) * d;
-  for (uint64_t e = t; e < words; e += kGenNT) out[e] = src[e];
 }
 
 int launch_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64_t i0, uint64_t n,
                       uint32_t *X, cudaStream_t st) {
   if (n == 0 || nr == 0) return QK_OK;
   const uint32_t d = ps->d, lognp = gen_lognp(d), NP = 1u << lognp;
-  const uint64_t tiles = ((i0 + n - 1) >> lognp) - (i0 >> lognp) + 1;
+  const uint64_t tiles = ((i0 + n - 1) >> lognp) - (i0 >> lognp) + 1;  // <= 2^29
   const size_t smem = sizeof(uint32_t) * ((size_t)NP * d + 32 * d + (NP / kGenRL) * d + d);
-  if (ps->kind == QK_NET_B2) smem_optin<k_points_tiled<true>>(smem);
-  else smem_optin<k_points_tiled<false>>(smem);
-  for (uint32_t rc = 0; rc < nr; rc += 65535) {  // grid.y limit
-    const uint32_t cnt = nr - rc < 65535 ? nr - rc : 65535;
-    dim3 grid((unsigned)tiles, cnt);
-    uint32_t *Xc = X + (size_t)rc * n * d;
-    if (ps->kind == QK_NET_B2)
-      k_points_tiled<true><<<grid, kGenNT, smem, st>>>(d, ps->order, ps->Ct, nullptr, ps->D, r0 + rc, i0, n, lognp, Xc);
-    else
-      k_points_tiled<false><<<grid, kGenNT, smem, st>>>(d, ps->order, nullptr, ps->g, ps->D, r0 + rc, i0, n, lognp, Xc);
-    int rc_ = check_launch("qk_gen_points");
-    if (rc_) return rc_;
+  int occ = 0;
+  if (ps->kind == QK_NET_B2) {
+    smem_optin<k_points_tiled<true>>(smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_points_tiled<true>, kGenNT, smem);
+  } else {
+    smem_optin<k_points_tiled<false>>(smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_points_tiled<false>, kGenNT, smem);
   }
-  return QK_OK;
+  if (occ < 1) occ = 1;
+  // one wave of resident CTAs, each taking an equal contiguous chunk of the (r, tile) items
+  const uint64_t total = (uint64_t)nr * tiles;
+  uint64_t grid = (uint64_t)sm_count() * occ;
+  if (grid > total) grid = total;
+  if (ps->kind == QK_NET_B2)
+    k_points_tiled<true><<<(unsigned)grid, kGenNT, smem, st>>>(d, ps->order, ps->Ct, nullptr, ps->D, r0, nr, i0, n,
+                                                               lognp, (uint32_t)tiles, X);
+  else
+    k_points_tiled<false><<<(unsigned)grid, kGenNT, smem, st>>>(d, ps->order, nullptr, ps->g, ps->D, r0, nr, i0, n,
+                                                                lognp, (uint32_t)tiles, X);
+  return check_launch("qk_gen_points");
 }
 
 template <typename T, int FAM, int ALPHA>
