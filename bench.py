@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--refine", type=int, default=1, help="refinement steps of the FP32 solve")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison timing")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--e2e-chunk", type=int, default=8, help="randomizations per host-copy chunk (e2e)")
+    ap.add_argument("--e2e-chunk", type=int, default=16, help="randomizations per host-copy chunk (e2e)")
     ap.add_argument("--sched", default="auto", choices=["auto", "launches", "persistent"],
                     help="batched schedule: tuned (auto), per-phase launches or one persistent launch")
     ap.add_argument("--lag", type=int, default=1, help="persistent schedule: units between phases")

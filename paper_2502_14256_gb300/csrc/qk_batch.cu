@@ -245,6 +245,30 @@ struct HostRunner {
 static std::mutex g_host_mu;
 static std::unordered_map<int, HostRunner> g_host_runners;
 
+// Chunk sizes (randomizations) for R randomizations with chunks of at most chunk_r: ramps of
+// chunk_r/4, chunk_r/2, ... at both ends (computing starts after a short first copy in, and
+// the last copy back is short), chunk_r in between; uniform chunks when R is too small.
+static std::vector<uint32_t> host_chunks(uint32_t R, uint32_t chunk_r) {
+  std::vector<uint32_t> ramp;
+  for (uint32_t c = chunk_r >> 2; c && c < chunk_r; c <<= 1) ramp.push_back(c);
+  uint64_t ramps = 0;
+  for (uint32_t c : ramp) ramps += 2ull * c;
+  std::vector<uint32_t> out;
+  if (ramp.empty() || R < ramps + chunk_r) {
+    for (uint32_t r0 = 0; r0 < R; r0 += chunk_r) out.push_back(R - r0 < chunk_r ? R - r0 : chunk_r);
+    return out;
+  }
+  out = ramp;
+  uint32_t mid = R - (uint32_t)ramps;
+  while (mid) {
+    const uint32_t c = mid < chunk_r ? mid : chunk_r;
+    out.push_back(c);
+    mid -= c;
+  }
+  for (auto it = ramp.rbegin(); it != ramp.rend(); ++it) out.push_back(*it);
+  return out;
+}
+
 }  // namespace qk
 
 using namespace qk;
@@ -388,12 +412,14 @@ int qk_batch_run_host(void *ws, size_t ws_bytes, const qk_host_io *io, uint32_t 
   if (chunk_r == 0) return fail(QK_EINVAL, "qk_batch_run_host: chunk_r must be >= 1");
   const size_t elem = p.dtype == QK_F64 ? 8 : 4;
   size_t nchunks = 0;
+  std::vector<std::vector<uint32_t>> chunks(p.tasks.size());
   for (size_t i = 0; i < p.tasks.size(); ++i) {
     const qk_task &t = p.tasks[i];
     if (!io[i].y || !io[i].out) return fail(QK_EINVAL, "task %zu: host y and out are required", i);
     if ((io[i].c && !t.c) || (io[i].lam && !t.lam) || (io[i].grad && !t.grad))
       return fail(QK_EINVAL, "task %zu: a host output whose device buffer was not planned", i);
-    nchunks += (t.ps.R + chunk_r - 1) / chunk_r;
+    chunks[i] = host_chunks(t.ps.R, chunk_r);
+    nchunks += chunks[i].size();
   }
   int dev = 0;
   cudaGetDevice(&dev);
@@ -417,8 +443,8 @@ int qk_batch_run_host(void *ws, size_t ws_bytes, const qk_host_io *io, uint32_t 
   for (size_t i = 0; i < p.tasks.size(); ++i) {
     const qk_task &t = p.tasks[i];
     const uint64_t n = 1ull << t.m, d = t.ps.d;
-    for (uint32_t r0 = 0; r0 < t.ps.R; r0 += chunk_r, ++k) {
-      const uint32_t nr = t.ps.R - r0 < chunk_r ? t.ps.R - r0 : chunk_r;
+    uint32_t r0 = 0;
+    for (const uint32_t nr : chunks[i]) {
       const qk_task s = sub_task(t, r0, nr, elem);
       const size_t ybytes = elem * nr * t.nrhs * n, yoff = elem * (size_t)r0 * t.nrhs * n;
       // host -> device: this chunk's right-hand sides
@@ -442,6 +468,8 @@ int qk_batch_run_host(void *ws, size_t ws_bytes, const qk_host_io *io, uint32_t 
       if (io[i].grad && (rc = cp(io[i].grad + (size_t)r0 * t.nrhs * (2 * d + 2), s.grad,
                                  8 * nr * t.nrhs * (2 * d + 2), cudaMemcpyDeviceToHost, hr.out)))
         return rc;
+      r0 += nr;
+      ++k;
     }
   }
   // the caller's stream completes only after the last copy back

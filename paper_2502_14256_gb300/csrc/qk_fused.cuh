@@ -324,10 +324,81 @@ __device__ __forceinline__ void xpose(T (&v)[FCfg<T>::L], T *sm, int from, int t
   __syncthreads();
 }
 
+// ------------------------------------- FP32 full-tile transposes through a warp-major tile
+// An FP32 tile (8192 elements, 256 threads x 32) exchanges the lane bits of layout L0 with
+// its register bits inside each warp (a per-warp region of the tile, __syncwarp), and only
+// the warp bits across the CTA (__syncthreads): two CTA barriers per full-tile transform
+// instead of four.  Element e sits at ((e >> 5) & 7) 1152 + (e >> 8) 36 + (e & 31): region =
+// warp bits (5-7), row = bits 8-12, column = lane bits, rows padded to 36 words so that
+// 128-bit row accesses of 8 lanes hit distinct banks.  Layout L1w: thread (lane, w) holds
+// e = l + 32 w + 256 lane in register l (bits 0-4), i.e. row `lane` of region w.  Every
+// function ends with its reads complete in all warps where a later write could reach them.
+constexpr int kWReg = 1152, kWRow = 36;
+
+__device__ __forceinline__ void xw_L0_to_L1w(float (&v)[32], float *sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float *rg = sm + w * kWReg;
+#pragma unroll
+  for (int l = 0; l < 32; ++l) rg[l * kWRow + lane] = v[l];  // e = lane + 32 w + 256 l
+  __syncwarp();
+#pragma unroll
+  for (int l = 0; l < 32; l += 4)
+    *reinterpret_cast<float4 *>(&v[l]) = *reinterpret_cast<const float4 *>(rg + lane * kWRow + l);
+}
+
+__device__ __forceinline__ void xw_L1w_to_L2(float (&v)[32], float *sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float *row = sm + w * kWReg + lane * kWRow;
+#pragma unroll
+  for (int l = 0; l < 32; l += 4) *reinterpret_cast<float4 *>(row + l) = *reinterpret_cast<const float4 *>(&v[l]);
+  __syncthreads();
+#pragma unroll
+  for (int l = 0; l < 32; ++l) v[l] = sm[(l & 7) * kWReg + ((l >> 3) + 4 * w) * kWRow + lane];  // e = lane + 32 l + 1024 w
+  __syncthreads();
+}
+
+__device__ __forceinline__ void xw_L2_to_L1w(float (&v)[32], float *sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int l = 0; l < 32; ++l) sm[(l & 7) * kWReg + ((l >> 3) + 4 * w) * kWRow + lane] = v[l];
+  __syncthreads();
+  const float *row = sm + w * kWReg + lane * kWRow;
+#pragma unroll
+  for (int l = 0; l < 32; l += 4) *reinterpret_cast<float4 *>(&v[l]) = *reinterpret_cast<const float4 *>(row + l);
+}
+
+__device__ __forceinline__ void xw_L1w_to_L0(float (&v)[32], float *sm) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float *rg = sm + w * kWReg;
+#pragma unroll
+  for (int l = 0; l < 32; l += 4)
+    *reinterpret_cast<float4 *>(rg + lane * kWRow + l) = *reinterpret_cast<const float4 *>(&v[l]);
+  __syncwarp();
+#pragma unroll
+  for (int l = 0; l < 32; ++l) v[l] = rg[l * kWRow + lane];
+  __syncthreads();
+}
+
 // Full tile WHT (bits [0, LOGT)): from L0 to L2 (dir 0) or from L2 to L0 (dir 1).
 template <typename T>
 __device__ __forceinline__ void xwht_full(T (&v)[FCfg<T>::L], T *sm, int dir) {
   constexpr int LOGL = Lay<T>::LOGL, LOGT = Lay<T>::LOGT;
+  if constexpr (sizeof(T) == 4) {  // warp-major tile: the same butterflies in the same order
+    if (dir == 0) {
+      reg_stages<T>(v, 8, 8, LOGT);
+      xw_L0_to_L1w(v, sm);
+      reg_stages<T>(v, 0, 0, LOGL);
+      xw_L1w_to_L2(v, sm);
+      reg_stages<T>(v, LOGL, LOGL, 8);
+    } else {
+      reg_stages<T>(v, LOGL, LOGL, 8);
+      xw_L2_to_L1w(v, sm);
+      reg_stages<T>(v, 0, 0, LOGL);
+      xw_L1w_to_L0(v, sm);
+      reg_stages<T>(v, 8, 8, LOGT);
+    }
+    return;
+  }
   if (dir == 0) {
     reg_stages<T>(v, 8, 8, LOGT);
     xpose<T>(v, sm, 0, 1);
@@ -424,6 +495,30 @@ __device__ __forceinline__ void reg_stages2(T (&vh)[FCfg<T>::L], T (&vl)[FCfg<T>
 template <typename T>
 __device__ __forceinline__ void xwht_full2(T (&vh)[FCfg<T>::L], T (&vl)[FCfg<T>::L], T *sm, T *sml, int dir) {
   constexpr int LOGL = Lay<T>::LOGL, LOGT = Lay<T>::LOGT;
+  if constexpr (sizeof(T) == 4) {  // warp-major tile (sm); the hi then the lo parts pass through it
+    (void)sml;
+    if (dir == 0) {
+      reg_stages2<T>(vh, vl, 8, 8, LOGT);
+      xw_L0_to_L1w(vh, sm);
+      __syncwarp();  // every lane has read its hi row before the lo parts overwrite the region
+      xw_L0_to_L1w(vl, sm);
+      reg_stages2<T>(vh, vl, 0, 0, LOGL);
+      xw_L1w_to_L2(vh, sm);
+      xw_L1w_to_L2(vl, sm);
+      reg_stages2<T>(vh, vl, LOGL, LOGL, 8);
+    } else {
+      reg_stages2<T>(vh, vl, LOGL, LOGL, 8);
+      xw_L2_to_L1w(vh, sm);
+      __syncthreads();  // every warp has read its hi rows before the lo parts fill the tile
+      xw_L2_to_L1w(vl, sm);
+      reg_stages2<T>(vh, vl, 0, 0, LOGL);
+      __syncthreads();
+      xw_L1w_to_L0(vh, sm);
+      xw_L1w_to_L0(vl, sm);
+      reg_stages2<T>(vh, vl, 8, 8, LOGT);
+    }
+    return;
+  }
   const int a = dir == 0 ? 0 : 2, b = dir == 0 ? 2 : 0;
   const int a0 = dir == 0 ? 8 : LOGL, a1 = dir == 0 ? LOGT : 8, b0 = dir == 0 ? LOGL : 8, b1 = dir == 0 ? 8 : LOGT;
   reg_stages2<T>(vh, vl, a0, a0, a1);

@@ -71,11 +71,14 @@ template <bool NET>
 __global__ void __launch_bounds__(kGenNT) k_points_tiled(uint32_t d, int order, const uint32_t *__restrict__ Ct,
                                                          const uint32_t *__restrict__ g, const uint32_t *__restrict__ D,
                                                          uint32_t r0, uint32_t nr, uint64_t i0, uint64_t n,
-                                                         uint32_t lognp, uint32_t tiles, uint32_t *__restrict__ X) {
+                                                         uint32_t lognp, uint32_t tiles, int direct,
+                                                         uint32_t *__restrict__ X) {
   extern __shared__ __align__(16) uint32_t gsm[];
   const uint32_t NP = 1u << lognp, runs = (NP / kGenRL) * d;
-  uint32_t *tile = gsm;             // NP x d
-  uint32_t *sC = tile + NP * d;     // nets: d x 32 columns; lattices: g
+  // direct: rows of d >= 16 words are written from registers (a warp's store covers whole
+  // 64-byte row pieces); otherwise the tile is staged in shared memory first
+  uint32_t *tile = gsm;             // NP x d (staged form only)
+  uint32_t *sC = tile + (direct ? 0 : NP * d);  // nets: d x 32 columns; lattices: g
   uint32_t *zrun = sC + 32 * d;     // nets: (NP / RL) x d run words
   uint32_t *ztile = zrun + runs;    // d tile words (shift included)
   const int t = threadIdx.x;
@@ -101,15 +104,43 @@ __global__ void __launch_bounds__(kGenNT) k_points_tiled(uint32_t d, int order, 
       }
     }
     const uint64_t base = ((i0 >> lognp) + tt) << lognp;  // < 2^32 (i0 + n <= 2^32)
-    for (uint32_t j = t; j < d; j += kGenNT) {
-      const uint32_t dj = D ? D[(size_t)r * d + j] : 0u;
-      if constexpr (NET) ztile[j] = xor_columns(sC + j * 32, order_map(order, (uint32_t)base)) ^ dj;
-      else ztile[j] = dj;
+    if constexpr (NET) {
+      // the tile word of dimension j: one warp XOR-reduces the columns selected by the
+      // digits of h(base), lane k holding column k
+      const uint32_t hb = order_map(order, (uint32_t)base), lane = t & 31;
+      for (uint32_t j = t >> 5; j < d; j += kGenNT / 32) {
+        const uint32_t v = __reduce_xor_sync(0xffffffffu, ((hb >> lane) & 1u) ? sC[j * 32 + lane] : 0u);
+        if (lane == 0) ztile[j] = v ^ (D ? D[(size_t)r * d + j] : 0u);
+      }
+    } else {
+      for (uint32_t j = t; j < d; j += kGenNT) ztile[j] = D ? D[(size_t)r * d + j] : 0u;
     }
     // also separates the previous item's copy-out (reads of the tile) from this item's writes
     __syncthreads();
-    for (uint32_t w = t; w < runs; w += kGenNT) {
-      const uint32_t q = w / d, j = w - q * d;
+    // run (q, j): points q RL .. q RL + 7 of the tile in dimension j
+    const uint64_t lo = base > i0 ? base : i0, hi = (base + NP) < (i0 + n) ? (base + NP) : (i0 + n);
+    auto run = [&](uint32_t q, uint32_t j, uint32_t w) {
+      if (direct) {  // straight to the output rows, positions inside [i0, i0 + n) only
+        const uint64_t p0 = base + (uint64_t)q * kGenRL;
+        uint32_t *dst = X + ((uint64_t)rl * n) * d + j;
+        uint32_t xs[kGenRL];
+        if constexpr (NET) {
+          const uint32_t *cj = sC + j * 32;
+          const uint32_t c0 = cj[0], c1 = cj[1], c2 = cj[2];
+          const uint32_t s0 = c0, s1 = order == QK_GRAY ? c1 : (c0 ^ c1), s2 = order == QK_GRAY ? c2 : (c0 ^ c1 ^ c2);
+          xs[0] = ztile[j] ^ zrun[w];
+          xs[1] = xs[0] ^ s0, xs[2] = xs[1] ^ s1, xs[3] = xs[2] ^ s0, xs[4] = xs[3] ^ s2;
+          xs[5] = xs[4] ^ s0, xs[6] = xs[5] ^ s1, xs[7] = xs[6] ^ s0;
+        } else {
+          const uint32_t gj = sC[j], dj = ztile[j];
+#pragma unroll
+          for (int k = 0; k < kGenRL; ++k) xs[k] = __brev((uint32_t)p0 + k) * gj + dj;
+        }
+#pragma unroll
+        for (int k = 0; k < kGenRL; ++k)
+          if (p0 + k >= lo && p0 + k < hi) dst[(p0 + k - i0) * d] = xs[k];
+        return;
+      }
       uint32_t *dst = tile + q * kGenRL * d + j;
       if constexpr (NET) {
         const uint32_t *cj = sC + j * 32;
@@ -131,9 +162,18 @@ __global__ void __launch_bounds__(kGenNT) k_points_tiled(uint32_t d, int order, 
 #pragma unroll
         for (int k = 0; k < kGenRL; ++k) dst[k * d] = __brev(i + k) * gj + dj;
       }
+    };
+    if (kGenNT % d == 0) {  // a thread keeps its dimension and steps through the runs
+      const uint32_t j = (uint32_t)t % d;
+      for (uint32_t q = (uint32_t)t / d; q < NP / kGenRL; q += kGenNT / d) run(q, j, q * d + j);
+    } else {
+      for (uint32_t w = t; w < runs; w += kGenNT) {
+        const uint32_t q = w / d;
+        run(q, w - q * d, w);
+      }
     }
     __syncthreads();
-    const uint64_t lo = base > i0 ? base : i0, hi = (base + NP) < (i0 + n) ? (base + NP) : (i0 + n);
+    if (direct) continue;  // the barrier above also separates this item's run phase from the next
     const uint64_t words = (hi - lo) * d, soff = (lo - base) * d;
     const uint32_t *src = tile + soff;
     uint32_t *out = X + ((uint64_t)rl * n + (lo - i0)) * d;
@@ -152,7 +192,8 @@ int launch_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64_t 
   if (n == 0 || nr == 0) return QK_OK;
   const uint32_t d = ps->d, lognp = gen_lognp(d), NP = 1u << lognp;
   const uint64_t tiles = ((i0 + n - 1) >> lognp) - (i0 >> lognp) + 1;  // <= 2^29
-  const size_t smem = sizeof(uint32_t) * ((size_t)NP * d + 32 * d + (NP / kGenRL) * d + d);
+  const int direct = d >= 16;
+  const size_t smem = sizeof(uint32_t) * ((direct ? 0 : (size_t)NP * d) + 32 * d + (NP / kGenRL) * d + d);
   int occ = 0;
   if (ps->kind == QK_NET_B2) {
     smem_optin<k_points_tiled<true>>(smem);
@@ -168,10 +209,10 @@ int launch_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64_t 
   if (grid > total) grid = total;
   if (ps->kind == QK_NET_B2)
     k_points_tiled<true><<<(unsigned)grid, kGenNT, smem, st>>>(d, ps->order, ps->Ct, nullptr, ps->D, r0, nr, i0, n,
-                                                               lognp, (uint32_t)tiles, X);
+                                                               lognp, (uint32_t)tiles, direct, X);
   else
     k_points_tiled<false><<<(unsigned)grid, kGenNT, smem, st>>>(d, ps->order, nullptr, ps->g, ps->D, r0, nr, i0, n,
-                                                                lognp, (uint32_t)tiles, X);
+                                                                lognp, (uint32_t)tiles, direct, X);
   return check_launch("qk_gen_points");
 }
 
