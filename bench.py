@@ -21,7 +21,6 @@ profiler: ncu -k <kernel> -c <n> python bench.py --profile fused --R 8); it prin
 from __future__ import annotations
 
 import argparse
-import glob
 import hashlib
 import json
 import math
@@ -45,9 +44,9 @@ UNIT = "points/s"
 # CUDA sources that capture ran (kernel_source_hash()).  A run whose sources differ reports
 # traffic null: the counters belong to another version of the kernels.
 NCU_TRAFFIC = {
-    "src_hash": None,
-    "bytes_r64": {},
-    "fwht_bytes": None,
+    "src_hash": "83a366f7a6c5",
+    "bytes_r64": {"k_fused_A": 1394955776, "k_fused_B": 1293584384, "k_fused_C": 1053322496},
+    "fwht_bytes": 592104448,
 }
 # Nominal FP64 rate of GB300 (profiling recipe's table; FP64 is not a tensor-core path here).
 FP64_PEAK_TFLOPS = 1.25
@@ -79,10 +78,17 @@ def parse():
     return ap.parse_args()
 
 
+# The sources the fused pipeline's and the batched FWHT's kernels are compiled from.
+FUSED_SOURCES = ("qk_fused.cuh", "qk_fused.cu", "qk_fused_f32.cu", "qk_fused_f32c.cu", "qk_fused_f32w.cu",
+                 "qk_fused_f64.cu", "qk_column.cuh", "qk_common.cuh", "qk_factors.cuh", "qk_internal.h")
+
+
 def kernel_source_hash() -> str:
-    """Hash of the library's CUDA sources (which kernel version a measurement belongs to)."""
+    """Hash of the CUDA sources of the fused pipeline and the batched FWHT (which kernel version
+    a measurement belongs to)."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2502_14256_gb300", "csrc", "*"))):
+    for name in FUSED_SOURCES + ("../../include/qk.h",):
+        f = os.path.join(ROOT, "paper_2502_14256_gb300", "csrc", name)
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode() + fh.read())
     return h.hexdigest()[:12]
@@ -265,6 +271,48 @@ def workload_config(m, d, R, world):
                         "division/logdet/variance, 1 refinement step",
             "global_batch": world * R, "seq_len": 1 << m, "parallelism": f"replicas x{world}",
             "l2": "inputs larger than L2 (y alone 256 MB)"}
+
+
+def lattice_line(qk, torch, dev, stream, R=16):
+    """The differentiation workload's shape (rank-1 lattice n = 2^18, d = 32, SI kernel of
+    smoothness 2, unit weights, nugget e^-12) through the batched schedule (standalone ops:
+    the lattice path is not fused): solve + MLL + gradient for R randomizations (shifts) in
+    FP64 and with the float-float first column; points/s and the time per op."""
+    from paper_2502_14256_gb300 import inputs
+    wl = inputs.workload("diff")
+    m, d = wl.ms[0], wl.d
+    n = 1 << m
+    lat = inputs.make_lattice(wl.seed, d, R, m)
+    u32 = lambda a: torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).to(dev)  # noqa: E731
+    gd, Dd = u32(lat.g), u32(lat.D)
+    ps = qk.pointset(qk.QK_LATTICE, d, R, g=gd, D=Dd)
+    w = torch.tensor(np.asarray(wl.gamma) * np.exp(wl.log_ls), dtype=torch.float64, device=dev)
+    kern = qk.kernel(qk.QK_SI, wl.alpha, w, wl.zeta)
+    X = torch.empty((R, n, d), dtype=torch.int32, device=dev)
+    qk.gen_points(ps, 0, R, 0, n, X)
+    x = (X.to(torch.int64) & 0xFFFFFFFF).to(torch.float64) * 2.0 ** -32
+    jj = torch.arange(1, d + 1, dtype=torch.float64, device=dev)
+    y64 = torch.prod(1.0 + (x - 0.5) / jj ** 2, dim=2).reshape(R, 1, n)
+    del X, x
+    out = {"workload": f"lattice n=2^{m}, d={d}, SI alpha={wl.alpha}, {R} shifts, nugget e^-12, 1 rhs",
+           "points_per_step": R * n}
+    for name, dt in (("fp64", torch.float64), ("f32w", qk.F32W)):
+        y = y64.to(torch.float32).to(qk.data_dtype(dt)).contiguous()
+        c = torch.empty_like(y)
+        o = torch.empty((R, 1, qk.QK_MLL_NOUT), dtype=torch.float64, device=dev)
+        g = torch.empty((R, 1, 2 * d + 2), dtype=torch.float64, device=dev)
+        task = qk.Task(ps, kern, m, 1, wl.eta, y.data_ptr(), c.data_ptr(), None, o.data_ptr(), g.data_ptr())
+        ws = qk.workspace(qk.batch_workspace_bytes([task], dt), dev)
+        qk.batch_plan([task], dt, 1, ws)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        ms_ = time_steps(torch, lambda: qk.batch_run(ws, status), 3, 1, stream)
+        qk.batch_timing(ws, 1)
+        qk.batch_run(ws, status)
+        per_op = {k: v[1] for k, v in qk.batch_kernel_ms(ws).items()}
+        qk.batch_timing(ws, 0)
+        out[name] = {"ms_per_step": ms_, "value": R * n / (ms_ * 1e-3), "ops_ms": per_op}
+        del y, c, ws
+    return out
 
 
 # ------------------------------------------------------------- profile cases
@@ -485,6 +533,9 @@ def main():
     ff_bytes = 2 * xc.numel() * 4
     del xc
 
+    # ---- the lattice (SI) path on the differentiation workload's shape
+    lattice = lattice_line(qk, torch, dev, stream)
+
     # ---- the same step with the float-float first column (QK_F32W): its cost beside the headline
     PW = Pipeline(qk, torch, dev, W, qk.F32W, refine=args.refine, keep_lam=True)
     wide_ms = time_steps(torch, PW.step, max(3, args.steps // 2), 1, stream)
@@ -571,6 +622,7 @@ def main():
             "gpu_launches_per_step": launches / max(1, args.steps),
             "fp64_plain": fp64,
             "wide": wide,
+            "lattice": lattice,
             "schedule": sched,
             "stages_ms": stage,
             "doubling": doubling,
