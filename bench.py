@@ -67,13 +67,13 @@ def parse():
     ap.add_argument("--sched", default="auto", choices=["auto", "launches", "persistent"],
                     help="batched schedule: tuned (auto), per-phase launches or one persistent launch")
     ap.add_argument("--lag", type=int, default=1, help="persistent schedule: units between phases")
-    ap.add_argument("--profile", default=None, choices=["fused", "fwht", "fftbr", "points", "col"],
+    ap.add_argument("--profile", default=None, choices=["fused", "fwht", "fftbr", "points", "col", "lattice"],
                     help="run one small case of a hot kernel (for a profiler) instead of the benchmark")
     ap.add_argument("--reps", type=int, default=2, help="--profile: runs after one warm-up")
     ap.add_argument("--fp64", action="store_true", help="--profile fused/fftbr/col: FP64")
     ap.add_argument("--wide", action="store_true", help="--profile fused/col: float-float first column")
     ap.add_argument("--two-pass", action="store_true", help="--profile fwht: two-launch form")
-    ap.add_argument("--persistent", action="store_true", help="--profile fused: one persistent launch")
+    ap.add_argument("--persistent", action="store_true", help="--profile fused / fftbr: one persistent launch")
     ap.add_argument("--d", type=int, default=16, help="--profile points/col: dimensions")
     return ap.parse_args()
 
@@ -273,11 +273,10 @@ def workload_config(m, d, R, world):
             "l2": "inputs larger than L2 (y alone 256 MB)"}
 
 
-def lattice_line(qk, torch, dev, stream, R=16):
+def lattice_setup(qk, torch, dev, R, dt):
     """The differentiation workload's shape (rank-1 lattice n = 2^18, d = 32, SI kernel of
-    smoothness 2, unit weights, nugget e^-12) through the batched schedule (standalone ops:
-    the lattice path is not fused): solve + MLL + gradient for R randomizations (shifts) in
-    FP64 and with the float-float first column; points/s and the time per op."""
+    smoothness 2, unit weights, nugget e^-12) as one planned batch task of R randomizations
+    (shifts) in dtype dt: returns (workspace, status, points per run)."""
     from paper_2502_14256_gb300 import inputs
     wl = inputs.workload("diff")
     m, d = wl.ms[0], wl.d
@@ -294,24 +293,35 @@ def lattice_line(qk, torch, dev, stream, R=16):
     jj = torch.arange(1, d + 1, dtype=torch.float64, device=dev)
     y64 = torch.prod(1.0 + (x - 0.5) / jj ** 2, dim=2).reshape(R, 1, n)
     del X, x
-    out = {"workload": f"lattice n=2^{m}, d={d}, SI alpha={wl.alpha}, {R} shifts, nugget e^-12, 1 rhs",
-           "points_per_step": R * n}
+    y = y64.to(torch.float32).to(qk.data_dtype(dt)).contiguous()
+    c = torch.empty_like(y)
+    o = torch.empty((R, 1, qk.QK_MLL_NOUT), dtype=torch.float64, device=dev)
+    g = torch.empty((R, 1, 2 * d + 2), dtype=torch.float64, device=dev)
+    task = qk.Task(ps, kern, m, 1, wl.eta, y.data_ptr(), c.data_ptr(), None, o.data_ptr(), g.data_ptr())
+    ws = qk.workspace(qk.batch_workspace_bytes([task], dt), dev)
+    qk.batch_plan([task], dt, 1, ws)
+    ws._keep = (ps, kern, gd, Dd, w, y, c, o, g)  # buffers the plan points at
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    return ws, status, R * n
+
+
+def lattice_line(qk, torch, dev, stream, R=16):
+    """The lattice setup (differentiation workload's shape) through the batched schedule:
+    solve + MLL + gradient for R randomizations in FP64 and with the float-float first
+    column; points/s and the time per op."""
+    from paper_2502_14256_gb300 import inputs
+    wl = inputs.workload("diff")
+    out = {"workload": f"lattice n=2^{wl.ms[0]}, d={wl.d}, SI alpha={wl.alpha}, {R} shifts, nugget e^-12, 1 rhs",
+           "points_per_step": R << wl.ms[0]}
     for name, dt in (("fp64", torch.float64), ("f32w", qk.F32W)):
-        y = y64.to(torch.float32).to(qk.data_dtype(dt)).contiguous()
-        c = torch.empty_like(y)
-        o = torch.empty((R, 1, qk.QK_MLL_NOUT), dtype=torch.float64, device=dev)
-        g = torch.empty((R, 1, 2 * d + 2), dtype=torch.float64, device=dev)
-        task = qk.Task(ps, kern, m, 1, wl.eta, y.data_ptr(), c.data_ptr(), None, o.data_ptr(), g.data_ptr())
-        ws = qk.workspace(qk.batch_workspace_bytes([task], dt), dev)
-        qk.batch_plan([task], dt, 1, ws)
-        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        ws, status, pts = lattice_setup(qk, torch, dev, R, dt)
         ms_ = time_steps(torch, lambda: qk.batch_run(ws, status), 3, 1, stream)
         qk.batch_timing(ws, 1)
         qk.batch_run(ws, status)
         per_op = {k: v[1] for k, v in qk.batch_kernel_ms(ws).items()}
         qk.batch_timing(ws, 0)
-        out[name] = {"ms_per_step": ms_, "value": R * n / (ms_ * 1e-3), "ops_ms": per_op}
-        del y, c, ws
+        out[name] = {"ms_per_step": ms_, "value": pts / (ms_ * 1e-3), "ops_ms": per_op}
+        del ws
     return out
 
 
@@ -331,9 +341,16 @@ def profile_case(args):
         ws = qk.fwht_workspace(R, dev)
         plan = dict(mode=qk.QK_FWHT_TWO_PASS if args.two_pass else qk.QK_FWHT_PERSISTENT)
         run = lambda: qk.fwht_ws(m, x, ws, plan=plan, status=status)  # noqa: E731
+    elif args.profile == "lattice":
+        ws, lst, _ = lattice_setup(qk, torch, dev, R, torch.float64 if args.fp64 else qk.F32W)
+        run = lambda: qk.batch_run(ws, lst)  # noqa: E731
     elif args.profile == "fftbr":
         x = torch.randn((R, 2 * n), dtype=torch.float64 if args.fp64 else torch.float32, device=dev)
-        run = lambda: qk.fftbr(m, x)  # noqa: E731
+        if args.persistent:
+            fws = qk.fwht_workspace(R, dev)
+            run = lambda: qk.fftbr_ws(m, x, ws=fws, status=status)  # noqa: E731
+        else:
+            run = lambda: qk.fftbr(m, x)  # noqa: E731
     else:
         wl = inputs.workload("solve20")
         d = args.d if args.profile in ("points", "col") else wl.d
@@ -529,9 +546,11 @@ def main():
     del xf, fw_ws
     # FFTBR (the lattice transform) on R complex FP32 vectors of the same length
     xc = torch.randn((R, 2 * n), dtype=torch.float32, device=dev)
-    ff_ms = time_steps(torch, lambda: qk.fftbr(m, xc), args.steps, 2, stream)
+    ff_ws = qk.fwht_workspace(R, dev)
+    ff_ms = time_steps(torch, lambda: qk.fftbr_ws(m, xc, ws=ff_ws), args.steps, 2, stream)
+    ff2_ms = time_steps(torch, lambda: qk.fftbr(m, xc), args.steps, 2, stream)
     ff_bytes = 2 * xc.numel() * 4
-    del xc
+    del xc, ff_ws
 
     # ---- the lattice (SI) path on the differentiation workload's shape
     lattice = lattice_line(qk, torch, dev, stream)
@@ -635,7 +654,8 @@ def main():
                      "two_launch_ms": fw2_ms, "two_launch_gbs": fw_bytes / (fw2_ms * 1e-3) / 1e9},
             "fftbr": {"gbs": ff_bytes / (ff_ms * 1e-3) / 1e9, "ms": ff_ms, "bytes": ff_bytes,
                       "frac_of_hbm": ff_bytes / (ff_ms * 1e-3) / 1e9 / hbm_peak,
-                      "shape": f"{R} x 2^{m} complex fp32, in place, two tile passes"},
+                      "shape": f"{R} x 2^{m} complex fp32, in place, both tile passes in one persistent launch",
+                      "two_launch_ms": ff2_ms, "two_launch_gbs": ff_bytes / (ff2_ms * 1e-3) / 1e9},
             "roofline": roof,
             "kernel_sources": src_hash,
             "cpu_baseline": cpu,

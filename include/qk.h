@@ -180,9 +180,10 @@ QK_API int qk_eigs(int32_t family, uint32_t m, uint32_t batch, int32_t dtype, in
  * transform type: 8 bytes for FP64 nets, 4 for FP32 nets, 16 and 8 for lattices)
  * return QK_EINVAL and launch nothing.  The first call on each device looks up the
  * array's device address with that device current; make it before any stream
- * capture.  All calls share the array and it keeps the last call's contents (none
- * needs to start at zero); calls whose kernels overlap on the GPU race on it and
- * must be serialised by the caller. */
+ * capture.  The address is kept for the life of the process: no call may follow a
+ * cudaDeviceReset of that device (the reset unloads the array).  All calls share the
+ * array and it keeps the last call's contents (none needs to start at zero); calls
+ * whose kernels overlap on the GPU race on it and must be serialised by the caller. */
 #define QK_EIGS_STATIC_MAX_BYTES ((size_t)4 << 20)
 QK_API int qk_eigs_static(int32_t family, uint32_t m, uint32_t batch, int32_t dtype, int32_t form,
                           const void *col, double zeta, double eta, double *lam, uint32_t *status,
@@ -278,6 +279,19 @@ typedef struct {
 #define QK_FWHT_PERSISTENT 1
 QK_API int qk_fwht_ws(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes,
                       const qk_fwht_plan *plan, uint32_t *status, qk_stream stream);
+
+/* qk_fftbr (inverse = 0) or qk_ifftbr (inverse = 1) with a workspace: the same transform,
+ * bit for bit, for FP32 and 2^16 <= n <= 2^20 run as ONE persistent launch in which
+ * resident CTAs take tiles from a global ticket counter: the contiguous 12-bit tiles and
+ * the column tiles of the remaining high bits (FFTBR: in that order; IFFTBR: reversed), a
+ * vector's second-pass tiles queued `lag` vectors after its first-pass tiles (0 = from the
+ * grid size and n) so that they read the first pass's output back from L2.  Other sizes
+ * and FP64 run the transform of qk_fftbr / qk_ifftbr.  ws: (1 + nvec) 32-bit counters,
+ * 256-byte aligned (qk_workspace_bytes op 4), reset by the call.  The wait of a
+ * second-pass tile is bounded (about 1 s); past it the tile is skipped and
+ * QK_STATUS_TIMEOUT set in `status` (nullable).  Graph-capturable. */
+QK_API int qk_fftbr_ws(uint32_t m, uint64_t nvec, int32_t dtype, int32_t inverse, void *x, void *ws,
+                       size_t ws_bytes, uint32_t lag, uint32_t *status, qk_stream stream);
 
 /* Autotuner for qk_fwht_ws (the paper has no counterpart): times the two-launch form and
  * the persistent launch over CTAs per SM x lag on the caller's buffer x (its contents are
@@ -434,7 +448,12 @@ QK_API int qk_batch_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, i
 QK_API int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream stream);
 
 /* How qk_batch_run executes a recorded plan.  QK_SCHED_LAUNCHES (the default after
- * qk_batch_plan): per task, a sequence of kernel launches (4 for fused tasks).
+ * qk_batch_plan): per task, a sequence of kernel launches (4 for fused tasks).  Lattice
+ * tasks run the column, the eigenvalues and one pass for MLL, gradient and solve (two real
+ * vectors per complex FFTBR, one forward transform of y, one inverse transform giving both
+ * c and the gradient's back-transformed weights); with QK_F32W the forward transforms and
+ * the spectral step are FP64 and the inverse transforms and gradient sweep FP32; a QK_F32
+ * schedule with refinement steps keeps a separate refined solve.
  * QK_SCHED_PERSISTENT: ONE launch of resident CTAs for the whole plan; every
  * randomization of every task is a unit whose tiles (column sweep, high-bit transform
  * and epilogue, inverse and gradient sweep, final reduction) are taken in ticket order,

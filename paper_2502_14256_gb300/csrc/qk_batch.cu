@@ -69,9 +69,22 @@ static bool use_fused(const qk_task &t, int dtype, int refine) {
   return fused_supported(t, dtype);
 }
 
+// Lattice tasks run as column, eigenvalues and one combined MLL + gradient + solve pass on
+// pairs of vectors (qk_spectral.cu); an FP32 solve with refinement steps keeps the separate
+// refined solve.
+static bool use_lattice(const qk_task &t, int dtype, int refine) {
+  return t.k.family == QK_SI && (dtype != QK_F32 || refine == 0 || !t.c);
+}
+
 static size_t task_scratch(const qk_task &t, int dtype, int refine) {
   if (use_fused(t, dtype, refine)) return fused_ws_bytes(t, dtype, refine);
   const uint32_t R = t.ps.R;
+  if (use_lattice(t, dtype, refine)) {
+    const size_t col = align256((dtype == QK_F32 ? 4 : 8) * ((uint64_t)R << t.m));
+    size_t s = ws_eigs(t.k.family, t.m, R, dtype == QK_F32 ? QK_F32 : QK_F64);
+    const size_t mw = ws_mll_si(t.m, R, t.nrhs, dtype, t.ps.d, t.c != nullptr);
+    return col + (mw > s ? mw : s);
+  }
   if (dtype == QK_F32W) {
     // float-float column stored as FP64, FP64 eigenvalues and spectral sums, FP32 solve
     // with refinement and FP32 gradient sweep
@@ -158,6 +171,20 @@ static int run_task(const Plan &p, const qk_task &t, unsigned char *ws, uint32_t
     const ColJob job = make_job(&t.ps, &t.k, 0, R, t.m);
     if (use_fused(t, p.dtype, p.refine)) return run_fused(t, job, p.dtype, p.refine, ws, status, st, tm);
     int rc;
+    if (use_lattice(t, p.dtype, p.refine)) {
+      const int eig_dtype = p.dtype == QK_F32 ? QK_F32 : QK_F64;
+      {
+        OpScope s(tm, p.dtype == QK_F32W ? "op_kernel_col_ff" : "op_kernel_col", st);
+        if ((rc = launch_kernel_col(job, p.dtype, QK_COL_P, col, st))) return rc;
+      }
+      {
+        OpScope s(tm, "op_eigs", st);
+        if ((rc = op_eigs(t.k.family, t.m, R, eig_dtype, QK_COL_P, col, t.k.zeta, t.eta, lam, scr, status, st)))
+          return rc;
+      }
+      OpScope s(tm, "op_mll_solve", st);
+      return op_mll_solve_si(job, t.nrhs, p.dtype, lam, t.y, t.out, t.grad, t.c, scr, st);
+    }
     if (p.dtype == QK_F32W) {
       {
         OpScope s(tm, "op_kernel_col_ff", st);

@@ -142,6 +142,35 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Ticket order of a persistent two-pass tile transform (one launch for both passes of a
+// batch of vectors): step s of the item sequence holds the first-pass tiles of vector s
+// followed by the second-pass tiles of vector s - lag, so a vector's second pass runs
+// while its first-pass output (written in place) is still in L2.  A second-pass tile of
+// vector v waits until every first-pass tile of v has been published; those tiles hold
+// smaller tickets, were claimed by CTAs that are running, and wait on nothing, so the
+// wait ends (it is bounded all the same).
+struct WhtSched {
+  uint32_t nvec, lt, lag;  // lt = log2(tiles per vector and pass); 1 <= lag <= nvec
+  __host__ __device__ uint32_t total() const { return (2u * nvec) << lt; }
+  __device__ void decode(uint32_t i, uint32_t &v, uint32_t &tile, bool &second) const {
+    const uint32_t T = 1u << lt, pre = lag << lt, mid = ((nvec - lag) << lt) * 2u;
+    if (i < pre) {
+      v = i >> lt, tile = i & (T - 1), second = false;
+    } else if (i - pre < mid) {
+      const uint32_t j = i - pre, s = j >> (lt + 1), k = j & (2 * T - 1);
+      second = k >= T;
+      v = second ? s : lag + s;
+      tile = k & (T - 1);
+    } else {
+      const uint32_t j = i - pre - mid;
+      v = (nvec - lag) + (j >> lt), tile = j & (T - 1), second = true;
+    }
+  }
+};
 
 // Packed FP32 pairs for the f32x2 arithmetic of sm_100+: one instruction applies the
 // same IEEE operation (same rounding) to both halves.

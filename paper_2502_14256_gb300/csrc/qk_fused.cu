@@ -52,33 +52,9 @@ __global__ void __launch_bounds__(kFNT) k_wht_high(T *__restrict__ x, T scale) {
 
 // ------------------------------------------- persistent batched WHT (one launch)
 // Both tile passes of every vector in a single launch of resident CTAs that take work
-// items in ticket order from a global counter.  Step s of the item sequence holds the
-// low-pass tiles of vector s followed by the column tiles of vector s - lag, so a
-// vector's second pass runs while its first-pass output (written in place) is still in
-// L2 and HBM sees each element read once and written once.  A column tile of vector v
-// waits until every low tile of v has been published; those tiles hold smaller tickets,
-// were claimed by CTAs that are running, and wait on nothing, so the wait ends.  The
-// wait is bounded all the same: past the limit the item is skipped and
-// QK_STATUS_TIMEOUT is raised.
-struct WhtSched {
-  uint32_t nvec, lt, lag;  // lt = log2(tiles per vector); 1 <= lag <= nvec
-  __host__ __device__ uint32_t total() const { return (2u * nvec) << lt; }
-  __device__ void decode(uint32_t i, uint32_t &v, uint32_t &tile, bool &high) const {
-    const uint32_t T = 1u << lt, pre = lag << lt, mid = ((nvec - lag) << lt) * 2u;
-    if (i < pre) {
-      v = i >> lt, tile = i & (T - 1), high = false;
-    } else if (i - pre < mid) {
-      const uint32_t j = i - pre, s = j >> (lt + 1), k = j & (2 * T - 1);
-      high = k >= T;
-      v = high ? s : lag + s;
-      tile = k & (T - 1);
-    } else {
-      const uint32_t j = i - pre - mid;
-      v = (nvec - lag) + (j >> lt), tile = j & (T - 1), high = true;
-    }
-  }
-};
-
+// items in ticket order (WhtSched) from a global counter: the low-pass tiles first, a
+// vector's column tiles `lag` vectors later.  Past the wait limit a column tile is skipped
+// and QK_STATUS_TIMEOUT is raised.
 template <typename T, int M>
 __global__ void __launch_bounds__(kFNT, 5) k_wht_persist(T *__restrict__ x, T scale, WhtSched sc,
                                                          uint32_t *__restrict__ ctr, uint32_t *status,

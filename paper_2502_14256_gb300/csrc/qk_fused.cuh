@@ -902,10 +902,6 @@ __device__ __forceinline__ void fused_final_item(const FTask &ft, uint32_t v) {
 
 static __global__ void __launch_bounds__(256) k_fused_final(FTask ft) { fused_final_item(ft, blockIdx.x); }
 
-__device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // -------------------------------------- persistent whole-pipeline schedule (one launch)
 // Every randomization of every task is a unit u with four kinds of work items: A tiles,
 // B column tiles, C tiles (x right-hand sides) and F (the final reduction, one per

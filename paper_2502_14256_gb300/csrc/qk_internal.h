@@ -47,10 +47,12 @@ ColJob make_job(const qk_pointset *ps, const qk_kernel *k, uint32_t r0, uint32_t
 int launch_kernel_col(const ColJob &job, int32_t dtype, int32_t form, void *out, cudaStream_t st);
 
 // Gradient partial sums.  u: (nr * nrhs, n) in dtype (vector v belongs to
-// randomization v / nrhs).  partial: (nr * nrhs, blocks, 2d) doubles with
-// blocks = grad_blocks(m): [0, d) sum_i u_i dk1_i/dc_j, [d, 2d) sum_i dk1_i/dc_j.
+// randomization v / nrhs); with `pairs`, u is the pair layout of the lattice transforms
+// instead: vector v is the real (v even) or imaginary (v odd) part of complex vector v / 2.
+// partial: (nr * nrhs, blocks, 2d) doubles with blocks = grad_blocks(m):
+// [0, d) sum_i u_i dk1_i/dc_j, [d, 2d) sum_i dk1_i/dc_j.
 int launch_grad_partials(const ColJob &job, uint32_t nrhs, int32_t dtype, const void *u,
-                         double *partial, cudaStream_t st);
+                         double *partial, cudaStream_t st, bool pairs = false);
 uint32_t grad_blocks(uint32_t m);
 
 int launch_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64_t i0, uint64_t n,
@@ -65,6 +67,11 @@ int tiled_wht(void *x, uint32_t m, uint64_t nvec, int dtype, double scale, cudaS
 // Persistent single-launch batched WHT (qk_fused.cu) and its tuner (qk_tune.cu).
 constexpr uint32_t kSpinLimit = 1u << 23;  // ~1 s of 128 ns sleeps
 size_t persist_wht_ws_bytes(uint64_t nvec);
+// Persistent FP32 FFTBR (kind 1) / IFFTBR (kind 2) of n = 2^m, 16 <= m <= 20, in one launch
+// (qk_transform.cuh k_fft_persist); ctr: (1 + nvec) counters; lag 0 = automatic.
+bool persist_fft_supported(uint32_t m, int dtype);
+int persist_fft(int kind, void *x, uint32_t m, uint64_t nvec, double scale, uint32_t *ctr, uint32_t *status,
+                uint32_t lag, cudaStream_t st, uint32_t spin_limit = kSpinLimit);
 int persist_wht_max_ctas_per_sm(int dtype);
 uint32_t persist_wht_default_lag(uint32_t m, uint64_t nvec, int dtype, uint32_t ctas);
 int persist_wht(void *x, uint32_t m, uint64_t nvec, int dtype, double scale, void *ws, uint32_t *status,
@@ -110,6 +117,11 @@ int op_eigs_extend(int family, uint32_t m, uint32_t batch, int dtype, int form, 
                    double eta, const double *lam_old, double *lam, void *ws, uint32_t *status, cudaStream_t st);
 int op_transform_extend(int kind, uint32_t m, uint64_t nvec, int dtype, const void *xt_old, void *x_new, void *out,
                         cudaStream_t st);
+// Lattice tasks: MLL, gradient (grad may be null) and solve (c may be null) in one pass on
+// pairs of vectors; workspace ws_mll_si(..., c != null).
+size_t ws_mll_si(uint32_t m, uint32_t nr, uint32_t nrhs, int dtype, uint32_t d, bool with_c);
+int op_mll_solve_si(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const void *y, double *out,
+                    double *grad, void *c, void *ws, cudaStream_t st);
 int op_mll(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const void *y, double *out, double *grad,
            void *ws, cudaStream_t st);
 }  // namespace qk

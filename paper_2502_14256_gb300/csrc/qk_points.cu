@@ -342,7 +342,7 @@ int launch_kernel_col(const ColJob &job, int32_t dtype, int32_t form, void *out,
 // zeta (1 + p_i) K_ij / f_ij (explicit product where f_ij == 0).
 template <typename T, int FAM, int ALPHA>
 __global__ void __launch_bounds__(kNT) k_grad_partials(ColJob job, uint32_t nrhs, const T *__restrict__ u,
-                                                       double *__restrict__ partial) {
+                                                       double *__restrict__ partial, int pairs) {
   extern __shared__ __align__(16) unsigned char smem[];
   double *wd;
   DiffTables tb;
@@ -365,7 +365,8 @@ __global__ void __launch_bounds__(kNT) k_grad_partials(ColJob job, uint32_t nrhs
     const uint64_t i = tile_base + threadIdx.x + ((uint64_t)l << 8);
     bi[l] = __brev((uint32_t)i);
     ok[l] = i < n;
-    uu[l] = ok[l] ? u[(size_t)v * n + i] : T(0);
+    const size_t ui = pairs ? ((((size_t)(v >> 1) * n) + i) << 1) + (v & 1) : (size_t)v * n + i;
+    uu[l] = ok[l] ? u[ui] : T(0);
   }
   T p[kL];
   column_sweep<T, FAM, ALPHA, kL>(job, tb, wT, bi, p);
@@ -385,27 +386,29 @@ __global__ void __launch_bounds__(kNT) k_grad_partials(ColJob job, uint32_t nrhs
 uint32_t grad_blocks(uint32_t m) { return ceil_div_u(1ull << m, kTile); }
 
 template <typename T, int FAM, int ALPHA>
-static void launch_grad_t(const ColJob &job, uint32_t nrhs, const T *u, double *partial, cudaStream_t st) {
+static void launch_grad_t(const ColJob &job, uint32_t nrhs, const T *u, double *partial, int pairs,
+                          cudaStream_t st) {
   dim3 grid(grad_blocks(job.m), job.nr * nrhs);
   const size_t smem = col_smem_bytes<kL>(job.d) + (size_t)(kNT / 32) * 2 * job.d * sizeof(double);
   smem_optin<k_grad_partials<T, FAM, ALPHA>>(smem);
-  k_grad_partials<T, FAM, ALPHA><<<grid, kNT, smem, st>>>(job, nrhs, u, partial);
+  k_grad_partials<T, FAM, ALPHA><<<grid, kNT, smem, st>>>(job, nrhs, u, partial, pairs);
 }
 
 template <typename T>
-static int dispatch_grad(const ColJob &job, uint32_t nrhs, const T *u, double *partial, cudaStream_t st) {
+static int dispatch_grad(const ColJob &job, uint32_t nrhs, const T *u, double *partial, int pairs,
+                         cudaStream_t st) {
   if (job.family == QK_DSI) {
     switch (job.alpha) {
-      case 1: launch_grad_t<T, 0, 1>(job, nrhs, u, partial, st); break;
-      case 2: launch_grad_t<T, 0, 2>(job, nrhs, u, partial, st); break;
-      case 3: launch_grad_t<T, 0, 3>(job, nrhs, u, partial, st); break;
-      case 4: launch_grad_t<T, 0, 4>(job, nrhs, u, partial, st); break;
+      case 1: launch_grad_t<T, 0, 1>(job, nrhs, u, partial, pairs, st); break;
+      case 2: launch_grad_t<T, 0, 2>(job, nrhs, u, partial, pairs, st); break;
+      case 3: launch_grad_t<T, 0, 3>(job, nrhs, u, partial, pairs, st); break;
+      case 4: launch_grad_t<T, 0, 4>(job, nrhs, u, partial, pairs, st); break;
       default: return fail(QK_EINVAL, "DSI order must be 1..4");
     }
   } else {
     switch (job.alpha) {
-      case 1: launch_grad_t<T, 1, 1>(job, nrhs, u, partial, st); break;
-      case 2: launch_grad_t<T, 1, 2>(job, nrhs, u, partial, st); break;
+      case 1: launch_grad_t<T, 1, 1>(job, nrhs, u, partial, pairs, st); break;
+      case 2: launch_grad_t<T, 1, 2>(job, nrhs, u, partial, pairs, st); break;
       default: return fail(QK_EINVAL, "SI smoothness must be 1 or 2");
     }
   }
@@ -413,11 +416,14 @@ static int dispatch_grad(const ColJob &job, uint32_t nrhs, const T *u, double *p
 }
 
 int launch_grad_partials(const ColJob &job, uint32_t nrhs, int32_t dtype, const void *u, double *partial,
-                         cudaStream_t st) {
+                         cudaStream_t st, bool pairs) {
   if (job.nr == 0 || nrhs == 0) return QK_OK;
-  if (job.kind == kHONet) return launch_grad_partials_ho(job, nrhs, dtype, u, partial, st);
-  return dtype == QK_F64 ? dispatch_grad<double>(job, nrhs, (const double *)u, partial, st)
-                         : dispatch_grad<float>(job, nrhs, (const float *)u, partial, st);
+  if (job.kind == kHONet) {
+    if (pairs) return fail(QK_EINVAL, "gradient partials: pair layout is for lattices");
+    return launch_grad_partials_ho(job, nrhs, dtype, u, partial, st);
+  }
+  return dtype == QK_F64 ? dispatch_grad<double>(job, nrhs, (const double *)u, partial, pairs ? 1 : 0, st)
+                         : dispatch_grad<float>(job, nrhs, (const float *)u, partial, pairs ? 1 : 0, st);
 }
 
 }  // namespace qk

@@ -146,6 +146,201 @@ __global__ void k_mll_spectral(E *__restrict__ X, const double *__restrict__ lam
   }
 }
 
+// ------------------------------------------ lattices: two real vectors per complex transform
+// The DFT is linear and maps a real vector a to a Hermitian A (A_{n-k} = conj A_k).  So two
+// real vectors a, b travel as the one complex vector z = a + i b, whose transform Z = A + i B
+// splits per frequency pair (k, n - k) as
+//   A_k = (Z_k + conj Z_{n-k}) / 2,   B_k = (Z_k - conj Z_{n-k}) / (2 i),
+// and the inverse transform of C + i D with C, D Hermitian is c + i d with c, d real.  The
+// kernel column is real and symmetric in linear order, so its transform is real: A = Re Z,
+// B = Im Z directly.  Vector v of a batch of nvec lives in pair v / 2 as its real (v even) or
+// imaginary (v odd) part; an odd batch leaves the last pair's imaginary part zero.  Every
+// lattice transform thus runs on half as many complex vectors.
+
+__host__ __device__ inline uint64_t npairs_of(uint64_t nvec) { return (nvec + 1) >> 1; }
+
+template <typename E>
+__device__ __forceinline__ E cplx(double re_, double im_) {
+  E z;
+  z.x = (decltype(z.x))re_;
+  z.y = (decltype(z.y))im_;
+  return z;
+}
+
+// out[q] = in[2q] + i in[2q+1] (real vectors of T, n = 2^m each)
+template <typename T, typename E>
+__global__ void k_load_pairs(const T *__restrict__ in, E *__restrict__ out, uint64_t nvec, int m) {
+  const uint64_t total = npairs_of(nvec) << m, mask = (1ull << m) - 1;
+  for (uint64_t i = gtid(); i < total; i += gstride()) {
+    const uint64_t q = i >> m, w = i & mask;
+    const uint64_t vb = 2 * q + 1;
+    out[i] = cplx<E>((double)in[((2 * q) << m) + w], vb < nvec ? (double)in[(vb << m) + w] : 0.0);
+  }
+}
+
+// out[2q] = Re in[q] * scale, out[2q+1] = Im in[q] * scale
+template <typename E, typename T>
+__global__ void k_store_pairs(const E *__restrict__ in, T *__restrict__ out, uint64_t nvec, int m, double scale) {
+  const uint64_t total = npairs_of(nvec) << m, mask = (1ull << m) - 1;
+  for (uint64_t i = gtid(); i < total; i += gstride()) {
+    const uint64_t q = i >> m, w = i & mask;
+    const uint64_t vb = 2 * q + 1;
+    const E z = in[i];
+    out[((2 * q) << m) + w] = (T)((double)z.x * scale);
+    if (vb < nvec) out[(vb << m) + w] = (T)((double)z.y * scale);
+  }
+}
+
+// lambda of column 2q from Re Z, of column 2q+1 from Im Z; as k_lam_final otherwise.
+template <typename E>
+__global__ void k_lam_pairs(const E *__restrict__ X, double *__restrict__ lam, uint64_t nvec, int m,
+                            double zmul, double dc, double eta, uint32_t *status) {
+  bool bad = false, floored = false;
+  const uint64_t total = npairs_of(nvec) << m, mask = (1ull << m) - 1;
+  for (uint64_t i = gtid(); i < total; i += gstride()) {
+    const uint64_t q = i >> m, w = i & mask;
+    const E z = X[i];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint64_t v = 2 * q + h;
+      if (v >= nvec) break;
+      double val = zmul * (double)(h ? z.y : z.x) + eta;
+      if (w == 0) val += dc;
+      if (eta > 0.0 && !(val >= eta)) {
+        val = eta;
+        floored = true;
+      }
+      lam[(v << m) + w] = val;
+      bad |= !(val > 0.0);
+    }
+  }
+  if (bad && status) atomicOr(status, (uint32_t)QK_STATUS_NOTPD);
+  if (floored && status) atomicOr(status, (uint32_t)QK_STATUS_FLOOR);
+}
+
+// The two transforms held by pair element k and its partner kk = n - k (mod n): A_k, B_k
+// (A_kk = conj A_k, B_kk = conj B_k).
+template <typename E>
+__device__ __forceinline__ void split_pair(E zk, E zkk, double2 &a, double2 &b) {
+  a = make_double2(0.5 * ((double)zk.x + (double)zkk.x), 0.5 * ((double)zk.y - (double)zkk.y));
+  b = make_double2(0.5 * ((double)zk.y + (double)zkk.y), -0.5 * ((double)zk.x - (double)zkk.x));
+}
+// c + i d for complex c, d
+__device__ __forceinline__ double2 join_pair(double2 c, double2 d) { return make_double2(c.x - d.y, c.y + d.x); }
+
+// Per frequency pair (k, n - k), k = 0 .. n/2, of pair q: the vectors' transforms
+// Y_v = A or B; X <- Y / lambda * fac (mode 0) or Y * lambda * fac (mode 1), re-joined
+// (the products stay Hermitian, so the inverse transform returns real vectors again).
+template <typename E>
+__global__ void k_scale_pairs(E *__restrict__ X, const double *__restrict__ lam, uint64_t nvec, int m,
+                              uint32_t nrhs, double fac, int mode) {
+  const uint64_t n = 1ull << m, half = n >> 1, per = half + 1;
+  const uint64_t total = npairs_of(nvec) * per;
+  for (uint64_t i = gtid(); i < total; i += gstride()) {
+    const uint64_t q = i / per, k = i - q * per, kk = (n - k) & (n - 1);
+    E *xq = X + (q << m);
+    double2 a, b;
+    split_pair(xq[k], xq[kk], a, b);
+    double sk[2], skk[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint64_t v = 2 * q + h < nvec ? 2 * q + h : 2 * q;  // an absent half scales a zero
+      const double *lr = lam + ((v / nrhs) << m);
+      sk[h] = mode == 0 ? fac / lr[k] : fac * lr[k];
+      skk[h] = mode == 0 ? fac / lr[kk] : fac * lr[kk];
+    }
+    const double2 ck = make_double2(a.x * sk[0], a.y * sk[0]), dk = make_double2(b.x * sk[1], b.y * sk[1]);
+    const double2 ckk = make_double2(a.x * skk[0], -a.y * skk[0]), dkk = make_double2(b.x * skk[1], -b.y * skk[1]);
+    const double2 wk = join_pair(ck, dk), wkk = join_pair(ckk, dkk);
+    xq[k] = cplx<E>(wk.x, wk.y);
+    if (kk != k) xq[kk] = cplx<E>(wkk.x, wkk.y);
+  }
+}
+
+// r = y - part(Kc) (residual of the refinement step, pair layout of Kc)
+template <typename E, typename T>
+__global__ void k_residual_pairs(const T *__restrict__ y, const E *__restrict__ Kc, T *__restrict__ r,
+                                 uint64_t nvec, int m, double scale) {
+  const uint64_t total = npairs_of(nvec) << m, mask = (1ull << m) - 1;
+  for (uint64_t i = gtid(); i < total; i += gstride()) {
+    const uint64_t q = i >> m, w = i & mask;
+    const E z = Kc[i];
+    const uint64_t ia = ((2 * q) << m) + w, vb = 2 * q + 1;
+    r[ia] = (T)((double)y[ia] - (double)z.x * scale);
+    if (vb < nvec) r[(vb << m) + w] = (T)((double)y[(vb << m) + w] - (double)z.y * scale);
+  }
+}
+
+// MLL spectral step on pairs: per vector v the partial sums of y^T K^-1 y = sum |Y|^2/(n lam)
+// and of g = (|Y|^2/(n lam) - 1) / (2 lam); G <- g_a + i g_b (real, symmetric: its inverse
+// transform is u_a + i u_b); with C != nullptr also C <- Y_a/(n lam) + i Y_b/(n lam) (the
+// solve).  G may alias X (each thread reads its pair elements before writing them).
+template <typename E, typename EG, typename EO>
+__global__ void k_mll_spectral_pairs(const E *X, const double *__restrict__ lam, uint64_t nvec, int m,
+                                     uint32_t nrhs, double *__restrict__ part, EG *G, EO *__restrict__ C) {
+  __shared__ double sh[32];
+  const uint64_t n = 1ull << m, half = n >> 1;
+  const uint64_t q = blockIdx.y;
+  const E *xq = X + (q << m);
+  EG *gq = G + (q << m);
+  EO *cq = C ? C + (q << m) : nullptr;
+  const double inv_n = 1.0 / (double)n;
+  double qs[2] = {0.0, 0.0}, gs[2] = {0.0, 0.0};
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= half;
+       k += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t kk = (n - k) & (n - 1);
+    double2 y[2];
+    split_pair(xq[k], xq[kk], y[0], y[1]);
+    double gk[2], gkk[2], ck[2][2], ckk[2][2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint64_t v = 2 * q + h;
+      gk[h] = gkk[h] = 0.0;
+      ck[h][0] = ck[h][1] = ckk[h][0] = ckk[h][1] = 0.0;
+      if (v >= nvec) continue;
+      const double *lr = lam + ((v / nrhs) << m);
+      const double lk = lr[k], lkk = lr[kk];
+      const double y2 = y[h].x * y[h].x + y[h].y * y[h].y;
+      const double ak = y2 * inv_n / lk;
+      gk[h] = 0.5 * (ak - 1.0) / lk;
+      qs[h] += ak;
+      gs[h] += gk[h];
+      // the solve's scaling as in k_scale_pairs (same roundings as qk_solve)
+      const double sk = inv_n / lk, skk = inv_n / lkk;
+      ck[h][0] = y[h].x * sk;
+      ck[h][1] = y[h].y * sk;
+      if (kk != k) {
+        const double akk = y2 * inv_n / lkk;
+        gkk[h] = 0.5 * (akk - 1.0) / lkk;
+        qs[h] += akk;
+        gs[h] += gkk[h];
+        ckk[h][0] = y[h].x * skk;
+        ckk[h][1] = -y[h].y * skk;
+      }
+    }
+    gq[k] = cplx<EG>(gk[0], gk[1]);
+    if (kk != k) gq[kk] = cplx<EG>(gkk[0], gkk[1]);
+    if (cq) {
+      const double2 wk = join_pair(make_double2(ck[0][0], ck[0][1]), make_double2(ck[1][0], ck[1][1]));
+      cq[k] = cplx<EO>(wk.x, wk.y);
+      if (kk != k) {
+        const double2 wkk = join_pair(make_double2(ckk[0][0], ckk[0][1]), make_double2(ckk[1][0], ckk[1][1]));
+        cq[kk] = cplx<EO>(wkk.x, wkk.y);
+      }
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const double sq = block_sum(qs[h], sh);
+    const double sg = block_sum(gs[h], sh);
+    const uint64_t v = 2 * q + h;
+    if (threadIdx.x == 0 && v < nvec) {
+      part[(v * gridDim.x + blockIdx.x) * 2 + 0] = sq;
+      part[(v * gridDim.x + blockIdx.x) * 2 + 1] = sg;
+    }
+  }
+}
+
 template <bool FAST_LOG>
 __global__ void k_logdet(const double *__restrict__ lam, int m, double *__restrict__ part) {
   __shared__ double sh[32];
@@ -265,7 +460,9 @@ uint32_t spec_blocks(uint32_t m) {
   return (uint32_t)(b > 256 ? 256 : b);
 }
 // dtype QK_F32W: FP32 y and gradient sweep, FP64 transforms and spectral sums.
+size_t ws_mll_si(uint32_t m, uint32_t nr, uint32_t nrhs, int dtype, uint32_t d, bool with_c);
 size_t ws_mll(int family, uint32_t m, uint32_t nr, uint32_t nrhs, int dtype, uint32_t d) {
+  if (family == QK_SI) return ws_mll_si(m, nr, nrhs, dtype, d, false);
   const uint64_t nv = (uint64_t)nr * nrhs;
   size_t s = sized(nv, m, elem_bytes(family, dtype == QK_F32W ? QK_F64 : dtype));
   if (family == QK_SI || dtype == QK_F32W) s = add_sat(s, sized(nv, m, dtype == QK_F64 ? 8 : 4));  // real u
@@ -415,13 +612,30 @@ int op_transform_extend(int kind, uint32_t m, uint64_t nvec, int dtype, const vo
   return check_launch("transform extend");
 }
 
+// Lattices: two columns per complex transform (their transforms are real).
+template <typename T, typename E>
+static int eigs_si_t(uint32_t m, uint32_t batch, int form, const void *col, double zeta, double eta, double *lam,
+                     void *ws, uint32_t *status, cudaStream_t st) {
+  const uint64_t np = npairs_of(batch), cnt = np << m;
+  E *X = (E *)ws;
+  k_load_pairs<T, E><<<grid_for(cnt), 256, 0, st>>>((const T *)col, X, batch, (int)m);
+  int rc = check_launch("eigs load");
+  if (rc) return rc;
+  if ((rc = xform<E, XF_DIT>(X, (int)m, np, 1.0, st))) return rc;
+  const double zmul = form == QK_COL_P ? zeta : 1.0;
+  const double dc = form == QK_COL_P ? zeta * (double)(1ull << m) : 0.0;
+  k_lam_pairs<E><<<grid_for(cnt), 256, 0, st>>>(X, lam, batch, (int)m, zmul, dc, eta, status);
+  return check_launch("eigs finalize");
+}
+
 int op_eigs(int family, uint32_t m, uint32_t batch, int dtype, int form, const void *col, double zeta, double eta,
             double *lam, void *ws, uint32_t *status, cudaStream_t st) {
+  if (batch == 0) return QK_OK;
   if (family == QK_DSI)
     return dtype == QK_F64 ? eigs_t<double, double>(family, m, batch, form, col, zeta, eta, lam, ws, status, st)
                            : eigs_t<float, float>(family, m, batch, form, col, zeta, eta, lam, ws, status, st);
-  return dtype == QK_F64 ? eigs_t<double, double2>(family, m, batch, form, col, zeta, eta, lam, ws, status, st)
-                         : eigs_t<float, float2>(family, m, batch, form, col, zeta, eta, lam, ws, status, st);
+  return dtype == QK_F64 ? eigs_si_t<double, double2>(m, batch, form, col, zeta, eta, lam, ws, status, st)
+                         : eigs_si_t<float, float2>(m, batch, form, col, zeta, eta, lam, ws, status, st);
 }
 
 // c = K^-1 y (mode 0) or K y (mode 1) in precision of E; X is scratch of nvec * n E.
@@ -472,8 +686,63 @@ static int solve_t(int family, uint32_t m, uint32_t batch, uint32_t nrhs, const 
   return QK_OK;
 }
 
+// Lattices: c = K^-1 y (mode 0) or K y (mode 1) on pairs of vectors; X: (nvec + 1) / 2
+// complex vectors of E.
+template <typename T, typename E>
+static int apply_si_t(uint32_t m, uint32_t nvec, uint32_t nrhs, const double *lam, const T *y, T *c, E *X, int mode,
+                      cudaStream_t st) {
+  const uint64_t np = npairs_of(nvec), cnt = np << m;
+  const double n = (double)(1ull << m);
+  k_load_pairs<T, E><<<grid_for(cnt), 256, 0, st>>>(y, X, nvec, (int)m);
+  int rc = check_launch("solve load");
+  if (rc) return rc;
+  if ((rc = xform<E, XF_DIT>(X, (int)m, np, 1.0, st))) return rc;
+  k_scale_pairs<E><<<grid_for(np * ((1ull << m) / 2 + 1)), 256, 0, st>>>(X, lam, nvec, (int)m, nrhs, 1.0 / n, mode);
+  if ((rc = check_launch("solve scale"))) return rc;
+  if ((rc = xform<E, XF_DIF>(X, (int)m, np, 1.0, st))) return rc;
+  k_store_pairs<E, T><<<grid_for(cnt), 256, 0, st>>>(X, c, nvec, (int)m, 1.0);
+  return check_launch("solve store");
+}
+
+template <typename T, typename E, typename E64>
+static int solve_si_t(uint32_t m, uint32_t batch, uint32_t nrhs, const double *lam, const T *y, T *c, int refine,
+                      void *ws, cudaStream_t st) {
+  const uint32_t nvec = batch * nrhs;
+  const uint64_t np = npairs_of(nvec), cnt = (uint64_t)nvec << m;
+  unsigned char *p = (unsigned char *)ws;
+  E *X = (E *)p;
+  p += align256(sizeof(E) * (np << m));
+  E64 *X64 = (E64 *)p;
+  p += align256(sizeof(E64) * (np << m));
+  T *tmp = (T *)p;
+  int rc = apply_si_t<T, E>(m, nvec, nrhs, lam, y, c, X, 0, st);
+  if (rc) return rc;
+  const double n = (double)(1ull << m);
+  for (int it = 0; it < refine; ++it) {
+    // residual r = y - K c with FP64 transforms, then c += K^-1 r
+    k_load_pairs<T, E64><<<grid_for(np << m), 256, 0, st>>>(c, X64, nvec, (int)m);
+    if ((rc = check_launch("refine load"))) return rc;
+    if ((rc = xform<E64, XF_DIT>(X64, (int)m, np, 1.0, st))) return rc;
+    k_scale_pairs<E64><<<grid_for(np * ((1ull << m) / 2 + 1)), 256, 0, st>>>(X64, lam, nvec, (int)m, nrhs, 1.0 / n, 1);
+    if ((rc = check_launch("refine scale"))) return rc;
+    if ((rc = xform<E64, XF_DIF>(X64, (int)m, np, 1.0, st))) return rc;
+    k_residual_pairs<E64, T><<<grid_for(np << m), 256, 0, st>>>(y, X64, tmp, nvec, (int)m, 1.0);
+    if ((rc = check_launch("refine residual"))) return rc;
+    if ((rc = apply_si_t<T, E>(m, nvec, nrhs, lam, tmp, tmp, X, 0, st))) return rc;
+    k_add<T><<<grid_for(cnt), 256, 0, st>>>(c, tmp, cnt);
+    if ((rc = check_launch("refine add"))) return rc;
+  }
+  return QK_OK;
+}
+
 int op_solve(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, const double *lam, const void *y,
              void *c, int refine, void *ws, cudaStream_t st) {
+  if ((uint64_t)batch * nrhs == 0) return QK_OK;
+  if (family == QK_SI) {
+    if (dtype == QK_F64)
+      return solve_si_t<double, double2, double2>(m, batch, nrhs, lam, (const double *)y, (double *)c, refine, ws, st);
+    return solve_si_t<float, float2, double2>(m, batch, nrhs, lam, (const float *)y, (float *)c, refine, ws, st);
+  }
   if (family == QK_DSI) {
     if (dtype == QK_F64)
       return solve_t<double, double, double>(family, m, batch, nrhs, lam, (const double *)y, (double *)c, refine, ws, st);
@@ -506,6 +775,10 @@ int op_forward_real(int family, uint32_t m, uint64_t nvec, int dtype, const void
 int op_matvec(int family, uint32_t m, uint32_t batch, uint32_t nrhs, int dtype, const double *lam, const void *y,
               void *u, void *ws, cudaStream_t st) {
   const uint32_t nvec = batch * nrhs;
+  if (nvec == 0) return QK_OK;
+  if (family == QK_SI)
+    return dtype == QK_F64 ? apply_si_t<double, double2>(m, nvec, nrhs, lam, (const double *)y, (double *)u, (double2 *)ws, 1, st)
+                           : apply_si_t<float, float2>(m, nvec, nrhs, lam, (const float *)y, (float *)u, (float2 *)ws, 1, st);
   if (family == QK_DSI)
     return dtype == QK_F64 ? apply_t<double, double>(family, m, nvec, nrhs, lam, (const double *)y, (double *)u, (double *)ws, 1, st)
                            : apply_t<float, float>(family, m, nvec, nrhs, lam, (const float *)y, (float *)u, (float *)ws, 1, st);
@@ -581,16 +854,183 @@ static int mll_t(const ColJob &job, uint32_t nrhs, const double *lam, const T *y
   return check_launch("mll final");
 }
 
+// Lattices: MLL, gradient and (with c) the solve on pairs of vectors.  Forward transforms in
+// E, the spectral step in FP64, the inverse transforms of the gradient's g pairs (G; in
+// place over the forward data when EG == E) and of the solve's pairs (C) in the data
+// precision.  With the float-float column (QK_F32W) the forward transforms are FP64 and the
+// inverses FP32: the gradient's accuracy is then set by the FP32 sweep over the points (its
+// terms cancel near the nugget floor), which an FP64 inverse of g does not change
+// (measured: the same 4e-4 .. 6e-4 relative error on dMLL/dc at n = 2^12, eta = 1e-6).
+template <typename E, typename EG, typename EO>
+static size_t ws_mll_si_t(uint32_t m, uint32_t nr, uint32_t nrhs, uint32_t d, bool with_c) {
+  const uint64_t nv = (uint64_t)nr * nrhs, np = npairs_of(nv);
+  size_t s = sized(np, m, sizeof(E));
+  if (!std::is_same<E, EG>::value) s = add_sat(s, sized(np, m, sizeof(EG)));
+  if (with_c) s = add_sat(s, sized(np, m, sizeof(EO)));
+  s = add_sat(s, align256(nv * spec_blocks(m) * 2 * sizeof(double)));
+  s = add_sat(s, align256((uint64_t)nr * spec_blocks(m) * sizeof(double)));
+  s = add_sat(s, align256(nv * sizeof(double)));
+  s = add_sat(s, align256(nv * grad_blocks(m) * 2 * (uint64_t)d * sizeof(double)));
+  return s;
+}
+
+size_t ws_mll_si(uint32_t m, uint32_t nr, uint32_t nrhs, int dtype, uint32_t d, bool with_c) {
+  if (dtype == QK_F64) return ws_mll_si_t<double2, double2, double2>(m, nr, nrhs, d, with_c);
+  if (dtype == QK_F32W) return ws_mll_si_t<double2, float2, float2>(m, nr, nrhs, d, with_c);
+  return ws_mll_si_t<float2, float2, float2>(m, nr, nrhs, d, with_c);
+}
+
+template <typename T, typename E, typename EG, typename EO>
+static int mll_si_t(const ColJob &job, uint32_t nrhs, const double *lam, const T *y, double *out, double *grad,
+                    T *c, void *ws, cudaStream_t st, bool fast_log) {
+  static_assert(sizeof(EO) == 2 * sizeof(T) && sizeof(EG) == 2 * sizeof(T), "inverse transforms in the data precision");
+  const uint32_t m = job.m;
+  const uint64_t nvec = (uint64_t)job.nr * nrhs, np = npairs_of(nvec);
+  if (nvec == 0) return QK_OK;
+  unsigned char *p = (unsigned char *)ws;
+  E *X = (E *)p;
+  p += align256(sizeof(E) * (np << m));
+  EG *G = reinterpret_cast<EG *>(X);
+  if (!std::is_same<E, EG>::value) {
+    G = (EG *)p;
+    p += align256(sizeof(EG) * (np << m));
+  }
+  EO *C = nullptr;
+  if (c) {
+    C = (EO *)p;
+    p += align256(sizeof(EO) * (np << m));
+  }
+  const uint32_t bs = spec_blocks(m);
+  double *spec_part = (double *)p;
+  p += align256(nvec * bs * 2 * sizeof(double));
+  double *log_part = (double *)p;
+  p += align256((uint64_t)job.nr * bs * sizeof(double));
+  double *y0 = (double *)p;
+  p += align256(nvec * sizeof(double));
+  double *grad_part = (double *)p;
+
+  k_load_pairs<T, E><<<grid_for(np << m), 256, 0, st>>>(y, X, nvec, (int)m);
+  int rc = check_launch("mll load");
+  if (rc) return rc;
+  k_sum_rows<T><<<(unsigned)nvec, 1024, 0, st>>>(y, (int)m, y0);
+  if ((rc = check_launch("mll sum y"))) return rc;
+  if ((rc = xform<E, XF_DIT>(X, (int)m, np, 1.0, st))) return rc;
+  k_mll_spectral_pairs<E, EG, EO><<<dim3(bs, (unsigned)np), kRedNT, 0, st>>>(X, lam, nvec, (int)m, nrhs, spec_part,
+                                                                             G, C);
+  if ((rc = check_launch("mll spectral"))) return rc;
+  if (fast_log)  // FP32 logs of the eigenvalues: each log off by ~eps32 (absolute)
+    k_logdet<true><<<dim3(bs, job.nr), kRedNT, 0, st>>>(lam, (int)m, log_part);
+  else
+    k_logdet<false><<<dim3(bs, job.nr), kRedNT, 0, st>>>(lam, (int)m, log_part);
+  if ((rc = check_launch("mll logdet"))) return rc;
+  // G -> u_a + i u_b (real vectors of the gradient), C -> c_a + i c_b
+  if (grad) {
+    if ((rc = xform<EG, XF_DIF>(G, (int)m, np, 1.0, st))) return rc;
+    if ((rc = launch_grad_partials(job, nrhs, sizeof(T) == 8 ? QK_F64 : QK_F32, G, grad_part, st, true))) return rc;
+  }
+  if (c && (rc = xform<EO, XF_DIF>(C, (int)m, np, 1.0, st))) return rc;
+  if (c) {
+    k_store_pairs<EO, T><<<grid_for(np << m), 256, 0, st>>>(C, c, nvec, (int)m, 1.0);
+    if ((rc = check_launch("mll solve store"))) return rc;
+  }
+  FinalArgs fa;
+  fa.nvec = (uint32_t)nvec;
+  fa.nrhs = nrhs;
+  fa.d = job.d;
+  fa.bspec = bs;
+  fa.blog = bs;
+  fa.bgrad = grad_blocks(m);
+  fa.m = (int)m;
+  fa.zeta = job.zeta;
+  fa.lam = lam;
+  fa.spec_part = spec_part;
+  fa.log_part = log_part;
+  fa.grad_part = grad_part;
+  fa.y0 = y0;
+  fa.out = out;
+  fa.grad = grad;
+  k_mll_final<<<(unsigned)((nvec + 127) / 128), 128, 0, st>>>(fa);
+  return check_launch("mll final");
+}
+
+// MLL, gradient and solve of lattice tasks in one pass (dtype QK_F64, QK_F32W or QK_F32):
+// c may be null (no solve), grad may be null.
+int op_mll_solve_si(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const void *y, double *out,
+                    double *grad, void *c, void *ws, cudaStream_t st) {
+  if (job.family != QK_SI) return fail(QK_EINVAL, "op_mll_solve_si: lattice tasks only");
+  if (dtype == QK_F64)
+    return mll_si_t<double, double2, double2, double2>(job, nrhs, lam, (const double *)y, out, grad, (double *)c, ws,
+                                                       st, false);
+  if (dtype == QK_F32W)
+    return mll_si_t<float, double2, float2, float2>(job, nrhs, lam, (const float *)y, out, grad, (float *)c, ws, st,
+                                                    true);
+  return mll_si_t<float, float2, float2, float2>(job, nrhs, lam, (const float *)y, out, grad, (float *)c, ws, st,
+                                                 true);
+}
+
 int op_mll(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const void *y, double *out, double *grad,
            void *ws, cudaStream_t st) {
-  if (dtype == QK_F32W)
-    return job.family == QK_DSI ? mll_t<float, double>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype)
-                                : mll_t<float, double2>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype);
-  if (job.family == QK_DSI)
-    return dtype == QK_F64 ? mll_t<double, double>(job, nrhs, lam, (const double *)y, out, grad, ws, st, dtype)
-                           : mll_t<float, float>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype);
-  return dtype == QK_F64 ? mll_t<double, double2>(job, nrhs, lam, (const double *)y, out, grad, ws, st, dtype)
-                         : mll_t<float, float2>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype);
+  if (job.family == QK_SI) return op_mll_solve_si(job, nrhs, dtype, lam, y, out, grad, nullptr, ws, st);
+  if (dtype == QK_F32W) return mll_t<float, double>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype);
+  return dtype == QK_F64 ? mll_t<double, double>(job, nrhs, lam, (const double *)y, out, grad, ws, st, dtype)
+                         : mll_t<float, float>(job, nrhs, lam, (const float *)y, out, grad, ws, st, dtype);
+}
+
+// ------------------------------------------------ persistent FP32 FFTBR / IFFTBR
+bool persist_fft_supported(uint32_t m, int dtype) { return dtype == QK_F32 && m >= 16 && m <= 20; }
+
+template <int KIND, int KH>
+static int persist_fft_t(float2 *x, uint32_t m, uint64_t nvec, double scale, uint32_t *ctr, uint32_t *status,
+                         uint32_t lag, uint32_t spin_limit, cudaStream_t st) {
+  const size_t smem = pass_smem<float2>();
+  static int occ = -1;  // per instantiation; the same on every GB300
+  if (occ < 0) {
+    smem_optin<k_fft_persist<KIND, KH>>(smem);
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_fft_persist<KIND, KH>, 256, smem) != cudaSuccess || o < 1)
+      return fail(QK_ECUDA, "persistent FFT: occupancy query failed");
+    occ = o;
+  }
+  const uint32_t T = 1u << (m - 12);
+  const uint64_t items = (2ull * nvec) * T;
+  if (items >= (1ull << 31)) return fail(QK_EINVAL, "persistent FFT: %llu work items exceed 2^31",
+                                         (unsigned long long)items);
+  const uint32_t grid = (uint32_t)sm_count() * (uint32_t)occ;
+  if (lag == 0) {
+    // enough tickets between a vector's last first-pass tile and its first second-pass
+    // tile that the former has finished (lag T >= resident CTAs), three vectors of slack,
+    // at most 48 MB of first-pass output waiting in L2
+    uint64_t lg = (grid + T - 1) / T + 3;
+    const uint64_t cap = (48ull << 20) / (8ull << m);
+    if (lg > cap) lg = cap;
+    lag = (uint32_t)(lg < 1 ? 1 : lg);
+  }
+  if (lag > nvec) lag = (uint32_t)nvec;
+  WhtSched sc{(uint32_t)nvec, m - 12, lag};
+  cudaError_t e = cudaMemsetAsync(ctr, 0, sizeof(uint32_t) * (1 + nvec), st);
+  if (e != cudaSuccess) return cuda_fail(e, "persistent FFT: counter reset");
+  k_fft_persist<KIND, KH><<<grid, 256, smem, st>>>(x, scale, sc, ctr, status, spin_limit);
+  return check_launch("persistent FFT");
+}
+
+template <int KIND>
+static int persist_fft_kind(float2 *x, uint32_t m, uint64_t nvec, double scale, uint32_t *ctr, uint32_t *status,
+                            uint32_t lag, uint32_t spin_limit, cudaStream_t st) {
+  switch (m) {
+    case 16: return persist_fft_t<KIND, 4>(x, m, nvec, scale, ctr, status, lag, spin_limit, st);
+    case 17: return persist_fft_t<KIND, 5>(x, m, nvec, scale, ctr, status, lag, spin_limit, st);
+    case 18: return persist_fft_t<KIND, 6>(x, m, nvec, scale, ctr, status, lag, spin_limit, st);
+    case 19: return persist_fft_t<KIND, 7>(x, m, nvec, scale, ctr, status, lag, spin_limit, st);
+    case 20: return persist_fft_t<KIND, 8>(x, m, nvec, scale, ctr, status, lag, spin_limit, st);
+    default: return fail(QK_EINVAL, "persistent FFT: m = %u outside 16..20", m);
+  }
+}
+
+int persist_fft(int kind, void *x, uint32_t m, uint64_t nvec, double scale, uint32_t *ctr, uint32_t *status,
+                uint32_t lag, cudaStream_t st, uint32_t spin_limit) {
+  if (nvec == 0) return QK_OK;
+  if (kind == XF_DIT) return persist_fft_kind<XF_DIT>((float2 *)x, m, nvec, scale, ctr, status, lag, spin_limit, st);
+  return persist_fft_kind<XF_DIF>((float2 *)x, m, nvec, scale, ctr, status, lag, spin_limit, st);
 }
 
 int op_transform(int kind, uint32_t m, uint64_t nvec, int dtype, void *x, cudaStream_t st) {

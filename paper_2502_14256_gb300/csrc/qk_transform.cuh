@@ -19,6 +19,7 @@
 // their stages in increasing (DIT) or decreasing (DIF) bit order, passes too.
 #pragma once
 
+#include <type_traits>
 #include <vector>
 
 #include "qk_common.cuh"
@@ -298,6 +299,171 @@ __global__ void __launch_bounds__(NT) k_transform_pass(E *__restrict__ x, PassDe
   }
 }
 
+// FP32 complex passes (FFTBR / IFFTBR) that keep the tile in registers between rounds:
+// 4096 elements, 256 threads x 16.  A pass over K = 4..8 or 12 row bits (c = 12 - K
+// contiguous column bits) runs its butterflies in rounds of up to 4 row bits on the
+// thread's registers; between rounds one padded shared-memory transpose regroups the
+// elements so that the next round's bits are in registers.  Register layout at row-bit
+// offset b: thread t = col | rowlow << c | rowhigh << (c + b) holds register l at row
+// rowlow | l << b | rowhigh << (b + 4).  Rounds follow k_transform_pass: DIT upwards from
+// bit 0, the last round holding the R = K mod 4 top bits (layout b = K - 4, register bits
+// [4 - R, 4)); DIF downwards from the top, the last round holding the R bottom bits (layout
+// b = 0, register bits [0, R)); each partial round runs for every value of the other
+// register bits.  Global loads and stores use a
+// layout in which a warp covers whole 128-byte lines: the round layout itself where
+// c >= 4, and b = 8 (element t + 256 l) for K = 12, whose b = 0 end takes one more
+// transpose.  Butterflies and twiddles are those of radix_round: the same results as
+// k_transform_pass, bit for bit.
+template <int K>
+__device__ __forceinline__ int fft_reg_elem(int t, int b, int l) {
+  constexpr int C = 12 - K;
+  const int col = t & ((1 << C) - 1);
+  const int rowlow = (t >> C) & ((1 << b) - 1);
+  const int rowhigh = t >> (C + b);
+  return col | ((rowlow | (l << b) | (rowhigh << (b + 4))) << C);
+}
+
+template <int K>
+__device__ __forceinline__ void fft_reg_relayout(float2 (&v)[16], float2 *sm, int from_b, int to_b) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int l = 0; l < 16; ++l) sm[pad_index<float2>(fft_reg_elem<K>(t, from_b, l))] = v[l];
+  __syncthreads();
+#pragma unroll
+  for (int l = 0; l < 16; ++l) v[l] = sm[pad_index<float2>(fft_reg_elem<K>(t, to_b, l))];
+  __syncthreads();
+}
+
+// Butterflies on register bits [H0, H0 + R) in layout b, for each value of the other bits.
+template <int KIND, int K, int R, int H0>
+__device__ __forceinline__ void fft_reg_round(float2 (&v)[16], const TileMap &tm, int b) {
+  constexpr int NO = 1 << (4 - R);  // values of the other register bits
+  const int gb0 = tm.s + b + H0;
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    // other bits: below H0 they are o's low bits, above H0 + R its high bits
+    const int olow = o & ((1 << H0) - 1), ohigh = o >> H0;
+    float2 g[1 << R];
+#pragma unroll
+    for (int q = 0; q < (1 << R); ++q) g[q] = v[olow | (q << H0) | (ohigh << (H0 + R))];
+    const uint64_t glow = tm.gindex(fft_reg_elem<K>(threadIdx.x, b, olow | (ohigh << (H0 + R)))) &
+                          ((1ull << gb0) - 1);
+    radix_round<KIND, R, float2>(g, glow, gb0);
+#pragma unroll
+    for (int q = 0; q < (1 << R); ++q) v[olow | (q << H0) | (ohigh << (H0 + R))] = g[q];
+  }
+}
+
+// One tile of a pass: load, all rounds, store (times scale).  CG: loads bypass L1 (data
+// written by other CTAs of the same launch).
+template <int KIND, int K, bool CG>
+__device__ __forceinline__ void fft_reg_tile(float2 *__restrict__ x, const TileMap &tm, float2 *sm, double scale) {
+  static_assert((K >= 4 && K <= 8) || K == 12, "4..8 or 12 row bits");
+  constexpr int F = K / 4, RP = K % 4;  // full rounds, bits of the partial round
+  // DIT: full rounds at b = 0, 4, ..., then the top RP bits in layout K - 4.
+  // DIF: full rounds at b = K - 4, K - 8, ..., then the bottom RP bits in layout 0.
+  constexpr int B_FIRST = KIND == XF_DIF ? K - 4 : 0;
+  constexpr int B_LAST = KIND == XF_DIF ? 0 : K - 4;
+  constexpr int B_IO_IN = K == 12 ? 8 : B_FIRST;
+  constexpr int B_IO_OUT = K == 12 ? 8 : B_LAST;
+  const int t = threadIdx.x;
+  float2 v[16];
+#pragma unroll
+  for (int l = 0; l < 16; ++l) {
+    const float2 *src = x + tm.offset(fft_reg_elem<K>(t, B_IO_IN, l));
+    v[l] = CG ? __ldcg(src) : *src;
+  }
+  if constexpr (B_IO_IN != B_FIRST) fft_reg_relayout<K>(v, sm, B_IO_IN, B_FIRST);
+  int bcur = B_FIRST;
+#pragma unroll
+  for (int rd = 0; rd < F; ++rd) {
+    const int b = KIND == XF_DIF ? K - 4 - 4 * rd : 4 * rd;
+    if (b != bcur) {
+      fft_reg_relayout<K>(v, sm, bcur, b);
+      bcur = b;
+    }
+    fft_reg_round<KIND, K, 4, 0>(v, tm, b);
+  }
+  if constexpr (RP > 0) {
+    if (bcur != B_LAST) {
+      fft_reg_relayout<K>(v, sm, bcur, B_LAST);
+      bcur = B_LAST;
+    }
+    if constexpr (KIND == XF_DIF) fft_reg_round<KIND, K, RP, 0>(v, tm, 0);
+    else fft_reg_round<KIND, K, RP, 4 - RP>(v, tm, K - 4);
+  }
+  if (bcur != B_IO_OUT) fft_reg_relayout<K>(v, sm, bcur, B_IO_OUT);
+  const bool do_scale = scale != 1.0;
+#pragma unroll
+  for (int l = 0; l < 16; ++l) {
+    float2 w = v[l];
+    if (do_scale) w = scale_elem(w, scale);
+    x[tm.offset(fft_reg_elem<K>(t, B_IO_OUT, l))] = w;
+  }
+}
+
+template <int KIND, int K>
+__global__ void __launch_bounds__(256) k_fft_reg(float2 *__restrict__ x, PassDesc p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  fft_reg_tile<KIND, K, false>(x, make_tilemap(p, 12, blockIdx.x), reinterpret_cast<float2 *>(smem_raw), p.scale);
+}
+
+// Both passes of an FP32 complex transform of n = 2^(12 + KH) (KH = 4..8) in ONE launch of
+// resident CTAs taking tiles in WhtSched ticket order: FFTBR runs the contiguous 12-bit
+// tiles first and the column tiles of the high KH bits second, IFFTBR the reverse; the
+// second pass of a vector starts after all its first-pass tiles are published (bounded
+// wait: past spin_limit tries the tile is skipped and QK_STATUS_TIMEOUT set).  The same
+// tiles and butterflies as the two launches: the same results, bit for bit.
+template <int KIND, int KH>
+__global__ void __launch_bounds__(256) k_fft_persist(float2 *__restrict__ x, double scale, WhtSched sc,
+                                                     uint32_t *__restrict__ ctr, uint32_t *status,
+                                                     uint32_t spin_limit) {
+  constexpr int M = 12 + KH;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ uint32_t s_item[2], s_ok[2];  // as in the persistent FWHT: item k's slots are k & 1
+  float2 *sm = reinterpret_cast<float2 *>(smem_raw);
+  uint32_t *ticket = ctr, *done = ctr + 1;
+  const int t = threadIdx.x;
+  const uint32_t total = sc.total(), T_ = 1u << sc.lt;
+  const PassDesc plo{M, 0, 12, 0, 0, 1ull << M, sc.nvec, 1.0};
+  const PassDesc phi{M, 12, KH, 12 - KH, 0, 1ull << M, sc.nvec, 1.0};
+  if (t == 0) s_item[0] = atomicAdd(ticket, 1u);
+  __syncthreads();
+  for (int k = 0;; ++k) {
+    const uint32_t it = s_item[k & 1];
+    if (it >= total) break;
+    if (t == 0) s_item[(k + 1) & 1] = atomicAdd(ticket, 1u);
+    uint32_t v, tile;
+    bool second;
+    sc.decode(it, v, tile, second);
+    const uint64_t blk = ((uint64_t)v << sc.lt) + tile;
+    if (!second) {
+      if constexpr (KIND == XF_DIF) fft_reg_tile<KIND, KH, false>(x, make_tilemap(phi, 12, blk), sm, 1.0);
+      else fft_reg_tile<KIND, 12, false>(x, make_tilemap(plo, 12, blk), sm, 1.0);
+      __syncthreads();  // every thread's stores precede thread 0's release
+      if (t == 0) red_release_add_u32(&done[v], 1u);
+    } else {
+      if (t == 0) {
+        uint32_t tries = 0, ok = 1;
+        while (ld_acquire_u32(&done[v]) < T_) {
+          if (++tries > spin_limit) {
+            ok = 0;
+            if (status) atomicOr(status, (uint32_t)QK_STATUS_TIMEOUT);
+            break;
+          }
+          __nanosleep(128);
+        }
+        s_ok[k & 1] = ok;
+      }
+      __syncthreads();
+      if (s_ok[k & 1]) {
+        if constexpr (KIND == XF_DIF) fft_reg_tile<KIND, 12, true>(x, make_tilemap(plo, 12, blk), sm, scale);
+        else fft_reg_tile<KIND, KH, true>(x, make_tilemap(phi, 12, blk), sm, scale);
+      }
+    }
+  }
+}
+
 // Host: split the m bits into passes.
 template <typename E>
 inline std::vector<PassDesc> plan_passes(int m, uint64_t vstride, uint64_t nvec) {
@@ -353,6 +519,22 @@ int run_transform(E *x, int m, uint64_t vstride, uint64_t nvec, double scale, cu
     const uint64_t blocks = pass_blocks<E>(p);
     if (blocks == 0) continue;
     if (blocks > 0x7FFFFFFFull) return fail(QK_EINVAL, "transform grid too large");
+    if constexpr (KIND != XF_WHT && std::is_same<E, float2>::value) {
+      // FP32 complex tiles of 4..8 or 12 row bits: registers between rounds
+      if (!p.small && p.c + p.k == 12 && ((p.k >= 4 && p.k <= 8) || p.k == 12)) {
+        switch (p.k) {
+          case 4: k_fft_reg<KIND, 4><<<(unsigned)blocks, NT, smem, st>>>(x, p); break;
+          case 5: k_fft_reg<KIND, 5><<<(unsigned)blocks, NT, smem, st>>>(x, p); break;
+          case 6: k_fft_reg<KIND, 6><<<(unsigned)blocks, NT, smem, st>>>(x, p); break;
+          case 7: k_fft_reg<KIND, 7><<<(unsigned)blocks, NT, smem, st>>>(x, p); break;
+          case 8: k_fft_reg<KIND, 8><<<(unsigned)blocks, NT, smem, st>>>(x, p); break;
+          default: k_fft_reg<KIND, 12><<<(unsigned)blocks, NT, smem, st>>>(x, p); break;
+        }
+        int rc = check_launch("transform pass (registers)");
+        if (rc) return rc;
+        continue;
+      }
+    }
     k_transform_pass<KIND, E, NT><<<(unsigned)blocks, NT, smem, st>>>(x, p);
     int rc = check_launch("transform pass");
     if (rc) return rc;

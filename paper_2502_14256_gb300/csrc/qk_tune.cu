@@ -74,6 +74,23 @@ int qk_fwht_ws(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size
   return run_plan_wht(p, m, nvec, dtype, x, ws, status, (cudaStream_t)stream);
 }
 
+int qk_fftbr_ws(uint32_t m, uint64_t nvec, int32_t dtype, int32_t inverse, void *x, void *ws, size_t ws_bytes,
+                uint32_t lag, uint32_t *status, qk_stream stream) {
+  set_error("%s", "");
+  if (dtype != QK_F64 && dtype != QK_F32) return fail(QK_EINVAL, "dtype must be QK_F64 or QK_F32");
+  if (m > QK_MAX_M) return fail(QK_EINVAL, "m = %u exceeds QK_MAX_M = %d", m, QK_MAX_M);
+  if (inverse != 0 && inverse != 1) return fail(QK_EINVAL, "inverse must be 0 or 1");
+  if (nvec == 0) return QK_OK;
+  if (!x) return fail(QK_EINVAL, "transform data is NULL");
+  const int kind = inverse ? 2 /* IFFTBR */ : 1 /* FFTBR */;
+  if (!persist_fft_supported(m, dtype)) return op_transform(kind, m, nvec, dtype, x, (cudaStream_t)stream);
+  const size_t need = persist_wht_ws_bytes(nvec);
+  if (!ws || ws_bytes < need) return fail(QK_EWORKSPACE, "qk_fftbr_ws: workspace has %zu bytes, %zu needed", ws_bytes, need);
+  if (((uintptr_t)ws & 255u) != 0) return fail(QK_EINVAL, "workspace must be 256-byte aligned");
+  return persist_fft(kind, x, m, nvec, 1.0 / std::sqrt((double)(1ull << m)), (uint32_t *)ws, status, lag,
+                     (cudaStream_t)stream);
+}
+
 int qk_fwht_tune(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes, qk_fwht_plan *best,
                  qk_stream stream) {
   set_error("%s", "");

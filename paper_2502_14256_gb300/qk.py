@@ -40,7 +40,8 @@ EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_sol
             "qk_fwht_tune", "qk_fwht_wait_selftest", "qk_batch_run_host", "qk_batch_schedule",
             "qk_kernel_col_at", "qk_eigs_extend", "qk_fwht_extend", "qk_fftbr_extend", "qk_batch_tune",
             "qk_integrand", "qk_rqmc", "qk_student_t_quantile", "qk_discrepancy", "qk_discrepancy_weights",
-            "qk_interlace", "qk_gen_points_ho", "qk_kernel_col_ho", "qk_mll_spectrum", "qk_mll_ho"]
+            "qk_interlace", "qk_gen_points_ho", "qk_kernel_col_ho", "qk_mll_spectrum", "qk_mll_ho",
+            "qk_fftbr_ws"]
 QK_F_SIMPLE1, QK_F_SIMPLE2, QK_F_OAKLEY, QK_F_GFUN, QK_F_GENZ_OSC, QK_F_GENZ_CP = range(6)
 INTEGRANDS = {"simple1": QK_F_SIMPLE1, "simple2": QK_F_SIMPLE2, "oakley": QK_F_OAKLEY, "gfun": QK_F_GFUN,
               "genz_osc": QK_F_GENZ_OSC, "genz_cp": QK_F_GENZ_CP}
@@ -109,6 +110,7 @@ def _load():
         "qk_batch_timing": [P, u32],
         "qk_batch_kernel_ms": [P, u32, C.c_char_p, sz, C.POINTER(u32), C.POINTER(dbl)],
         "qk_fwht_ws": [u32, u64, i32, P, P, sz, C.POINTER(FwhtPlan), P, P],
+        "qk_fftbr_ws": [u32, u64, i32, i32, P, P, sz, u32, P, P],
         "qk_fwht_tune": [u32, u64, i32, P, P, sz, C.POINTER(FwhtPlan), P],
         "qk_fwht_wait_selftest": [u32, u64, i32, P, P, sz, u32, P, P],
         "qk_batch_run_host": [P, sz, C.POINTER(HostIO), u32, P, P],
@@ -376,6 +378,17 @@ def fwht_ws(m: int, x, ws=None, plan=None, status=None, stream=None):
         pp = C.byref(FwhtPlan(plan["mode"], plan.get("lag", 0), plan.get("ctas_per_sm", 0), 0.0))
     _check(LIB.qk_fwht_ws(m, nvec, dtype_code(x.dtype), _ptr(x), _ptr(ws), ws.numel(), pp, _ptr(status),
                           _stream(stream)))
+    return x
+
+
+def fftbr_ws(m: int, x, inverse=False, ws=None, lag=0, status=None, stream=None):
+    """qk_fftbr (or qk_ifftbr) with a workspace: one persistent launch for FP32 and
+    16 <= m <= 20 (the same results bit for bit), the plain transform otherwise."""
+    nvec = _nvec_m(x, m, True)
+    if ws is None:
+        ws = fwht_workspace(nvec, x.device)
+    _check(LIB.qk_fftbr_ws(m, nvec, dtype_code(x.dtype), 1 if inverse else 0, _ptr(x), _ptr(ws), ws.numel(),
+                           lag, _ptr(status), _stream(stream)))
     return x
 
 

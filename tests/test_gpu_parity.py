@@ -391,10 +391,10 @@ def test_batch_schedule_matches_per_call_results_and_replays_in_a_graph(qk):
 
 
 # --------------------------------------------------------- public transforms
-@pytest.mark.parametrize("m", [0, 1, 5, 12, 13, 14, 17, 20, 21])
+@pytest.mark.parametrize("m", [0, 1, 5, 12, 13, 14, 16, 17, 18, 19, 20, 21, 24])
 def test_fwht_fftbr_ifftbr(qk, m):
     n = 1 << m
-    nvec = 3 if m < 20 else 2
+    nvec = 3 if m < 20 else (2 if m < 24 else 1)
     rng = np.random.default_rng(m)
     x = rng.standard_normal((nvec, n))
     want = o.hadamard_apply(x) / math.sqrt(n)
@@ -412,6 +412,27 @@ def test_fwht_fftbr_ifftbr(qk, m):
         qk.ifftbr(m, t)
         got = t.cpu().numpy()
         assert qc.rel_err(got[..., 0] + 1j * got[..., 1], z) < tol, (dt, m)
+
+
+@pytest.mark.parametrize("m", [13, 16, 17, 18, 19, 20])
+def test_fftbr_persistent_equals_two_pass(qk, m):
+    """qk_fftbr_ws: both passes of FFTBR / IFFTBR in one persistent launch, bit for bit the
+    pass-by-pass transform (m = 13 and FP64 fall back to it), for several lags."""
+    n = 1 << m
+    nvec = 7
+    rng = np.random.default_rng(700 + m)
+    z = np.stack([rng.standard_normal((nvec, n)), rng.standard_normal((nvec, n))], axis=-1)
+    for dt in (F32, F64):
+        for inverse in (False, True):
+            ref = torch.tensor(z, dtype=dt, device=qc.dev()).contiguous()
+            (qk.ifftbr if inverse else qk.fftbr)(m, ref)
+            for lag in (0, 1, 3, nvec):
+                t = torch.tensor(z, dtype=dt, device=qc.dev()).contiguous()
+                status = torch.zeros(1, dtype=torch.int32, device=qc.dev())
+                qk.fftbr_ws(m, t, inverse=inverse, lag=lag, status=status)
+                torch.cuda.synchronize()
+                assert int(status.item()) == 0
+                assert torch.equal(t, ref), (dt, inverse, lag)
 
 
 # ------------------------------------------------------------ fused pipeline
