@@ -71,7 +71,11 @@ __device__ __forceinline__ T dsi_factor(uint32_t Z) {
 template <typename T, int ALPHA>
 __device__ __forceinline__ T si_factor(uint32_t W) {
   const T x = word_to_unit(T(), W);
-  const T q = x * (T(1) - x);
+  // x (1 - x): in FP64, 1 - x is exact (x has 32 significant bits), so x * (1 - x) and the
+  // fused x - x * x both round the same real number once; the fused form is one operation
+  T q;
+  if constexpr (sizeof(T) == 8) q = fma(-x, x, x);
+  else q = x * (T(1) - x);
   if constexpr (ALPHA == 1) {
     return T(3.2898681336964528729) - T(19.739208802178717238) * q;  // pi^2/3, 2 pi^2
   } else {

@@ -105,17 +105,19 @@ __global__ void k_add(T *__restrict__ c, const T *__restrict__ dc, uint64_t coun
 
 constexpr int kRedNT = 256;
 
-// Per vector: FP64 sum of y (the posterior mean needs it with relative accuracy,
-// and for a centred integrand it is a small difference of large terms).
+// Per vector: FP64 partial sums of y over gridDim.x contiguous chunks, out[v][chunk] (the
+// posterior mean needs the sum with relative accuracy, and for a centred integrand it is
+// a small difference of large terms; k_mll_final adds the chunks).
 template <typename T>
 __global__ void k_sum_rows(const T *__restrict__ y, int m, double *__restrict__ out) {
   __shared__ double sh[32];
-  const uint64_t n = 1ull << m;
-  const T *yv = y + (uint64_t)blockIdx.x * n;
+  const uint64_t n = 1ull << m, chunk = (n + gridDim.x - 1) / gridDim.x;
+  const uint64_t lo = (uint64_t)blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  const T *yv = y + (uint64_t)blockIdx.y * n;
   double s = 0.0;
-  for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)yv[i];
+  for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += (double)yv[i];
   const double t = block_sum(s, sh);
-  if (threadIdx.x == 0) out[blockIdx.x] = t;
+  if (threadIdx.x == 0) out[(uint64_t)blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 // Per vector: quad and sum g partials; overwrite X with g (real); keep Re Y_0.
@@ -299,19 +301,20 @@ __global__ void k_mll_spectral_pairs(const E *X, const double *__restrict__ lam,
       ck[h][0] = ck[h][1] = ckk[h][0] = ckk[h][1] = 0.0;
       if (v >= nvec) continue;
       const double *lr = lam + ((v / nrhs) << m);
-      const double lk = lr[k], lkk = lr[kk];
+      // one division per eigenvalue; inv_n is a power of two, so sk = inv_n / lambda exactly
+      // as k_scale_pairs rounds it (the same solve as qk_solve, bit for bit)
+      const double rk = 1.0 / lr[k], rkk = 1.0 / lr[kk];
+      const double sk = inv_n * rk, skk = inv_n * rkk;
       const double y2 = y[h].x * y[h].x + y[h].y * y[h].y;
-      const double ak = y2 * inv_n / lk;
-      gk[h] = 0.5 * (ak - 1.0) / lk;
+      const double ak = y2 * sk;
+      gk[h] = 0.5 * (ak - 1.0) * rk;
       qs[h] += ak;
       gs[h] += gk[h];
-      // the solve's scaling as in k_scale_pairs (same roundings as qk_solve)
-      const double sk = inv_n / lk, skk = inv_n / lkk;
       ck[h][0] = y[h].x * sk;
       ck[h][1] = y[h].y * sk;
       if (kk != k) {
-        const double akk = y2 * inv_n / lkk;
-        gkk[h] = 0.5 * (akk - 1.0) / lkk;
+        const double akk = y2 * skk;
+        gkk[h] = 0.5 * (akk - 1.0) * rkk;
         qs[h] += akk;
         gs[h] += gkk[h];
         ckk[h][0] = y[h].x * skk;
@@ -354,46 +357,72 @@ __global__ void k_logdet(const double *__restrict__ lam, int m, double *__restri
 }
 
 struct FinalArgs {
-  uint32_t nvec, nrhs, d, bspec, blog, bgrad;
+  uint32_t nvec, nrhs, d, bspec, blog, bgrad, by0;
   int m;
   double zeta;
-  const double *lam, *spec_part, *log_part, *grad_part, *y0;
+  const double *lam, *spec_part, *log_part, *grad_part, *y0;  // y0: (nvec, by0) partial sums of y
   double *out, *grad;
 };
 
-__global__ void k_mll_final(FinalArgs a) {
-  const uint32_t v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= a.nvec) return;
+constexpr int kFinNT = 256;
+
+// One CTA per vector: the partial sums of the spectral step, the log-determinant, y and the
+// gradient sweep added up (threads over the blocks, then over (entry, block group)).
+__global__ void __launch_bounds__(kFinNT) k_mll_final(FinalArgs a) {
+  __shared__ double sh[32];
+  __shared__ double gsh[kFinNT];
+  const uint32_t v = blockIdx.x, t = threadIdx.x;
   const uint32_t r = v / a.nrhs;
   const double n = (double)(1ull << a.m);
-  double quad = 0.0, gsum = 0.0, ld = 0.0;
-  for (uint32_t b = 0; b < a.bspec; ++b) {
+  double quad = 0.0, gsum = 0.0, ld = 0.0, sy = 0.0;
+  for (uint32_t b = t; b < a.bspec; b += kFinNT) {
     quad += a.spec_part[((uint64_t)v * a.bspec + b) * 2 + 0];
     gsum += a.spec_part[((uint64_t)v * a.bspec + b) * 2 + 1];
   }
-  for (uint32_t b = 0; b < a.blog; ++b) ld += a.log_part[(uint64_t)r * a.blog + b];
+  for (uint32_t b = t; b < a.blog; b += kFinNT) ld += a.log_part[(uint64_t)r * a.blog + b];
+  for (uint32_t b = t; b < a.by0; b += kFinNT) sy += a.y0[(uint64_t)v * a.by0 + b];
+  quad = block_sum(quad, sh);
+  gsum = block_sum(gsum, sh);
+  ld = block_sum(ld, sh);
+  sy = block_sum(sy, sh);
+  __shared__ double s_sumy;
+  if (t == 0) s_sumy = sy;
+  __syncthreads();
+  const double sumy = s_sumy;
   const double lam0 = a.lam[(uint64_t)r << a.m];
-  const double sumy = a.y0[v];
-  double *o = a.out + (uint64_t)v * QK_MLL_NOUT;
-  o[QK_MLL_QUAD] = quad;
-  o[QK_MLL_LOGDET] = ld;
-  o[QK_MLL_MLL] = -0.5 * quad - 0.5 * ld - 0.5 * n * 1.8378770664093454836;  // log(2 pi)
-  o[QK_MLL_MEAN] = a.zeta * sumy / lam0;
-  o[QK_MLL_VAR] = a.zeta * ((lam0 - a.zeta * n) / lam0);
-  if (a.grad) {
-    double *g = a.grad + (uint64_t)v * (2 * a.d + 2);
-    const double mfac = -a.zeta * sumy / (lam0 * lam0);
-    for (uint32_t j = 0; j < a.d; ++j) {
-      double su = 0.0, s1 = 0.0;
-      for (uint32_t b = 0; b < a.bgrad; ++b) {
-        su += a.grad_part[((uint64_t)v * a.bgrad + b) * 2 * a.d + j];
-        s1 += a.grad_part[((uint64_t)v * a.bgrad + b) * 2 * a.d + a.d + j];
-      }
-      g[j] = su;
-      g[a.d + 1 + j] = mfac * s1;
-    }
+  if (t == 0) {
+    double *o = a.out + (uint64_t)v * QK_MLL_NOUT;
+    o[QK_MLL_QUAD] = quad;
+    o[QK_MLL_LOGDET] = ld;
+    o[QK_MLL_MLL] = -0.5 * quad - 0.5 * ld - 0.5 * n * 1.8378770664093454836;  // log(2 pi)
+    o[QK_MLL_MEAN] = a.zeta * sumy / lam0;
+    o[QK_MLL_VAR] = a.zeta * ((lam0 - a.zeta * n) / lam0);
+  }
+  if (!a.grad) return;
+  double *g = a.grad + (uint64_t)v * (2 * a.d + 2);
+  const double mfac = -a.zeta * sumy / (lam0 * lam0);
+  if (t == 0) {
     g[a.d] = gsum;
     g[2 * a.d + 1] = mfac;
+  }
+  // entries q in [0, 2d): thread t takes entry q0 + t % nq over the blocks b = t / nq mod ng
+  const uint32_t nq2 = 2 * a.d;
+  const uint32_t nq = nq2 < (uint32_t)kFinNT ? nq2 : (uint32_t)kFinNT, ng = kFinNT / nq;
+  const double *gp = a.grad_part + (uint64_t)v * a.bgrad * nq2;
+  for (uint32_t q0 = 0; q0 < nq2; q0 += nq) {
+    const uint32_t q = q0 + t % nq, grp = t / nq;
+    double s = 0.0;
+    if (grp < ng && q < nq2)
+      for (uint32_t b = grp; b < a.bgrad; b += ng) s += gp[(uint64_t)b * nq2 + q];
+    gsh[t] = s;
+    __syncthreads();
+    if (t < nq && q < nq2) {
+      double tot = 0.0;
+      for (uint32_t k = 0; k < ng; ++k) tot += gsh[k * nq + t];
+      if (q < a.d) g[q] = tot;
+      else g[a.d + 1 + (q - a.d)] = mfac * tot;
+    }
+    __syncthreads();
   }
 }
 
@@ -468,7 +497,7 @@ size_t ws_mll(int family, uint32_t m, uint32_t nr, uint32_t nrhs, int dtype, uin
   if (family == QK_SI || dtype == QK_F32W) s = add_sat(s, sized(nv, m, dtype == QK_F64 ? 8 : 4));  // real u
   s = add_sat(s, align256(nv * spec_blocks(m) * 2 * sizeof(double)));
   s = add_sat(s, align256((uint64_t)nr * spec_blocks(m) * sizeof(double)));
-  s = add_sat(s, align256(nv * sizeof(double)));
+  s = add_sat(s, align256(nv * spec_blocks(m) * sizeof(double)));
   s = add_sat(s, align256(nv * grad_blocks(m) * 2 * (uint64_t)d * sizeof(double)));
   return s;
 }
@@ -809,13 +838,13 @@ static int mll_t(const ColJob &job, uint32_t nrhs, const double *lam, const T *y
   double *log_part = (double *)p;
   p += align256((uint64_t)job.nr * bs * sizeof(double));
   double *y0 = (double *)p;
-  p += align256((uint64_t)nvec * sizeof(double));
+  p += align256((uint64_t)nvec * bs * sizeof(double));
   double *grad_part = (double *)p;
 
   k_load_real<T, E><<<grid_for(cnt), 256, 0, st>>>(y, X, cnt);
   int rc = check_launch("mll load");
   if (rc) return rc;
-  k_sum_rows<T><<<nvec, 1024, 0, st>>>(y, (int)m, y0);
+  k_sum_rows<T><<<dim3(spec_blocks(m), nvec), 256, 0, st>>>(y, (int)m, y0);
   if ((rc = check_launch("mll sum y"))) return rc;
   if ((rc = fwd<E>(job.family, X, (int)m, nvec, st))) return rc;
   k_mll_spectral<E><<<dim3(bs, nvec), kRedNT, 0, st>>>(X, lam, (int)m, nrhs, spec_part, y0);
@@ -848,9 +877,10 @@ static int mll_t(const ColJob &job, uint32_t nrhs, const double *lam, const T *y
   fa.log_part = log_part;
   fa.grad_part = grad_part;
   fa.y0 = y0;
+  fa.by0 = bs;
   fa.out = out;
   fa.grad = grad;
-  k_mll_final<<<(nvec + 127) / 128, 128, 0, st>>>(fa);
+  k_mll_final<<<nvec, kFinNT, 0, st>>>(fa);
   return check_launch("mll final");
 }
 
@@ -869,7 +899,7 @@ static size_t ws_mll_si_t(uint32_t m, uint32_t nr, uint32_t nrhs, uint32_t d, bo
   if (with_c) s = add_sat(s, sized(np, m, sizeof(EO)));
   s = add_sat(s, align256(nv * spec_blocks(m) * 2 * sizeof(double)));
   s = add_sat(s, align256((uint64_t)nr * spec_blocks(m) * sizeof(double)));
-  s = add_sat(s, align256(nv * sizeof(double)));
+  s = add_sat(s, align256(nv * spec_blocks(m) * sizeof(double)));
   s = add_sat(s, align256(nv * grad_blocks(m) * 2 * (uint64_t)d * sizeof(double)));
   return s;
 }
@@ -906,13 +936,13 @@ static int mll_si_t(const ColJob &job, uint32_t nrhs, const double *lam, const T
   double *log_part = (double *)p;
   p += align256((uint64_t)job.nr * bs * sizeof(double));
   double *y0 = (double *)p;
-  p += align256(nvec * sizeof(double));
+  p += align256(nvec * bs * sizeof(double));
   double *grad_part = (double *)p;
 
   k_load_pairs<T, E><<<grid_for(np << m), 256, 0, st>>>(y, X, nvec, (int)m);
   int rc = check_launch("mll load");
   if (rc) return rc;
-  k_sum_rows<T><<<(unsigned)nvec, 1024, 0, st>>>(y, (int)m, y0);
+  k_sum_rows<T><<<dim3(spec_blocks(m), (unsigned)nvec), 256, 0, st>>>(y, (int)m, y0);
   if ((rc = check_launch("mll sum y"))) return rc;
   if ((rc = xform<E, XF_DIT>(X, (int)m, np, 1.0, st))) return rc;
   k_mll_spectral_pairs<E, EG, EO><<<dim3(bs, (unsigned)np), kRedNT, 0, st>>>(X, lam, nvec, (int)m, nrhs, spec_part,
@@ -947,9 +977,10 @@ static int mll_si_t(const ColJob &job, uint32_t nrhs, const double *lam, const T
   fa.log_part = log_part;
   fa.grad_part = grad_part;
   fa.y0 = y0;
+  fa.by0 = bs;
   fa.out = out;
   fa.grad = grad;
-  k_mll_final<<<(unsigned)((nvec + 127) / 128), 128, 0, st>>>(fa);
+  k_mll_final<<<(unsigned)nvec, kFinNT, 0, st>>>(fa);
   return check_launch("mll final");
 }
 
