@@ -313,6 +313,14 @@ def lattice_line(qk, torch, dev, stream, R=16):
     wl = inputs.workload("diff")
     out = {"workload": f"lattice n=2^{wl.ms[0]}, d={wl.d}, SI alpha={wl.alpha}, {R} shifts, nugget e^-12, 1 rhs",
            "points_per_step": R << wl.ms[0]}
+    m, d = wl.ms[0], wl.d
+    n = 1 << m
+    # algorithmic FP64 flops of the FP64 step: column sweep 10 per (point, dimension)
+    # (x - x^2, its square, the polynomial, the weight, p <- p + a + p a), gradient sweep 17
+    # (the column again, 1 + c K, the quotient, two accumulations), 5 N log2 N per complex
+    # transform of N (R/2 pairs each: eigenvalues, y forward; g and c inverse), 20 per
+    # (frequency, vector) in the spectral step
+    flops = R * n * d * (10 + 17) + 4 * (R // 2) * 5 * n * m + 20 * R * n
     for name, dt in (("fp64", torch.float64), ("f32w", qk.F32W)):
         ws, status, pts = lattice_setup(qk, torch, dev, R, dt)
         ms_ = time_steps(torch, lambda: qk.batch_run(ws, status), 3, 1, stream)
@@ -321,6 +329,12 @@ def lattice_line(qk, torch, dev, stream, R=16):
         per_op = {k: v[1] for k, v in qk.batch_kernel_ms(ws).items()}
         qk.batch_timing(ws, 0)
         out[name] = {"ms_per_step": ms_, "value": pts / (ms_ * 1e-3), "ops_ms": per_op}
+        if name == "fp64":
+            ach = flops / (ms_ * 1e-3) / 1e12
+            out[name]["roofline"] = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                     "frac": ach / FP64_PEAK_TFLOPS, "scope": "whole step, algorithmic FP64 flops",
+                                     "flops_per_step": flops,
+                                     "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)"}
         del ws
     return out
 

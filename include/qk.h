@@ -307,6 +307,12 @@ QK_API int qk_fwht_tune(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void 
 QK_API int qk_fwht_wait_selftest(uint32_t m, uint64_t nvec, int32_t dtype, void *x, void *ws, size_t ws_bytes,
                                  uint32_t spin_limit, uint32_t *status, qk_stream stream);
 
+/* Test of the FP64 quotient of the gradient sweeps (no counterpart in the paper): q[i] =
+ * a[i] / b[i] as those sweeps form it (two Newton steps on the FP32 reciprocal estimate,
+ * then a product; the divide for b outside 2^-100 .. 2^100 in magnitude); a, b, q: n device
+ * doubles.  Within 2 ulp of the correctly rounded quotient. */
+QK_API int qk_ratio_selftest(const double *a, const double *b, double *q, uint64_t n, qk_stream stream);
+
 /* --------------------------------------------------- higher-order nets --- */
 
 /* Digital interlacing of order alpha (Sec. 4.3, "Digital interlacing for higher-order

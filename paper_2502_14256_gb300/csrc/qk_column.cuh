@@ -476,7 +476,25 @@ __device__ __forceinline__ float rcp_approx(float a) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
   return r;
 }
-__device__ __forceinline__ double ratio(double a, double b) { return a / b; }
+// a / b in FP64 without the FP64 divide (GB300 has about two FP64 lanes per SM and cycle):
+// the reciprocal of b by two Newton-Raphson steps r <- r + r (1 - b r), each squaring the
+// relative error, from the FP32 reciprocal estimate of b (b's leading 24 bits, rel. error
+// below 2^-22); the second step's error is below one unit in the last place, then one
+// product: within 2 ulp of the rounded quotient (checked against the divide by
+// qk_ratio_selftest).  Five FP64 operations; b outside [2^-100, 2^100] in magnitude, zero,
+// subnormal, inf or NaN, takes the divide.
+__device__ __forceinline__ double ratio(double a, double b) {
+  const uint32_t hi = (uint32_t)__double2hiint(b), lo = (uint32_t)__double2loint(b);
+  const uint32_t ex = (hi >> 20) & 0x7FFu;
+  if (ex - 923u > 200u) return a / b;
+  const uint32_t fb = (hi & 0x80000000u) | ((ex - 896u) << 23) | ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+  double r = f2d_exact(rcp_approx(__uint_as_float(fb)));
+  double e = fma(-b, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-b, r, 1.0);
+  r = fma(r, e, r);
+  return a * r;
+}
 
 // Gradient sweep: for each dimension j, warp-reduced sums over this warp's points of
 // u_i dk1_i/dc_j and dk1_i/dc_j (float-float pairs in FP32 sweeps, doubles in FP64

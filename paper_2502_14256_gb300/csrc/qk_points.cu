@@ -385,6 +385,12 @@ __global__ void __launch_bounds__(kNT) k_grad_partials(ColJob job, uint32_t nrhs
 
 uint32_t grad_blocks(uint32_t m) { return ceil_div_u(1ull << m, kTile); }
 
+__global__ void k_ratio_selftest(const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ q,
+                                 uint64_t n) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    q[i] = ratio(a[i], b[i]);
+}
+
 template <typename T, int FAM, int ALPHA>
 static void launch_grad_t(const ColJob &job, uint32_t nrhs, const T *u, double *partial, int pairs,
                           cudaStream_t st) {
@@ -427,3 +433,16 @@ int launch_grad_partials(const ColJob &job, uint32_t nrhs, int32_t dtype, const 
 }
 
 }  // namespace qk
+
+using namespace qk;
+
+extern "C" int qk_ratio_selftest(const double *a, const double *b, double *q, uint64_t n, qk_stream stream) {
+  set_error("%s", "");
+  if (n == 0) return QK_OK;
+  if (!a || !b || !q) return fail(QK_EINVAL, "qk_ratio_selftest: NULL array");
+  uint64_t blocks = (n + 255) / 256;
+  const uint64_t cap = (uint64_t)sm_count() * 8;
+  if (blocks > cap) blocks = cap;
+  k_ratio_selftest<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(a, b, q, n);
+  return check_launch("qk_ratio_selftest");
+}

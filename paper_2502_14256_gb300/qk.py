@@ -41,7 +41,7 @@ EXPORTED = ["qk_lms_setup", "qk_gen_points", "qk_kernel_col", "qk_eigs", "qk_sol
             "qk_kernel_col_at", "qk_eigs_extend", "qk_fwht_extend", "qk_fftbr_extend", "qk_batch_tune",
             "qk_integrand", "qk_rqmc", "qk_student_t_quantile", "qk_discrepancy", "qk_discrepancy_weights",
             "qk_interlace", "qk_gen_points_ho", "qk_kernel_col_ho", "qk_mll_spectrum", "qk_mll_ho",
-            "qk_fftbr_ws"]
+            "qk_fftbr_ws", "qk_ratio_selftest"]
 QK_F_SIMPLE1, QK_F_SIMPLE2, QK_F_OAKLEY, QK_F_GFUN, QK_F_GENZ_OSC, QK_F_GENZ_CP = range(6)
 INTEGRANDS = {"simple1": QK_F_SIMPLE1, "simple2": QK_F_SIMPLE2, "oakley": QK_F_OAKLEY, "gfun": QK_F_GFUN,
               "genz_osc": QK_F_GENZ_OSC, "genz_cp": QK_F_GENZ_CP}
@@ -111,6 +111,7 @@ def _load():
         "qk_batch_kernel_ms": [P, u32, C.c_char_p, sz, C.POINTER(u32), C.POINTER(dbl)],
         "qk_fwht_ws": [u32, u64, i32, P, P, sz, C.POINTER(FwhtPlan), P, P],
         "qk_fftbr_ws": [u32, u64, i32, i32, P, P, sz, u32, P, P],
+        "qk_ratio_selftest": [P, P, P, u64, P],
         "qk_fwht_tune": [u32, u64, i32, P, P, sz, C.POINTER(FwhtPlan), P],
         "qk_fwht_wait_selftest": [u32, u64, i32, P, P, sz, u32, P, P],
         "qk_batch_run_host": [P, sz, C.POINTER(HostIO), u32, P, P],
@@ -390,6 +391,16 @@ def fftbr_ws(m: int, x, inverse=False, ws=None, lag=0, status=None, stream=None)
     _check(LIB.qk_fftbr_ws(m, nvec, dtype_code(x.dtype), 1 if inverse else 0, _ptr(x), _ptr(ws), ws.numel(),
                            lag, _ptr(status), _stream(stream)))
     return x
+
+
+def ratio_selftest(a, b, stream=None):
+    """q = a / b as the FP64 gradient sweeps form it (test support); a, b: FP64 device tensors."""
+    if a.dtype != torch.float64 or b.dtype != torch.float64 or a.shape != b.shape:
+        raise ValueError("ratio_selftest needs two FP64 tensors of one shape")
+    a, b = a.contiguous(), b.contiguous()
+    q = torch.empty_like(a)
+    _check(LIB.qk_ratio_selftest(_ptr(a), _ptr(b), _ptr(q), a.numel(), _stream(stream)))
+    return q
 
 
 def fwht_tune(m: int, x, ws=None, stream=None) -> dict:

@@ -198,3 +198,71 @@ def test_lattice_batch_task_combined_pass(qk, dtype):
                     assert abs(g_h[r, q, j] - g_r[r, q, j]) < bound, (j, g_h[r, q, j], g_r[r, q, j], bound)
             else:
                 assert np.all(np.isfinite(c_h[r, q])) and np.all(np.isfinite(g_h[r, q]))
+
+
+@pytest.mark.parametrize("m", [14, 18, 21])
+@pytest.mark.parametrize("dtype", ["f64", "f32w"])
+def test_lattice_batch_task_against_oracle_at_scale(qk, m, dtype):
+    """Lattice batch tasks (column, eigenvalues, one MLL + gradient + solve pass) against the
+    oracle's spectral formulas at n = 2^14, 2^18 and 2^21: eigenvalues element-wise, the
+    solve, quadratic form, log det, and the gradient (FP64: normwise; float-float column:
+    bounded by the FP32 sweep's rounding of its cancelling terms)."""
+    d, R, nrhs, eta = 4, 2, 1, 1e-4
+    gamma = 0.7 ** np.arange(1, d + 1)
+    case = qc.make_case("lattice", "si", 2, d, R, seed=5400 + m, c=gamma, zeta=0.9)
+    kern = qc.kernel_of(case)
+    n = 1 << m
+    td = F64 if dtype == "f64" else qk.F32W
+    ys, refs = [], []
+    for r in range(R):
+        k1, X = case.k1_ref(r, m)
+        lv = o.eigenvalues("si", k1, eta)
+        Y = _rhs(X, nrhs)
+        ys.append(Y)
+        refs.append((lv, X))
+    y = torch.tensor(np.stack(ys), dtype=qk.data_dtype(td), device=qc.dev())
+    c = torch.zeros_like(y)
+    lam = torch.zeros((R, n), dtype=F64, device=qc.dev())
+    out = torch.zeros((R, nrhs, 5), dtype=F64, device=qc.dev())
+    grad = torch.zeros((R, nrhs, 2 * d + 2), dtype=F64, device=qc.dev())
+    task = qk.Task(case.ps, kern, m, nrhs, eta, y.data_ptr(), c.data_ptr(), lam.data_ptr(), out.data_ptr(),
+                   grad.data_ptr())
+    ws = qk.workspace(qk.batch_workspace_bytes([task], td))
+    qk.batch_plan([task], td, 0, ws)
+    qk.batch_run(ws)
+    torch.cuda.synchronize()
+    lam_h, c_h, o_h, g_h = lam.cpu().numpy(), c.cpu().numpy().astype(np.float64), out.cpu().numpy(), grad.cpu().numpy()
+    y_h = y.to(F64).cpu().numpy()
+    for r in range(R):
+        lv, X = refs[r]
+        eps = qc.EPS64 if dtype == "f64" else 4 * qc.EPS64
+        assert qc.lam_elementwise_ok(lam_h[r], lv, 1e-10, eps, m), qc.lam_elementwise_report(lam_h[r], lv)
+        cond = float(np.max(lv) / np.min(lv))
+        for q in range(nrhs):
+            yq = y_h[r, q]
+            cw = o.spectral_solve("si", lv, yq)
+            sp = o.spectral_mll("si", lv, yq, case.zeta)
+            gr = o.spectral_mll_grad("si", 2, X, yq, lv, case.c, case.zeta)
+            tol = max(1e-10, 20 * cond * qc.EPS64) if dtype == "f64" else 1e-5
+            assert qc.rel_err(c_h[r, q], cw) < tol, (qc.rel_err(c_h[r, q], cw), tol)
+            qt = 1e-10 if dtype == "f64" else 1e-5
+            # y^T K^-1 y moves by 2 c^T dy for a transform rounding dy ~ m eps ||y||: relative
+            # 2 m eps ||c|| ||y|| / (y^T c), about m eps sqrt(cond) for these smooth y
+            qq = max(qt, 4 * m * qc.EPS64 * math.sqrt(cond)) if dtype == "f64" else qt
+            assert abs(o_h[r, q, 0] - sp["quad"]) < qq * abs(sp["quad"]), (o_h[r, q, 0], sp["quad"], qq)
+            assert abs(o_h[r, q, 1] - sp["logdet"]) < qt * max(1.0, abs(sp["logdet"]))
+            assert abs(o_h[r, q, 3] - sp["post_mean"]) < qt * max(1.0, abs(sp["post_mean"]))
+            assert abs(g_h[r, q, d] - gr["deta"]) < 1e-8 * max(1.0, abs(gr["deta"]))
+            if dtype == "f64":
+                assert qc.rel_err(g_h[r, q, :d], gr["dc"]) < 1e-9, qc.rel_err(g_h[r, q, :d], gr["dc"])
+            else:
+                yt = o.forward_transform("si", yq)
+                gw = 0.5 * (np.abs(yt) ** 2 / lv ** 2 - 1.0 / lv)
+                u = o.to_natural_order(np.fft.fft(gw).real, m)
+                fac = [o.factor_values("si", 2, o.pair_difference("si", X[:, j], X[0, j])) for j in range(d)]
+                for j in range(d):
+                    dk = np.full(n, case.zeta)
+                    for jj in range(d):
+                        dk *= fac[jj] if jj == j else 1.0 + case.c[jj] * fac[jj]
+                    bound = 1e-5 * abs(gr["dc"][j]) + 8 * math.sqrt(32) * qc.EPS32 * float(np.sum(np.abs(u * dk)))
+                    assert abs(g_h[r, q, j] - gr["dc"][j]) < bound, (j, g_h[r, q, j], gr["dc"][j], bound)

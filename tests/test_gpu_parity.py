@@ -806,3 +806,27 @@ def test_empty_inputs_are_no_ops(qk):
     torch.cuda.synchronize()
     qk.read_status(status)
     assert int(status.item()) == 0
+
+
+def test_fp64_quotient_of_the_gradient_sweeps(qk):
+    """The FP64 sweeps' a / b (Newton steps on the FP32 reciprocal estimate) against numpy's
+    correctly rounded division: within 2 ulp over a wide range of magnitudes and signs, and
+    exactly the divide outside 2^-100 .. 2^100 (where the sweeps take it)."""
+    rng = np.random.default_rng(17)
+    n = 1 << 20
+    b = rng.uniform(0.5, 1.0, n) * 2.0 ** rng.integers(-99, 99, n) * rng.choice([-1.0, 1.0], n)
+    a = rng.standard_normal(n) * 2.0 ** rng.integers(-300, 300, n)
+    # the sweeps' own argument range: 1 + c K near 1, and values close to powers of two
+    b[:4096] = 1.0 + rng.uniform(-0.999, 3.0, 4096)
+    b[4096:8192] = np.nextafter(2.0 ** rng.integers(-60, 60, 4096), 0.0)
+    b[8192:8200] = [2.0 ** 101, -2.0 ** -101, 1e300, 1e-300, 5e-324, 0.0, np.inf, -np.inf]
+    at = torch.tensor(a, dtype=F64, device=qc.dev())
+    bt = torch.tensor(b, dtype=F64, device=qc.dev())
+    q = qk.ratio_selftest(at, bt).cpu().numpy()
+    with np.errstate(divide="ignore", invalid="ignore"):
+        want = a / b
+    fast = (np.abs(b) >= 2.0 ** -100) & (np.abs(b) <= 2.0 ** 100)
+    ulp = np.spacing(np.abs(want[fast]))
+    assert np.all(np.abs(q[fast] - want[fast]) <= 2 * ulp), float(np.max(np.abs(q[fast] - want[fast]) / ulp))
+    slow = ~fast
+    assert np.array_equal(q[slow], want[slow], equal_nan=True)
