@@ -172,7 +172,7 @@ static int run_task(const Plan &p, const qk_task &t, unsigned char *ws, uint32_t
     if (use_fused(t, p.dtype, p.refine)) return run_fused(t, job, p.dtype, p.refine, ws, status, st, tm);
     int rc;
     if (use_lattice(t, p.dtype, p.refine)) {
-      const int eig_dtype = p.dtype == QK_F32 ? QK_F32 : QK_F64;
+      const int eig_dtype = p.dtype;  // QK_F32W: float-float transforms of the float-float column
       {
         OpScope s(tm, p.dtype == QK_F32W ? "op_kernel_col_ff" : "op_kernel_col", st);
         if ((rc = launch_kernel_col(job, p.dtype, QK_COL_P, col, st))) return rc;
@@ -183,7 +183,9 @@ static int run_task(const Plan &p, const qk_task &t, unsigned char *ws, uint32_t
           return rc;
       }
       OpScope s(tm, "op_mll_solve", st);
-      return op_mll_solve_si(job, t.nrhs, p.dtype, lam, t.y, t.out, t.grad, t.c, scr, st);
+      // the gradient sweep reads the stored column (FP64 for QK_F64 and QK_F32W)
+      const double *pcol = p.dtype == QK_F32 ? nullptr : reinterpret_cast<const double *>(col);
+      return op_mll_solve_si(job, t.nrhs, p.dtype, lam, t.y, t.out, t.grad, t.c, scr, st, pcol);
     }
     if (p.dtype == QK_F32W) {
       {

@@ -49,10 +49,11 @@ int launch_kernel_col(const ColJob &job, int32_t dtype, int32_t form, void *out,
 // Gradient partial sums.  u: (nr * nrhs, n) in dtype (vector v belongs to
 // randomization v / nrhs); with `pairs`, u is the pair layout of the lattice transforms
 // instead: vector v is the real (v even) or imaginary (v odd) part of complex vector v / 2.
-// partial: (nr * nrhs, blocks, 2d) doubles with blocks = grad_blocks(m):
-// [0, d) sum_i u_i dk1_i/dc_j, [d, 2d) sum_i dk1_i/dc_j.
+// pcol (nullable): the job's first column in p form, FP64 (nr, n), read instead of a
+// second column sweep.  partial: (nr * nrhs, blocks, 2d) doubles with
+// blocks = grad_blocks(m): [0, d) sum_i u_i dk1_i/dc_j, [d, 2d) sum_i dk1_i/dc_j.
 int launch_grad_partials(const ColJob &job, uint32_t nrhs, int32_t dtype, const void *u,
-                         double *partial, cudaStream_t st, bool pairs = false);
+                         double *partial, cudaStream_t st, bool pairs = false, const double *pcol = nullptr);
 uint32_t grad_blocks(uint32_t m);
 
 int launch_gen_points(const qk_pointset *ps, uint32_t r0, uint32_t nr, uint64_t i0, uint64_t n,
@@ -121,7 +122,7 @@ int op_transform_extend(int kind, uint32_t m, uint64_t nvec, int dtype, const vo
 // pairs of vectors; workspace ws_mll_si(..., c != null).
 size_t ws_mll_si(uint32_t m, uint32_t nr, uint32_t nrhs, int dtype, uint32_t d, bool with_c);
 int op_mll_solve_si(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const void *y, double *out,
-                    double *grad, void *c, void *ws, cudaStream_t st);
+                    double *grad, void *c, void *ws, cudaStream_t st, const double *pcol = nullptr);
 int op_mll(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const void *y, double *out, double *grad,
            void *ws, cudaStream_t st);
 }  // namespace qk

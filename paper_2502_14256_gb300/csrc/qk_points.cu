@@ -342,7 +342,8 @@ int launch_kernel_col(const ColJob &job, int32_t dtype, int32_t form, void *out,
 // zeta (1 + p_i) K_ij / f_ij (explicit product where f_ij == 0).
 template <typename T, int FAM, int ALPHA>
 __global__ void __launch_bounds__(kNT) k_grad_partials(ColJob job, uint32_t nrhs, const T *__restrict__ u,
-                                                       double *__restrict__ partial, int pairs) {
+                                                       double *__restrict__ partial, int pairs,
+                                                       const double *__restrict__ pcol) {
   extern __shared__ __align__(16) unsigned char smem[];
   double *wd;
   DiffTables tb;
@@ -369,7 +370,15 @@ __global__ void __launch_bounds__(kNT) k_grad_partials(ColJob job, uint32_t nrhs
     uu[l] = ok[l] ? u[ui] : T(0);
   }
   T p[kL];
-  column_sweep<T, FAM, ALPHA, kL>(job, tb, wT, bi, p);
+  if (pcol) {  // the first column as computed before (p form, FP64): no second column sweep
+#pragma unroll
+    for (int l = 0; l < kL; ++l) {
+      const uint64_t i = tile_base + threadIdx.x + ((uint64_t)l << 8);
+      p[l] = ok[l] ? (T)pcol[(size_t)rl * n + i] : T(0);
+    }
+  } else {
+    column_sweep<T, FAM, ALPHA, kL>(job, tb, wT, bi, p);
+  }
   const T zeta = (T)job.zeta;
   T wk[kL];
 #pragma unroll
@@ -393,28 +402,28 @@ __global__ void k_ratio_selftest(const double *__restrict__ a, const double *__r
 
 template <typename T, int FAM, int ALPHA>
 static void launch_grad_t(const ColJob &job, uint32_t nrhs, const T *u, double *partial, int pairs,
-                          cudaStream_t st) {
+                          const double *pcol, cudaStream_t st) {
   dim3 grid(grad_blocks(job.m), job.nr * nrhs);
   const size_t smem = col_smem_bytes<kL>(job.d) + (size_t)(kNT / 32) * 2 * job.d * sizeof(double);
   smem_optin<k_grad_partials<T, FAM, ALPHA>>(smem);
-  k_grad_partials<T, FAM, ALPHA><<<grid, kNT, smem, st>>>(job, nrhs, u, partial, pairs);
+  k_grad_partials<T, FAM, ALPHA><<<grid, kNT, smem, st>>>(job, nrhs, u, partial, pairs, pcol);
 }
 
 template <typename T>
 static int dispatch_grad(const ColJob &job, uint32_t nrhs, const T *u, double *partial, int pairs,
-                         cudaStream_t st) {
+                         const double *pcol, cudaStream_t st) {
   if (job.family == QK_DSI) {
     switch (job.alpha) {
-      case 1: launch_grad_t<T, 0, 1>(job, nrhs, u, partial, pairs, st); break;
-      case 2: launch_grad_t<T, 0, 2>(job, nrhs, u, partial, pairs, st); break;
-      case 3: launch_grad_t<T, 0, 3>(job, nrhs, u, partial, pairs, st); break;
-      case 4: launch_grad_t<T, 0, 4>(job, nrhs, u, partial, pairs, st); break;
+      case 1: launch_grad_t<T, 0, 1>(job, nrhs, u, partial, pairs, pcol, st); break;
+      case 2: launch_grad_t<T, 0, 2>(job, nrhs, u, partial, pairs, pcol, st); break;
+      case 3: launch_grad_t<T, 0, 3>(job, nrhs, u, partial, pairs, pcol, st); break;
+      case 4: launch_grad_t<T, 0, 4>(job, nrhs, u, partial, pairs, pcol, st); break;
       default: return fail(QK_EINVAL, "DSI order must be 1..4");
     }
   } else {
     switch (job.alpha) {
-      case 1: launch_grad_t<T, 1, 1>(job, nrhs, u, partial, pairs, st); break;
-      case 2: launch_grad_t<T, 1, 2>(job, nrhs, u, partial, pairs, st); break;
+      case 1: launch_grad_t<T, 1, 1>(job, nrhs, u, partial, pairs, pcol, st); break;
+      case 2: launch_grad_t<T, 1, 2>(job, nrhs, u, partial, pairs, pcol, st); break;
       default: return fail(QK_EINVAL, "SI smoothness must be 1 or 2");
     }
   }
@@ -422,14 +431,14 @@ static int dispatch_grad(const ColJob &job, uint32_t nrhs, const T *u, double *p
 }
 
 int launch_grad_partials(const ColJob &job, uint32_t nrhs, int32_t dtype, const void *u, double *partial,
-                         cudaStream_t st, bool pairs) {
+                         cudaStream_t st, bool pairs, const double *pcol) {
   if (job.nr == 0 || nrhs == 0) return QK_OK;
   if (job.kind == kHONet) {
-    if (pairs) return fail(QK_EINVAL, "gradient partials: pair layout is for lattices");
+    if (pairs || pcol) return fail(QK_EINVAL, "gradient partials: pair layout and stored column are for lattices");
     return launch_grad_partials_ho(job, nrhs, dtype, u, partial, st);
   }
-  return dtype == QK_F64 ? dispatch_grad<double>(job, nrhs, (const double *)u, partial, pairs ? 1 : 0, st)
-                         : dispatch_grad<float>(job, nrhs, (const float *)u, partial, pairs ? 1 : 0, st);
+  return dtype == QK_F64 ? dispatch_grad<double>(job, nrhs, (const double *)u, partial, pairs ? 1 : 0, pcol, st)
+                         : dispatch_grad<float>(job, nrhs, (const float *)u, partial, pairs ? 1 : 0, pcol, st);
 }
 
 }  // namespace qk

@@ -168,6 +168,16 @@ __device__ __forceinline__ E cplx(double re_, double im_) {
   z.y = (decltype(z.y))im_;
   return z;
 }
+template <>
+__device__ __forceinline__ FFC cplx<FFC>(double re_, double im_) {
+  return ffc_from(re_, im_);
+}
+__device__ __forceinline__ double cre(float2 z) { return (double)z.x; }
+__device__ __forceinline__ double cim(float2 z) { return (double)z.y; }
+__device__ __forceinline__ double cre(double2 z) { return z.x; }
+__device__ __forceinline__ double cim(double2 z) { return z.y; }
+__device__ __forceinline__ double cre(FFC z) { return ffc_re(z); }
+__device__ __forceinline__ double cim(FFC z) { return ffc_im(z); }
 
 // out[q] = in[2q] + i in[2q+1] (real vectors of T, n = 2^m each)
 template <typename T, typename E>
@@ -206,7 +216,7 @@ __global__ void k_lam_pairs(const E *__restrict__ X, double *__restrict__ lam, u
     for (int h = 0; h < 2; ++h) {
       const uint64_t v = 2 * q + h;
       if (v >= nvec) break;
-      double val = zmul * (double)(h ? z.y : z.x) + eta;
+      double val = zmul * (h ? cim(z) : cre(z)) + eta;
       if (w == 0) val += dc;
       if (eta > 0.0 && !(val >= eta)) {
         val = eta;
@@ -224,8 +234,9 @@ __global__ void k_lam_pairs(const E *__restrict__ X, double *__restrict__ lam, u
 // (A_kk = conj A_k, B_kk = conj B_k).
 template <typename E>
 __device__ __forceinline__ void split_pair(E zk, E zkk, double2 &a, double2 &b) {
-  a = make_double2(0.5 * ((double)zk.x + (double)zkk.x), 0.5 * ((double)zk.y - (double)zkk.y));
-  b = make_double2(0.5 * ((double)zk.y + (double)zkk.y), -0.5 * ((double)zk.x - (double)zkk.x));
+  const double kr = cre(zk), ki = cim(zk), kkr = cre(zkk), kki = cim(zkk);
+  a = make_double2(0.5 * (kr + kkr), 0.5 * (ki - kki));
+  b = make_double2(0.5 * (ki + kki), -0.5 * (kr - kkr));
 }
 // c + i d for complex c, d
 __device__ __forceinline__ double2 join_pair(double2 c, double2 d) { return make_double2(c.x - d.y, c.y + d.x); }
@@ -467,7 +478,8 @@ static size_t sized(uint64_t count_hi, uint32_t m, size_t bytes) {
 static size_t add_sat(size_t a, size_t b) { return a > SIZE_MAX - b ? SIZE_MAX : a + b; }
 
 size_t elem_bytes(int family, int dtype) {
-  const size_t s = dtype == QK_F64 ? 8 : 4;
+  // QK_F32W: FP64 columns (nets) and float-float complex transforms (lattices), 8 per part
+  const size_t s = (dtype == QK_F64 || dtype == QK_F32W) ? 8 : 4;
   return family == QK_SI ? 2 * s : s;
 }
 
@@ -660,9 +672,13 @@ static int eigs_si_t(uint32_t m, uint32_t batch, int form, const void *col, doub
 int op_eigs(int family, uint32_t m, uint32_t batch, int dtype, int form, const void *col, double zeta, double eta,
             double *lam, void *ws, uint32_t *status, cudaStream_t st) {
   if (batch == 0) return QK_OK;
-  if (family == QK_DSI)
+  if (family == QK_DSI) {
+    if (dtype == QK_F32W) dtype = QK_F64;  // FP64 column, FP64 transform
     return dtype == QK_F64 ? eigs_t<double, double>(family, m, batch, form, col, zeta, eta, lam, ws, status, st)
                            : eigs_t<float, float>(family, m, batch, form, col, zeta, eta, lam, ws, status, st);
+  }
+  // QK_F32W: the float-float column (stored FP64) through float-float transforms
+  if (dtype == QK_F32W) return eigs_si_t<double, FFC>(m, batch, form, col, zeta, eta, lam, ws, status, st);
   return dtype == QK_F64 ? eigs_si_t<double, double2>(m, batch, form, col, zeta, eta, lam, ws, status, st)
                          : eigs_si_t<float, float2>(m, batch, form, col, zeta, eta, lam, ws, status, st);
 }
@@ -906,13 +922,13 @@ static size_t ws_mll_si_t(uint32_t m, uint32_t nr, uint32_t nrhs, uint32_t d, bo
 
 size_t ws_mll_si(uint32_t m, uint32_t nr, uint32_t nrhs, int dtype, uint32_t d, bool with_c) {
   if (dtype == QK_F64) return ws_mll_si_t<double2, double2, double2>(m, nr, nrhs, d, with_c);
-  if (dtype == QK_F32W) return ws_mll_si_t<double2, float2, float2>(m, nr, nrhs, d, with_c);
+  if (dtype == QK_F32W) return ws_mll_si_t<FFC, float2, float2>(m, nr, nrhs, d, with_c);
   return ws_mll_si_t<float2, float2, float2>(m, nr, nrhs, d, with_c);
 }
 
 template <typename T, typename E, typename EG, typename EO>
 static int mll_si_t(const ColJob &job, uint32_t nrhs, const double *lam, const T *y, double *out, double *grad,
-                    T *c, void *ws, cudaStream_t st, bool fast_log) {
+                    T *c, void *ws, cudaStream_t st, bool fast_log, const double *pcol) {
   static_assert(sizeof(EO) == 2 * sizeof(T) && sizeof(EG) == 2 * sizeof(T), "inverse transforms in the data precision");
   const uint32_t m = job.m;
   const uint64_t nvec = (uint64_t)job.nr * nrhs, np = npairs_of(nvec);
@@ -956,7 +972,8 @@ static int mll_si_t(const ColJob &job, uint32_t nrhs, const double *lam, const T
   // G -> u_a + i u_b (real vectors of the gradient), C -> c_a + i c_b
   if (grad) {
     if ((rc = xform<EG, XF_DIF>(G, (int)m, np, 1.0, st))) return rc;
-    if ((rc = launch_grad_partials(job, nrhs, sizeof(T) == 8 ? QK_F64 : QK_F32, G, grad_part, st, true))) return rc;
+    if ((rc = launch_grad_partials(job, nrhs, sizeof(T) == 8 ? QK_F64 : QK_F32, G, grad_part, st, true, pcol)))
+      return rc;
   }
   if (c && (rc = xform<EO, XF_DIF>(C, (int)m, np, 1.0, st))) return rc;
   if (c) {
@@ -987,16 +1004,16 @@ static int mll_si_t(const ColJob &job, uint32_t nrhs, const double *lam, const T
 // MLL, gradient and solve of lattice tasks in one pass (dtype QK_F64, QK_F32W or QK_F32):
 // c may be null (no solve), grad may be null.
 int op_mll_solve_si(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const void *y, double *out,
-                    double *grad, void *c, void *ws, cudaStream_t st) {
+                    double *grad, void *c, void *ws, cudaStream_t st, const double *pcol) {
   if (job.family != QK_SI) return fail(QK_EINVAL, "op_mll_solve_si: lattice tasks only");
   if (dtype == QK_F64)
     return mll_si_t<double, double2, double2, double2>(job, nrhs, lam, (const double *)y, out, grad, (double *)c, ws,
-                                                       st, false);
+                                                       st, false, pcol);
   if (dtype == QK_F32W)
-    return mll_si_t<float, double2, float2, float2>(job, nrhs, lam, (const float *)y, out, grad, (float *)c, ws, st,
-                                                    true);
+    return mll_si_t<float, FFC, float2, float2>(job, nrhs, lam, (const float *)y, out, grad, (float *)c, ws, st,
+                                                true, pcol);
   return mll_si_t<float, float2, float2, float2>(job, nrhs, lam, (const float *)y, out, grad, (float *)c, ws, st,
-                                                 true);
+                                                 true, pcol);
 }
 
 int op_mll(const ColJob &job, uint32_t nrhs, int dtype, const double *lam, const void *y, double *out, double *grad,

@@ -51,6 +51,16 @@ template <> struct ScalarOf<double> { using type = double; };
 template <> struct ScalarOf<float2> { using type = float; };
 template <> struct ScalarOf<double2> { using type = double; };
 
+// A complex value in float-float arithmetic on the FP32 pipes: h = (Re_h, Im_h) and
+// l = (Re_l, Im_l) as packed f32x2 pairs, Re = Re_h + Re_l to about 2^-46 relative.  The
+// transforms of the float-float column path run in it: GB300's FP64 rate is a small
+// fraction of its FP32 rate, and a float-float butterfly costs a few dozen FP32 operations.
+struct __align__(16) FFC {
+  F2 h, l;
+};
+template <> struct ElemTraits<FFC> { static constexpr int LOGE = 11, CMIN = 3, PAD = 3; };
+template <> struct ScalarOf<FFC> { using type = double; };
+
 // ------------------------------------------------------------ element algebra
 __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -72,6 +82,51 @@ template <> __device__ __forceinline__ double zero_elem<double>() { return 0.0; 
 template <> __device__ __forceinline__ float2 zero_elem<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 zero_elem<double2>() { return make_double2(0.0, 0.0); }
 
+__device__ __forceinline__ FFC operator+(FFC a, FFC b) {
+  const FF<F2> r = ff_add(FF<F2>{a.h, a.l}, FF<F2>{b.h, b.l});
+  return {r.h, r.l};
+}
+__device__ __forceinline__ FFC operator-(FFC a, FFC b) { return a + FFC{vneg(b.h), vneg(b.l)}; }
+__device__ __forceinline__ F2 vswap(F2 a) {
+  float x, y;
+  vunpack(a, x, y);
+  return vpack(y, x);
+}
+// a w = (a.re, a.im) (w.re, w.re) + (a.im, a.re) (-w.im, w.im), each product a float-float
+// product of packed pairs
+__device__ __forceinline__ FFC cmul(FFC a, FFC w) {
+  float wrh, wih, wrl, wil;
+  vunpack(w.h, wrh, wih);
+  vunpack(w.l, wrl, wil);
+  const FF<F2> p1 = ff_mul(FF<F2>{a.h, a.l}, FF<F2>{vpack(wrh, wrh), vpack(wrl, wrl)});
+  const FF<F2> p2 = ff_mul(FF<F2>{vswap(a.h), vswap(a.l)}, FF<F2>{vpack(-wih, wih), vpack(-wil, wil)});
+  const FF<F2> r = ff_add(p1, p2);
+  return {r.h, r.l};
+}
+// the pair of two doubles (re, im): h = fl32(v), l = fl32(v - h)
+__device__ __forceinline__ FFC ffc_from(double re, double im) {
+  const float rh = __double2float_rn(re), ih = __double2float_rn(im);
+  return {vpack(rh, ih), vpack(__double2float_rn(re - (double)rh), __double2float_rn(im - (double)ih))};
+}
+__device__ __forceinline__ double ffc_re(FFC a) {
+  float h, i, l, j;
+  vunpack(a.h, h, i);
+  vunpack(a.l, l, j);
+  return f2d_exact(h) + f2d_exact(l);
+}
+__device__ __forceinline__ double ffc_im(FFC a) {
+  float h, i, l, j;
+  vunpack(a.h, h, i);
+  vunpack(a.l, l, j);
+  return f2d_exact(i) + f2d_exact(j);
+}
+__device__ __forceinline__ FFC scale_elem(FFC a, double s) {
+  const float2 sp = ff_split(s);
+  const FF<F2> r = ff_mul(FF<F2>{a.h, a.l}, FF<F2>{vsplat(sp.x), vsplat(sp.y)});
+  return {r.h, r.l};
+}
+template <> __device__ __forceinline__ FFC zero_elem<FFC>() { return {vsplat(0.f), vsplat(0.f)}; }
+
 // Twiddle e^{sign i pi j / 2^b} for 0 <= j < 2^b.
 __device__ __forceinline__ float2 twiddle(float2, uint64_t j, int b, float sign) {
   float sv, cv;
@@ -82,6 +137,11 @@ __device__ __forceinline__ double2 twiddle(double2, uint64_t j, int b, double si
   double sv, cv;
   sincospi(sign * (double)j * exp2neg(0.0, b), &sv, &cv);
   return make_double2(cv, sv);
+}
+__device__ __forceinline__ FFC twiddle(FFC, uint64_t j, int b, double sign) {
+  double sv, cv;
+  sincospi(sign * (double)j * exp2neg(0.0, b), &sv, &cv);
+  return ffc_from(cv, sv);
 }
 
 // e^{sign i pi k / 8} for k = 0..7: cos and sin of multiples of pi/8 (k is a compile-time
@@ -104,6 +164,13 @@ __device__ __forceinline__ E root8(int k, S sign) {
   w.x = (S)c;
   w.y = (S)(sign * s);
   return w;
+}
+
+template <>
+__device__ __forceinline__ FFC root8<FFC, double>(int k, double sign) {
+  const double2 w = root8<double2>(k, sign);
+  const float2 c = ff_split(w.x), s = ff_split(w.y);
+  return {vpack(c.x, s.x), vpack(c.y, s.y)};
 }
 
 template <typename E>
