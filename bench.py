@@ -315,12 +315,12 @@ def lattice_line(qk, torch, dev, stream, R=16):
            "points_per_step": R << wl.ms[0]}
     m, d = wl.ms[0], wl.d
     n = 1 << m
-    # algorithmic FP64 flops of the FP64 step: column sweep 10 per (point, dimension)
-    # (x - x^2, its square, the polynomial, the weight, p <- p + a + p a), gradient sweep 17
-    # (the column again, 1 + c K, the quotient, two accumulations), 5 N log2 N per complex
-    # transform of N (R/2 pairs each: eigenvalues, y forward; g and c inverse), 20 per
-    # (frequency, vector) in the spectral step
-    flops = R * n * d * (10 + 17) + 4 * (R // 2) * 5 * n * m + 20 * R * n
+    # algorithmic FP64 flops of the FP64 step: column sweep 9 per (point, dimension) (the
+    # factor x - x^2, its square and the polynomial, 5; the weight; p <- p + a + p a, 3),
+    # gradient sweep 12 (the factor, 5; 1 + c K; the quotient; two accumulations, 4), 5 N
+    # log2 N per complex transform of N (R/2 pairs each: eigenvalues, y forward; g and c
+    # inverse), 20 per (frequency, vector) in the spectral step
+    flops = R * n * d * (9 + 12) + 4 * (R // 2) * 5 * n * m + 20 * R * n
     for name, dt in (("fp64", torch.float64), ("f32w", qk.F32W)):
         ws, status, pts = lattice_setup(qk, torch, dev, R, dt)
         ms_ = time_steps(torch, lambda: qk.batch_run(ws, status), 3, 1, stream)
