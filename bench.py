@@ -44,9 +44,9 @@ UNIT = "points/s"
 # CUDA sources that capture ran (kernel_source_hash()).  A run whose sources differ reports
 # traffic null: the counters belong to another version of the kernels.
 NCU_TRAFFIC = {
-    "src_hash": "83a366f7a6c5",
-    "bytes_r64": {"k_fused_A": 1394955776, "k_fused_B": 1293584384, "k_fused_C": 1053322496},
-    "fwht_bytes": 592104448,
+    "src_hash": "5b6ca4f01927",
+    "bytes_r64": {"k_fused_A": 1394571008, "k_fused_B": 1293506560, "k_fused_C": 1053725952},
+    "fwht_bytes": 588819200,
 }
 # Nominal FP64 rate of GB300 (profiling recipe's table; FP64 is not a tensor-core path here).
 FP64_PEAK_TFLOPS = 1.25
