@@ -483,9 +483,9 @@ QK_API int qk_batch_schedule(void *ws, size_t ws_bytes, int32_t mode, uint32_t l
 QK_API int qk_batch_tune(void *ws, size_t ws_bytes, int32_t *mode, uint32_t *lag, float *ms, qk_stream stream);
 
 /* Run a planned schedule with HOST inputs and outputs (the planned device buffers are
- * the staging area): every task's randomizations go in chunks of at most chunk_r (ramps of
- * chunk_r/4, chunk_r/2, ... at both ends, so that computing starts after a short first copy
- * and the last copy back is short); chunk k's
+ * the staging area): every task's randomizations go in chunks of at most chunk_r (a half
+ * chunk at both ends, so that computing starts after a short first copy and the last copy
+ * back is short); chunk k's
  * right-hand sides are copied in on a library stream while chunk k-1 computes on
  * `stream`, and its results (c, lam, out, grad: those whose host pointer is non-NULL;
  * each needs its device buffer in the plan) are copied back on another library stream

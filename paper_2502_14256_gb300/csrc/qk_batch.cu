@@ -274,27 +274,26 @@ struct HostRunner {
 static std::mutex g_host_mu;
 static std::unordered_map<int, HostRunner> g_host_runners;
 
-// Chunk sizes (randomizations) for R randomizations with chunks of at most chunk_r: ramps of
-// chunk_r/4, chunk_r/2, ... at both ends (computing starts after a short first copy in, and
-// the last copy back is short), chunk_r in between; uniform chunks when R is too small.
+// Chunk sizes (randomizations) for R randomizations with chunks of at most chunk_r: a half
+// chunk at both ends (computing starts after a short first copy in, and the last copy back
+// is short), chunk_r in between; uniform chunks when R is too small.  A chunk's kernels fill
+// whole waves of resident CTAs only for some sizes, so the caller picks chunk_r (bench.py
+// times a few).
 static std::vector<uint32_t> host_chunks(uint32_t R, uint32_t chunk_r) {
-  std::vector<uint32_t> ramp;
-  for (uint32_t c = chunk_r >> 2; c && c < chunk_r; c <<= 1) ramp.push_back(c);
-  uint64_t ramps = 0;
-  for (uint32_t c : ramp) ramps += 2ull * c;
+  const uint32_t h = chunk_r / 2;
   std::vector<uint32_t> out;
-  if (ramp.empty() || R < ramps + chunk_r) {
+  if (h == 0 || R < chunk_r + 2 * h) {
     for (uint32_t r0 = 0; r0 < R; r0 += chunk_r) out.push_back(R - r0 < chunk_r ? R - r0 : chunk_r);
     return out;
   }
-  out = ramp;
-  uint32_t mid = R - (uint32_t)ramps;
+  out.push_back(h);
+  uint32_t mid = R - 2 * h;
   while (mid) {
     const uint32_t c = mid < chunk_r ? mid : chunk_r;
     out.push_back(c);
     mid -= c;
   }
-  for (auto it = ramp.rbegin(); it != ramp.rend(); ++it) out.push_back(*it);
+  out.push_back(h);
   return out;
 }
 

@@ -1046,10 +1046,11 @@ static int persist_fft_t(float2 *x, uint32_t m, uint64_t nvec, double scale, uin
   const uint32_t grid = (uint32_t)sm_count() * (uint32_t)occ;
   if (lag == 0) {
     // enough tickets between a vector's last first-pass tile and its first second-pass
-    // tile that the former has finished (lag T >= resident CTAs), three vectors of slack,
-    // at most 48 MB of first-pass output waiting in L2
-    uint64_t lg = (grid + T - 1) / T + 3;
-    const uint64_t cap = (48ull << 20) / (8ull << m);
+    // tile that the former has finished (lag T >= resident CTAs), one vector of slack, at
+    // most 24 MB of first-pass output waiting in L2 (measured, 64 x 2^20: lag 2-3 0.380 ms,
+    // 5 0.414 ms, 8 0.424 ms)
+    uint64_t lg = (grid + T - 1) / T + 1;
+    const uint64_t cap = (24ull << 20) / (8ull << m);
     if (lg > cap) lg = cap;
     lag = (uint32_t)(lg < 1 ? 1 : lg);
   }
