@@ -62,8 +62,18 @@ template <> struct ElemTraits<FFC> { static constexpr int LOGE = 11, CMIN = 3, P
 template <> struct ScalarOf<FFC> { using type = double; };
 
 // ------------------------------------------------------------ element algebra
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// FP32 complex addition as one packed f32x2 instruction (the same IEEE operation on both
+// halves: the same results as two scalar additions, in half the instructions)
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) {
+  float2 r;
+  vunpack(vadd(vpack(a.x, a.y), vpack(b.x, b.y)), r.x, r.y);
+  return r;
+}
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+  float2 r;
+  vunpack(vsub(vpack(a.x, a.y), vpack(b.x, b.y)), r.x, r.y);
+  return r;
+}
 __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 w) {
