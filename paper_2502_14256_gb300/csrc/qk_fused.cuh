@@ -546,8 +546,18 @@ __device__ __forceinline__ void xwht_col2(T (&vh)[FCfg<T>::L], T (&vl)[FCfg<T>::
   }
 }
 
-__device__ __forceinline__ float fused_log(float v) { return logf(v); }
+// log lambda for the log-determinant: FP32 tiles take the hardware log2 approximation
+// (absolute error ~2^-22 per term, about 1e-8 relative on a log det summed over 2^20
+// eigenvalues even if every term erred the same way; the sum itself is FP64), FP64 tiles
+// the full-precision log.  1 / lambda likewise: the FP32 tiles' reciprocal estimate plus one
+// Newton step (within 1 ulp); the solve's exact-residual correction below absorbs it.
+__device__ __forceinline__ float fused_log(float v) { return __logf(v); }
 __device__ __forceinline__ double fused_log(double v) { return log(v); }
+__device__ __forceinline__ float fused_rcp(float v) {
+  const float r = rcp_approx(v);
+  return fmaf(fmaf(-v, r, 1.f), r, r);
+}
+__device__ __forceinline__ double fused_rcp(double v) { return 1.0 / v; }
 
 // ------------------------------------------------------------------ phase A
 template <typename T, int FAM, int ALPHA, bool COMP, bool WIDE>
@@ -739,7 +749,7 @@ __device__ __forceinline__ void fused_B_item(const FTask &ft, uint32_t r, uint32
     for (int l = 0; l < L; ++l) {
       const int e = t + (l << kLOGNT);  // this thread's own entries only
       const T lw = lmv[e];
-      const T il = T(1) / lw;
+      const T il = fused_rcp(lw);
       const T sc = inv_n * il;          // 1 / (n lambda_w)
       T ch = y[l] * sc;                 // c^_w = Y_w / (n lambda_w)
       const T a = ch * y[l];            // Y_w^2 / (n lambda_w)
