@@ -592,18 +592,14 @@ __device__ __forceinline__ void fused_A_item(const FTask &ft, uint32_t r, uint32
   if constexpr (WIDE) column_sweep_ff<FAM, ALPHA, L>(job, tb, reinterpret_cast<const float2 *>(wd), bi, p, pl);
   else column_sweep<T, FAM, ALPHA, L>(job, tb, wT, bi, p);
   T *P = reinterpret_cast<T *>(ft.p) + (uint64_t)r * n + base;
-  T ps = T(0), pe = T(0);  // compensated thread partial: the sum cancels
-#pragma unroll
-  for (int l = 0; l < L; ++l) {
-    P[t + (l << kLOGNT)] = p[l];  // phase C's k_1 needs p to FP32 precision only
-    ff_add(ps, pe, p[l]);
-    if constexpr (WIDE) pe += pl[l];
-  }
-  const double sps = block_sum_c(ps, pe, red);
-  if (t == 0) ft.sp[(uint64_t)r * ft.tiles + tile] = sps;
   T *PT = reinterpret_cast<T *>(ft.pT) + (uint64_t)r * n + base;
   if constexpr (WIDE) {
+#pragma unroll
+    for (int l = 0; l < L; ++l) P[t + (l << kLOGNT)] = p[l];  // phase C's k_1 needs p to FP32 only
     xwht_full2<T>(p, pl, sm, sml, 0);  // L0 -> L2, compensated
+    // the tile sum of p is the transform's element 0 (thread 0, register 0 of layout L2),
+    // already a compensated pair: no separate sum
+    if (t == 0) ft.sp[(uint64_t)r * ft.tiles + tile] = f2d_exact(p[0]) + f2d_exact(pl[0]);
     T *PTL = reinterpret_cast<T *>(ft.pTL) + (uint64_t)r * n + base;
 #pragma unroll
     for (int l = 0; l < L; ++l) {
@@ -611,6 +607,14 @@ __device__ __forceinline__ void fused_A_item(const FTask &ft, uint32_t r, uint32
       PTL[e_of<T>(2, t, l)] = pl[l];
     }
   } else {
+    T ps = T(0), pe = T(0);  // compensated thread partial: the sum cancels
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      P[t + (l << kLOGNT)] = p[l];  // phase C's k_1 needs p to FP32 precision only
+      ff_add(ps, pe, p[l]);
+    }
+    const double sps = block_sum_c(ps, pe, red);
+    if (t == 0) ft.sp[(uint64_t)r * ft.tiles + tile] = sps;
     xwht_full<T>(p, sm, 0);  // L0 -> L2
 #pragma unroll
     for (int l = 0; l < L; ++l) PT[e_of<T>(2, t, l)] = p[l];
@@ -619,20 +623,23 @@ __device__ __forceinline__ void fused_A_item(const FTask &ft, uint32_t r, uint32
     const uint64_t v = (uint64_t)r * ft.nrhs + q;
     const T *Y = reinterpret_cast<const T *>(ft.y) + v * n + base;
     T yv[L];
-    T ys = T(0), ye = T(0);
 #pragma unroll
-    for (int l = 0; l < L; ++l) {
-      yv[l] = Y[t + (l << kLOGNT)];
-      ff_add(ys, ye, yv[l]);
+    for (int l = 0; l < L; ++l) yv[l] = Y[t + (l << kLOGNT)];
+    if constexpr (!COMP) {
+      T ys = T(0), ye = T(0);
+#pragma unroll
+      for (int l = 0; l < L; ++l) ff_add(ys, ye, yv[l]);
+      const double sys = block_sum_c(ys, ye, red);
+      if (t == 0) ft.sy[v * ft.tiles + tile] = sys;
     }
-    const double sys = block_sum_c(ys, ye, red);
-    if (t == 0) ft.sy[v * ft.tiles + tile] = sys;
     T *YT = reinterpret_cast<T *>(ft.yT) + v * n + base;
     if constexpr (COMP) {
       T yl[L];
 #pragma unroll
       for (int l = 0; l < L; ++l) yl[l] = T(0);
       xwht_full2<T>(yv, yl, sm, sml, 0);
+      // the tile sum of y: element 0 of the compensated transform (a float-float pair)
+      if (t == 0) ft.sy[v * ft.tiles + tile] = f2d_exact(yv[0]) + f2d_exact(yl[0]);
       T *YL = reinterpret_cast<T *>(ft.yL) + v * n + base;
 #pragma unroll
       for (int l = 0; l < L; ++l) {
