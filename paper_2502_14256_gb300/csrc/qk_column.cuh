@@ -306,6 +306,23 @@ __device__ __forceinline__ uint32_t diff_word(const DiffTables &tb, uint32_t d, 
   else return bi * tb.gs[j];
 }
 
+// Difference words of this thread's points l .. l + 3 in dimension j.  Nets read the four
+// table words with one 128-bit shared load: carve_tables places zl at a multiple of 16
+// bytes from the (16-byte aligned) shared base, and a row holds L words, L a multiple of 4.
+template <int FAM, int L>
+__device__ __forceinline__ void diff_words4(const DiffTables &tb, uint32_t base, const uint32_t (&bi)[L], int l,
+                                            uint32_t j, uint32_t (&z)[4]) {
+  static_assert(L % 4 == 0, "rows of whole quads");
+  if constexpr (FAM == 0) {
+    const uint4 q = *reinterpret_cast<const uint4 *>(tb.zl + j * L + l);
+    z[0] = base ^ q.x, z[1] = base ^ q.y, z[2] = base ^ q.z, z[3] = base ^ q.w;
+  } else {
+    const uint32_t gj = tb.gs[j];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) z[i] = bi[l + i] * gj;
+  }
+}
+
 // p[l] = prod_j (1 + c_j K_j(point l)) - 1 for the L points of this thread.
 template <typename T, int FAM, int ALPHA, int L>
 __device__ __forceinline__ void column_sweep(const ColJob &job, const DiffTables &tb, const T *wT,
@@ -318,15 +335,27 @@ __device__ __forceinline__ void column_sweep(const ColJob &job, const DiffTables
     const T wj = wT[j];
     uint32_t base = 0;
     if constexpr (FAM == 0) base = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * d + j];
-    if constexpr (sizeof(T) == 4 && L % 2 == 0) {
+    if constexpr (sizeof(T) == 4 && L % 4 == 0) {
       // two points per packed f32x2 multiply / add / fma: the same roundings as below
       const unsigned long long W = pack_f2(wj, wj);
 #pragma unroll
-      for (int l = 0; l < L; l += 2) {
-        const T k0 = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
-        const T k1 = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l + 1], l + 1, j));
-        const unsigned long long A = mul_f2(W, pack_f2(k0, k1)), P = pack_f2(p[l], p[l + 1]);
-        unpack_f2(fma_f2(P, A, add_f2(P, A)), p[l], p[l + 1]);
+      for (int l = 0; l < L; l += 4) {
+        uint32_t z[4];
+        diff_words4<FAM, L>(tb, base, bi, l, j, z);
+#pragma unroll
+        for (int i = 0; i < 4; i += 2) {
+          const T k0 = kfac<T, FAM, ALPHA>(tb, z[i]), k1 = kfac<T, FAM, ALPHA>(tb, z[i + 1]);
+          const unsigned long long A = mul_f2(W, pack_f2(k0, k1)), P = pack_f2(p[l + i], p[l + i + 1]);
+          unpack_f2(fma_f2(P, A, add_f2(P, A)), p[l + i], p[l + i + 1]);
+        }
+      }
+    } else if constexpr (L % 4 == 0) {
+#pragma unroll
+      for (int l = 0; l < L; l += 4) {
+        uint32_t z[4];
+        diff_words4<FAM, L>(tb, base, bi, l, j, z);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) p[l + i] = pm1_step(p[l + i], wj * kfac<T, FAM, ALPHA>(tb, z[i]));
       }
     } else {
 #pragma unroll
@@ -429,7 +458,7 @@ __device__ __forceinline__ void build_all_ff(const ColJob &job, const uint32_t *
 template <int FAM, int ALPHA, int L>
 __device__ __forceinline__ void column_sweep_ff(const ColJob &job, const DiffTables &tb, const float2 *wff,
                                                 const uint32_t (&bi)[L], float (&ph)[L], float (&pl)[L]) {
-  static_assert(L % 2 == 0, "pairs of points");
+  static_assert(L % 4 == 0, "quads of points");
   const uint32_t d = job.d;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   FF<F2> P[L / 2];
@@ -442,10 +471,11 @@ __device__ __forceinline__ void column_sweep_ff(const ColJob &job, const DiffTab
     uint32_t base = 0;
     if constexpr (FAM == 0) base = tb.zlane[j * 32 + lane] ^ tb.zwarp[warp * d + j];
 #pragma unroll
-    for (int h = 0; h < L / 2; ++h) {
-      const uint32_t z0 = diff_word<FAM, L>(tb, d, base, bi[2 * h], 2 * h, j);
-      const uint32_t z1 = diff_word<FAM, L>(tb, d, base, bi[2 * h + 1], 2 * h + 1, j);
-      P[h] = ff_pm1_step(P[h], ff_mul(W, kfac_ff2<FAM, ALPHA>(tb, z0, z1)), one);
+    for (int h = 0; h < L / 2; h += 2) {
+      uint32_t z[4];
+      diff_words4<FAM, L>(tb, base, bi, 2 * h, j, z);
+      P[h] = ff_pm1_step(P[h], ff_mul(W, kfac_ff2<FAM, ALPHA>(tb, z[0], z[1])), one);
+      P[h + 1] = ff_pm1_step(P[h + 1], ff_mul(W, kfac_ff2<FAM, ALPHA>(tb, z[2], z[3])), one);
     }
   }
 #pragma unroll
@@ -496,6 +526,44 @@ __device__ __forceinline__ double ratio(double a, double b) {
   return a * r;
 }
 
+// Warp sums of four per-lane values, the pair (a0, a1) of one dimension and (b0, b1) of
+// the next, by a reduce-scatter: at the xor-16 step a lane keeps one dimension's pair and
+// sends the other's, at the xor-8 step it keeps one value of that pair, and the last three
+// steps finish one sum per group of 8 lanes.  Lane 0 ends with the total of a0, lane 8 of
+// a1, lane 16 of b0 and lane 24 of b1 (every lane of a group of 8 holds its group's total).
+// Each sum is formed in the same order of additions as a full xor butterfly, so the FP64
+// totals equal those of one butterfly per value; FP32 totals are float-float pairs (s, e).
+// 5 shuffle steps for 4 values instead of 20.
+__device__ __forceinline__ void warp_sum4_ff(float a0, float a1, float b0, float b1, float &s, float &e) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  const float k0 = h16 ? b0 : a0, k1 = h16 ? b1 : a1;
+  const float r0 = __shfl_xor_sync(0xffffffffu, h16 ? a0 : b0, 16);
+  const float r1 = __shfl_xor_sync(0xffffffffu, h16 ? a1 : b1, 16);
+  float s0, e0, s1, e1;
+  two_sum(k0, r0, s0, e0);
+  two_sum(k1, r1, s1, e1);
+  s = h8 ? s1 : s0, e = h8 ? e1 : e0;
+  const float rs = __shfl_xor_sync(0xffffffffu, h8 ? s0 : s1, 8);
+  const float re = __shfl_xor_sync(0xffffffffu, h8 ? e0 : e1, 8);
+  ff_merge(s, e, rs, re);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), e2 = __shfl_xor_sync(0xffffffffu, e, o);
+    ff_merge(s, e, s2, e2);
+  }
+}
+__device__ __forceinline__ double warp_sum4(double a0, double a1, double b0, double b1) {
+  const int lane = threadIdx.x & 31;
+  const bool h16 = lane & 16, h8 = lane & 8;
+  const double s0 = (h16 ? b0 : a0) + __shfl_xor_sync(0xffffffffu, h16 ? a0 : b0, 16);
+  const double s1 = (h16 ? b1 : a1) + __shfl_xor_sync(0xffffffffu, h16 ? a1 : b1, 16);
+  double s = (h8 ? s1 : s0) + __shfl_xor_sync(0xffffffffu, h8 ? s0 : s1, 8);
+#pragma unroll
+  for (int o = 4; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
 // Gradient sweep: for each dimension j, warp-reduced sums over this warp's points of
 // u_i dk1_i/dc_j and dk1_i/dc_j (float-float pairs in FP32 sweeps, doubles in FP64
 // sweeps), written to red[warp][2d] and totalled by red_total, with
@@ -503,13 +571,15 @@ __device__ __forceinline__ double ratio(double a, double b) {
 // !ok[l]; uget(l) returns u_l and is called only for the rare exact zero of
 // 1 + c_j K_ij, handled after the loop by the explicit product over the other dimensions.
 // ALL_OK (unpacked sweeps): every point is valid, so no per-point validity select.
+// Dimensions are reduced in pairs (warp_sum4*): an even dimension's two lane sums wait in
+// registers for the next dimension's; an odd d leaves the last dimension to a butterfly.
 template <typename T, int FAM, int ALPHA, int L, bool ALL_OK = false, typename UF>
 __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTables &tb, const T *wT,
                                                const uint32_t (&bi)[L], const T (&k1)[L], const T (&wk)[L],
                                                const bool (&ok)[L], UF uget, double *red) {
   const uint32_t d = job.d;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr bool PACKED = sizeof(T) == 4 && L % 2 == 0;
+  constexpr bool PACKED = sizeof(T) == 4 && L % 4 == 0;
   // packed form: points (2h, 2h+1) share one f32x2 fma / mul, with the two halves summed
   // separately; a zero 1 + c_j K gives an infinite reciprocal, so the sums come out
   // non-finite and the exact fallback below runs instead of a per-point zero test.
@@ -523,6 +593,7 @@ __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTabl
       K1[h] = pack_f2(k1[2 * h], k1[2 * h + 1]);
     }
   }
+  T cu = T(0), c1 = T(0);  // lane sums of the even dimension of the current pair
   for (uint32_t j = 0; j < d; ++j) {
     const T wj = wT[j];
     T su = T(0), s1 = T(0);
@@ -533,15 +604,20 @@ __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTabl
       const unsigned long long W = pack_f2(wj, wj), ONE = pack_f2(1.f, 1.f);
       unsigned long long SU = pack_f2(0.f, 0.f), S1 = SU;
 #pragma unroll
-      for (int h = 0; h < L / 2; ++h) {
-        const T ka = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[2 * h], 2 * h, j));
-        const T kb = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[2 * h + 1], 2 * h + 1, j));
-        const unsigned long long KK = pack_f2(ka, kb);
-        float fa, fb;
-        unpack_f2(fma_f2(W, KK, ONE), fa, fb);
-        const unsigned long long Q = mul_f2(KK, pack_f2(rcp_approx(fa), rcp_approx(fb)));
-        SU = fma_f2(WK[h], Q, SU);
-        S1 = fma_f2(K1[h], Q, S1);
+      for (int l = 0; l < L; l += 4) {
+        uint32_t z[4];
+        diff_words4<FAM, L>(tb, base, bi, l, j, z);
+#pragma unroll
+        for (int i = 0; i < 4; i += 2) {
+          const int h = (l + i) >> 1;
+          const T ka = kfac<T, FAM, ALPHA>(tb, z[i]), kb = kfac<T, FAM, ALPHA>(tb, z[i + 1]);
+          const unsigned long long KK = pack_f2(ka, kb);
+          float fa, fb;
+          unpack_f2(fma_f2(W, KK, ONE), fa, fb);
+          const unsigned long long Q = mul_f2(KK, pack_f2(rcp_approx(fa), rcp_approx(fb)));
+          SU = fma_f2(WK[h], Q, SU);
+          S1 = fma_f2(K1[h], Q, S1);
+        }
       }
       float a, b;
       unpack_f2(SU, a, b);
@@ -550,15 +626,26 @@ __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTabl
       s1 = a + b;
       anyzero = !(isfinite(su) && isfinite(s1));
     } else {
-#pragma unroll
-      for (int l = 0; l < L; ++l) {
-        const T K = kfac<T, FAM, ALPHA>(tb, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
+      auto step = [&](int l, uint32_t z) {
+        const T K = kfac<T, FAM, ALPHA>(tb, z);
         const T f = fmadd(wj, K, T(1));
         anyzero |= f == T(0);
         T q = ratio(K, f);
         if constexpr (!ALL_OK) q = ok[l] ? q : T(0);
         su = fmadd(wk[l], q, su);
         s1 = fmadd(k1[l], q, s1);
+      };
+      if constexpr (L % 4 == 0) {
+#pragma unroll
+        for (int l = 0; l < L; l += 4) {
+          uint32_t z[4];
+          diff_words4<FAM, L>(tb, base, bi, l, j, z);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) step(l + i, z[i]);
+        }
+      } else {
+#pragma unroll
+        for (int l = 0; l < L; ++l) step(l, diff_word<FAM, L>(tb, d, base, bi[l], l, j));
       }
     }
     if (anyzero) {  // exact zeros of 1 + c_j K: use prod_{j' != j} (1 + c_j' K_j') directly
@@ -573,26 +660,42 @@ __device__ __forceinline__ void gradient_sweep(const ColJob &job, const DiffTabl
         s1 += dk;
       }
     }
+    if (!(j & 1) && j + 1 < d) {  // uniform over the warp: wait for the pair's odd dimension
+      cu = su, c1 = s1;
+      continue;
+    }
     if constexpr (sizeof(T) == 4) {
       // float-float warp sums, kept as (hi, lo) pairs: no FP64 arithmetic per dimension
-      float ue = 0.f, oe = 0.f;
-      warp_sum_ff(su, ue);
-      warp_sum_ff(s1, oe);
-      if (lane == 0) {
-        float2 *r2 = reinterpret_cast<float2 *>(red);
-        r2[(size_t)warp * 2 * d + j] = make_float2(su, ue);
-        r2[(size_t)warp * 2 * d + d + j] = make_float2(s1, oe);
+      float2 *r2 = reinterpret_cast<float2 *>(red) + (size_t)warp * 2 * d;
+      if (j & 1) {
+        float s, e;
+        warp_sum4_ff(cu, c1, su, s1, s, e);
+        if (!(lane & 7)) r2[((lane & 8) ? d : 0) + j - ((lane & 16) ? 0 : 1)] = make_float2(s, e);
+      } else {
+        float ue = 0.f, oe = 0.f;
+        warp_sum_ff(su, ue);
+        warp_sum_ff(s1, oe);
+        if (lane == 0) {
+          r2[j] = make_float2(su, ue);
+          r2[d + j] = make_float2(s1, oe);
+        }
       }
     } else {
-      double du = su, d1 = s1;
+      double *rw = red + (size_t)warp * 2 * d;
+      if (j & 1) {
+        const double s = warp_sum4(cu, c1, su, s1);
+        if (!(lane & 7)) rw[((lane & 8) ? d : 0) + j - ((lane & 16) ? 0 : 1)] = s;
+      } else {
+        double du = su, d1 = s1;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        du += __shfl_xor_sync(0xffffffffu, du, o);
-        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-      }
-      if (lane == 0) {
-        red[(size_t)warp * 2 * d + j] = du;
-        red[(size_t)warp * 2 * d + d + j] = d1;
+        for (int o = 16; o > 0; o >>= 1) {
+          du += __shfl_xor_sync(0xffffffffu, du, o);
+          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+        }
+        if (lane == 0) {
+          rw[j] = du;
+          rw[d + j] = d1;
+        }
       }
     }
   }
