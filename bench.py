@@ -44,9 +44,9 @@ UNIT = "points/s"
 # CUDA sources that capture ran (kernel_source_hash()).  A run whose sources differ reports
 # traffic null: the counters belong to another version of the kernels.
 NCU_TRAFFIC = {
-    "src_hash": "f6e672564b10",
-    "bytes_r64": {"k_fused_A": 1394922240, "k_fused_B": 1294307072, "k_fused_C": 1054025728},
-    "fwht_bytes": 591744000,
+    "src_hash": "e6a625a8d54c",
+    "bytes_r64": {"k_fused_A": 1283025408, "k_fused_B": 1294175744, "k_fused_C": 1053564672},
+    "fwht_bytes": 589224704,
 }
 # Nominal FP64 rate of GB300 (profiling recipe's table; FP64 is not a tensor-core path here).
 FP64_PEAK_TFLOPS = 1.25
