@@ -60,14 +60,33 @@ __global__ void k_store_real(const E *__restrict__ in, T *__restrict__ out, uint
   for (uint64_t i = gtid(); i < count; i += gstride()) out[i] = (T)(re(in[i]) * scale);
 }
 
-// lambda = zmul * Re(X) + [form P] zeta n delta_{w0} + eta, with the sign test.
+// Real transform values x > 0 (finite) tested without FP64 compares.
+__device__ __forceinline__ bool pos_finite(float x) { return x > 0.f && x <= 3.4028234663852886e38f; }
+__device__ __forceinline__ bool pos_finite(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 && b < 0x7FF0000000000000ll;
+}
+
+// lambda = zmul * Re(X) + [form P] zeta n delta_{w0} + eta, with the sign test.  Real
+// transforms take a short path for the usual entry (x > 0 away from w = 0, zmul > 0,
+// eta > 0): then lambda >= eta > 0 exactly, so neither test can fire, and lambda costs one
+// FP64 FMA on x widened by integer operations (GB300's FP64 conversion and compare run at
+// the rate of its FP64 adder).  The value is the same FMA as the general path's.
 template <typename E>
 __global__ void k_lam_final(const E *__restrict__ X, double *__restrict__ lam, uint64_t total, int m,
                             double zmul, double dc, double eta, uint32_t *status) {
   bool bad = false, floored = false;
   const uint64_t mask = (1ull << m) - 1;
+  const bool shortcut = zmul > 0.0 && eta > 0.0;
   for (uint64_t i = gtid(); i < total; i += gstride()) {
-    double v = zmul * re(X[i]) + eta;
+    if constexpr (std::is_same<E, float>::value || std::is_same<E, double>::value) {
+      const E x = X[i];
+      if (shortcut && (i & mask) != 0 && pos_finite(x)) {
+        lam[i] = fma(zmul, f2d_exact(x), eta);
+        continue;
+      }
+    }
+    double v = fma(zmul, re(X[i]), eta);
     if ((i & mask) == 0) v += dc;
     if (eta > 0.0 && !(v >= eta)) {  // K + eta I has no eigenvalue below eta: rounding
       v = eta;
