@@ -486,10 +486,13 @@ QK_API int qk_batch_tune(void *ws, size_t ws_bytes, int32_t *mode, uint32_t *lag
  * the staging area): every task's randomizations go in chunks of at most chunk_r (a half
  * chunk at both ends, so that computing starts after a short first copy and the last copy
  * back is short); chunk k's
- * right-hand sides are copied in on a library stream while chunk k-1 computes on
- * `stream`, and its results (c, lam, out, grad: those whose host pointer is non-NULL;
- * each needs its device buffer in the plan) are copied back on another library stream
- * while chunk k+1 computes.  io: one qk_host_io per planned task (host pointers, same
+ * right-hand sides are copied in on a library stream while chunk k-1 computes, and its
+ * results (c, lam, out, grad: those whose host pointer is non-NULL; each needs its device
+ * buffer in the plan) are copied back on another library stream while chunk k+1
+ * computes.  Chunks compute on `stream`, or, when every task runs fused and two chunks'
+ * scratch fits in the workspace in front of the persistent schedule's region, on two
+ * library streams in turn, each chunk with its own half of that scratch, so that two
+ * chunks' kernels overlap.  io: one qk_host_io per planned task (host pointers, same
  * layouts as the task's device buffers; page-locked memory lets the copies overlap).
  * Returns after enqueueing; `stream` completes after the last copy back.  Not for
  * stream capture.  (The paper has no counterpart: this is the runtime's host path.) */

@@ -252,14 +252,17 @@ static qk_task sub_task(const qk_task &t, uint32_t r0, uint32_t nr, size_t elem)
   return s;
 }
 
-// Streams and events of the host-buffer runner, created once per device.
+// Streams and events of the host-buffer runner, created once per device: copies in, copies
+// back, and two compute streams that alternating chunks run on.
 struct HostRunner {
-  cudaStream_t in = nullptr, out = nullptr;
+  cudaStream_t in = nullptr, out = nullptr, cmp[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> ev;
   int ensure(size_t nev) {
     if (!in) {
       cudaError_t e = cudaStreamCreateWithFlags(&in, cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&out, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cmp[0], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cmp[1], cudaStreamNonBlocking);
       if (e != cudaSuccess) return cuda_fail(e, "qk_batch_run_host: stream creation");
     }
     while (ev.size() < nev) {
@@ -449,6 +452,23 @@ int qk_batch_run_host(void *ws, size_t ws_bytes, const qk_host_io *io, uint32_t 
     chunks[i] = host_chunks(t.ps.R, chunk_r);
     nchunks += chunks[i].size();
   }
+  // Two chunks in flight: when every task runs fused and two chunks' scratch fits in front of
+  // the workspace's persistent-schedule region, consecutive chunks compute on two library
+  // streams, each with its own scratch slot, so that one chunk's kernels fill the SMs that
+  // the other's last wave leaves idle (a chunk's launches end in partial waves).  A slot is
+  // reused only by the chunk two on, on the same stream.
+  size_t slot = 0;
+  bool dual = true;
+  for (size_t i = 0; i < p.tasks.size() && dual; ++i) {
+    const qk_task &t = p.tasks[i];
+    if (!use_fused(t, p.dtype, p.refine)) dual = false;
+    for (const uint32_t nr : chunks[i]) {
+      const size_t b = align256(task_scratch(sub_task(t, 0, nr, elem), p.dtype, p.refine));
+      if (b > slot) slot = b;
+    }
+  }
+  const size_t avail = p.persist_bytes ? p.persist_off : p.total;
+  if (nchunks < 2 || 2 * slot > avail) dual = false;
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_host_mu);
@@ -456,11 +476,13 @@ int qk_batch_run_host(void *ws, size_t ws_bytes, const qk_host_io *io, uint32_t 
   int rc = hr.ensure(2 * nchunks + 1);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  // the copies must not start before earlier work on the caller's stream
+  // the copies and the compute streams must not start before earlier work on the caller's
+  // stream
   cudaEvent_t start = hr.ev[2 * nchunks];
   cudaError_t e = cudaEventRecord(start, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(hr.in, start, 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(hr.out, start, 0);
+  for (int c = 0; c < 2 && dual && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(hr.cmp[c], start, 0);
   if (e != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
   size_t k = 0;
   auto cp = [&](void *dst, const void *src, size_t bytes, cudaMemcpyKind kind, cudaStream_t s) -> int {
@@ -479,10 +501,13 @@ int qk_batch_run_host(void *ws, size_t ws_bytes, const qk_host_io *io, uint32_t 
       if ((rc = cp((void *)s.y, (const unsigned char *)io[i].y + yoff, ybytes, cudaMemcpyHostToDevice, hr.in)))
         return rc;
       if ((e = cudaEventRecord(hr.ev[2 * k], hr.in)) != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
-      // compute on the caller's stream once the chunk has landed
-      if ((e = cudaStreamWaitEvent(st, hr.ev[2 * k], 0)) != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
-      if ((rc = run_task(p, s, (unsigned char *)ws, status, st, nullptr))) return rc;
-      if ((e = cudaEventRecord(hr.ev[2 * k + 1], st)) != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
+      // compute once the chunk has landed: on the caller's stream, or on compute stream k mod 2
+      // with scratch slot k mod 2
+      cudaStream_t cs = dual ? hr.cmp[k & 1] : st;
+      unsigned char *wsk = (unsigned char *)ws + (dual ? (k & 1) * slot : 0);
+      if ((e = cudaStreamWaitEvent(cs, hr.ev[2 * k], 0)) != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
+      if ((rc = run_task(p, s, wsk, status, cs, nullptr))) return rc;
+      if ((e = cudaEventRecord(hr.ev[2 * k + 1], cs)) != cudaSuccess) return cuda_fail(e, "qk_batch_run_host");
       // device -> host: this chunk's results, overlapping the next chunk's compute
       if ((e = cudaStreamWaitEvent(hr.out, hr.ev[2 * k + 1], 0)) != cudaSuccess)
         return cuda_fail(e, "qk_batch_run_host");
