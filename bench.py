@@ -502,10 +502,10 @@ def main():
         # pick the chunk size (a chunk's kernels fill whole waves of resident CTAs only for
         # some sizes) by timing a few, before the timed region
         tried = {}
-        for cr in (2, 3, 4, 6, 8, 14, 16, 21, 32):
+        for cr in (3, 4, 6, 8, 14, 16, 21, 32):
             if cr <= R:
                 chunk["r"] = cr
-                tried[cr] = time_steps(torch, e2e_step, 2, 1, stream)
+                tried[cr] = time_steps(torch, e2e_step, 4, 1, stream)
         chunk["r"] = min(tried, key=tried.get)
     e2e_ms = time_steps(torch, e2e_step, max(2, args.steps // 2), 1, stream)
     e2e_ms = max_over_ranks(e2e_ms, torch, dist, world, dev)
