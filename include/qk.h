@@ -464,9 +464,11 @@ QK_API int qk_batch_run(void *ws, size_t ws_bytes, uint32_t *status, qk_stream s
  * randomization of every task is a unit whose tiles (column sweep, high-bit transform
  * and epilogue, inverse and gradient sweep, final reduction) are taken in ticket order,
  * a unit's next phase `lag` units (1 or 2; 0 = 1) after its previous one, with bounded
- * waits on per-unit completion counters (QK_STATUS_TIMEOUT if one ever runs out).  Needs
- * every task to be a DSI net of one order in the fused size range (2^13 < n <= 2^21 FP32,
- * 2^12 < n <= 2^20 FP64); QK_EINVAL otherwise.  Uploads the schedule tables into the
+ * waits on per-unit completion counters (QK_STATUS_TIMEOUT if one ever runs out).  The
+ * launch takes the plan's DSI nets in the fused size range (2^13 < n <= 2^21 FP32,
+ * 2^12 < n <= 2^20 FP64) of the order of the first such task; the other tasks (lattices,
+ * other sizes or orders) run after it as their launch sequence on the same stream.
+ * QK_EINVAL if no task qualifies.  Uploads the schedule tables into the
  * workspace synchronously: call it outside stream capture; runs are capturable.
  * Results equal the launch sequence's bit for bit.  qk_batch_run_host always uses the
  * launch sequence. */

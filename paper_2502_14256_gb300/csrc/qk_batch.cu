@@ -51,6 +51,8 @@ struct Plan {
   size_t scratch = 0;   // bytes of the shared scratch region
   size_t lam_off = 0;   // offset of the eigenvalue buffer
   size_t persist_off = 0, persist_bytes = 0;  // region of the persistent schedule (if eligible)
+  std::vector<qk_task> persist_tasks;   // the tasks the persistent launch takes (see persist_subset)
+  std::vector<uint8_t> in_persist;      // per task: 1 if it is one of them
   size_t total = 0;
   int32_t mode = QK_SCHED_LAUNCHES;
   PersistState persist;
@@ -110,6 +112,23 @@ static size_t task_scratch(const qk_task &t, int dtype, int refine) {
   return col + s;
 }
 
+// The tasks one persistent launch can take: fused DSI nets of the order of the plan's first
+// such task.  The others (lattices, sizes outside the fused range, other orders) run as
+// their launch sequence after it.
+static void persist_subset(Plan &p) {
+  p.persist_tasks.clear();
+  p.in_persist.assign(p.tasks.size(), 0);
+  int alpha = 0;
+  for (size_t i = 0; i < p.tasks.size(); ++i) {
+    const qk_task &t = p.tasks[i];
+    if (!fused_supported(t, p.dtype)) continue;
+    if (!alpha) alpha = t.k.alpha;
+    if (t.k.alpha != alpha) continue;
+    p.persist_tasks.push_back(t);
+    p.in_persist[i] = 1;
+  }
+}
+
 static int make_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, int32_t refine, Plan &p) {
   if (!tasks && ntasks) return fail(QK_EINVAL, "task list is NULL");
   if (dtype != QK_F64 && dtype != QK_F32 && dtype != QK_F32W)
@@ -137,9 +156,10 @@ static int make_plan(const qk_task *tasks, uint32_t ntasks, int32_t dtype, int32
   p.total = p.scratch + lam;
   p.persist_off = align256(p.total);
   p.persist_bytes = 0;
-  if (persist_eligible(p.tasks, dtype)) {
+  persist_subset(p);
+  if (persist_eligible(p.persist_tasks, dtype)) {
     for (uint32_t lag = 1; lag <= kMaxPersistLag; ++lag) {
-      const size_t b = persist_ws_bytes(p.tasks, dtype, refine, lag);
+      const size_t b = persist_ws_bytes(p.persist_tasks, dtype, refine, lag);
       if (b > p.persist_bytes) p.persist_bytes = b;
     }
     p.total = p.persist_off + p.persist_bytes;
@@ -229,9 +249,14 @@ static int run_task(const Plan &p, const qk_task &t, unsigned char *ws, uint32_t
 }
 
 static int run_plan(const Plan &p, unsigned char *ws, uint32_t *status, cudaStream_t st, LaunchTimer *tm) {
-  if (p.mode == QK_SCHED_PERSISTENT && p.persist.ok) return persist_run(p.persist, status, st, tm);
-  for (const qk_task &t : p.tasks) {
-    int rc = run_task(p, t, ws, status, st, tm);
+  const bool persistent = p.mode == QK_SCHED_PERSISTENT && p.persist.ok;
+  if (persistent) {
+    int rc = persist_run(p.persist, status, st, tm);
+    if (rc) return rc;
+  }
+  for (size_t i = 0; i < p.tasks.size(); ++i) {
+    if (persistent && p.in_persist[i]) continue;  // done by the persistent launch
+    int rc = run_task(p, p.tasks[i], ws, status, st, tm);
     if (rc) return rc;
   }
   return QK_OK;
@@ -363,9 +388,9 @@ int qk_batch_schedule(void *ws, size_t ws_bytes, int32_t mode, uint32_t lag) {
     return QK_OK;
   }
   if (!p.persist_bytes)
-    return fail(QK_EINVAL, "the persistent schedule needs every task to be a fused DSI net task of one order");
+    return fail(QK_EINVAL, "the persistent schedule needs at least one task that is a fused DSI net");
   PersistState st;
-  int rc = persist_setup(p.tasks, p.dtype, p.refine, lag ? lag : 1, (unsigned char *)ws + p.persist_off,
+  int rc = persist_setup(p.persist_tasks, p.dtype, p.refine, lag ? lag : 1, (unsigned char *)ws + p.persist_off,
                          p.persist_bytes, st);
   if (rc) return rc;
   p.persist = st;

@@ -247,3 +247,29 @@ def test_mixed_workload_full_size(qk):
             assert torch.isfinite(bw[key]).all(), (k, key)
         for a, v in errs.items():
             assert v < (loose if a in ("solve", "grad") else 1e-5), (k, inst.wl.kind, inst.m, d, a, v)
+
+
+@pytest.mark.parametrize("precision", ["float32w", "float32"])
+def test_persistent_schedule_takes_the_fused_nets_of_a_mixed_plan(qk, precision):
+    """A plan of mixed-workload instances: lattices, nets in and out of the fused size range
+    and one net of another DSI order.  The persistent schedule takes the fused nets of the
+    first net's order in one launch and runs the other tasks as their launch sequence after
+    it; captured in a CUDA graph, the results equal the launch sequence's bit for bit."""
+    import dataclasses
+    wls = [wl for wl in inputs.mixed_batch() if wl.ms[0] <= 16][:20]
+    odd = next(wl for wl in wls if wl.kind == "net" and wl.ms[0] >= 14)
+    wls.append(dataclasses.replace(odd, name=odd.name + "-order4", alpha=4))
+    insts = [W.build_instance(qk, wl, wl.ms[0], 1, 1, seed_shift=0, y_kind="product") for wl in wls]
+    fused_nets = [i for i in insts if i.wl.kind == "net" and i.m >= 14 and i.wl.alpha == 2]
+    assert fused_nets and any(i.wl.kind == "lattice" for i in insts) and any(
+        i.wl.kind == "net" and i.m < 14 for i in insts), "the plan must mix persistent and launched tasks"
+    dt = qk.F32W if precision == "float32w" else F32
+    runs = []
+    for persistent in (False, True):
+        tasks, bufs = zip(*[W.outputs(qk, inst, dt) for inst in insts])
+        W.run_tasks(qk, list(tasks), dt, refine=1, graph=True, allow_floor=True, persistent=persistent)
+        runs.append(bufs)
+    for k, (a, b) in enumerate(zip(*runs)):
+        for key in ("out", "c", "lam", "grad"):
+            assert torch.isfinite(a[key]).all(), (k, key)
+            assert torch.equal(a[key], b[key]), (k, insts[k].wl.kind, insts[k].m, insts[k].wl.alpha, key)
