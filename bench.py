@@ -24,6 +24,7 @@ import argparse
 import hashlib
 import json
 import math
+import re
 import os
 import statistics
 import subprocess
@@ -42,10 +43,9 @@ UNIT = "points/s"
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, bytes per launch) of the fused
 # kernels at 64 randomizations of n = 2^20, d = 16, from one ncu capture, and the hash of the
 # CUDA sources that capture ran (kernel_source_hash()).  A run whose sources differ reports
-# traffic null: the counters belong to another version of the kernels.  (The capture ran on
-# sources e6a625a8d54c, which differ from these only in a comment of include/qk.h.)
+# traffic null: the counters belong to another version of the kernels.
 NCU_TRAFFIC = {
-    "src_hash": "1aec1fa58638",
+    "src_hash": "98279e7026e4",
     "bytes_r64": {"k_fused_A": 1283025408, "k_fused_B": 1294175744, "k_fused_C": 1053564672},
     "fwht_bytes": 589224704,
 }
@@ -85,14 +85,21 @@ FUSED_SOURCES = ("qk_fused.cuh", "qk_fused.cu", "qk_fused_f32.cu", "qk_fused_f32
                  "qk_fused_f64.cu", "qk_column.cuh", "qk_common.cuh", "qk_factors.cuh", "qk_internal.h")
 
 
+def _code_only(text: bytes) -> bytes:
+    """C / C++ source without its comments and blank lines (a comment never changes a kernel)."""
+    t = re.sub(rb"/\*.*?\*/", b"", text, flags=re.S)
+    t = re.sub(rb"//[^\n]*", b"", t)
+    return b"\n".join(line.rstrip() for line in t.splitlines() if line.strip())
+
+
 def kernel_source_hash() -> str:
-    """Hash of the CUDA sources of the fused pipeline and the batched FWHT (which kernel version
-    a measurement belongs to)."""
+    """Hash of the CUDA sources of the fused pipeline and the batched FWHT, comments left out
+    (which kernel version a measurement belongs to)."""
     h = hashlib.sha256()
     for name in FUSED_SOURCES + ("../../include/qk.h",):
         f = os.path.join(ROOT, "paper_2502_14256_gb300", "csrc", name)
         with open(f, "rb") as fh:
-            h.update(os.path.basename(f).encode() + fh.read())
+            h.update(os.path.basename(f).encode() + _code_only(fh.read()))
     return h.hexdigest()[:12]
 
 
