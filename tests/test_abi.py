@@ -209,3 +209,36 @@ def test_workspace_sizes_saturate_instead_of_wrapping(lib_path):
                        C.c_size_t(0), None, None) == qk.QK_EWORKSPACE
     assert lib.qk_eigs(qk.QK_SI, 30, 1 << 30, qk.QK_F64, 0, fake, C.c_double(1.0), C.c_double(0.0), fake, fake,
                        C.c_size_t(1 << 40), None, None) == qk.QK_EWORKSPACE
+
+
+def test_persistent_schedule_takes_a_subset_of_the_plan(lib_path):
+    """Host side of QK_SCHED_PERSISTENT on mixed plans: the persistent launch takes the fused
+    DSI nets of one order, so a plan of a lattice and a net outside the fused size range has
+    none (QK_EINVAL, nothing launched) and reserves no persistent region, while adding one
+    fused net reserves it.  Plans are recorded on a fake workspace: nothing touches it."""
+    from paper_2502_14256_gb300 import qk
+    lib = qk.LIB
+    fake = C.c_void_p(0x2000000)
+    ws = C.c_void_p(0x40000000)  # 256-byte aligned, never dereferenced by plan or refusal
+
+    def net(m, alpha=2):
+        ps = qk.PointSet(qk.QK_NET_B2, qk.QK_GRAY, 2, 2, fake, None, fake)
+        return qk.Task(ps, qk.Kernel(qk.QK_DSI, alpha, 2, fake, 1.0), m, 1, 1e-8, fake, fake, None, fake, fake)
+
+    def lattice(m):
+        ps = qk.PointSet(qk.QK_LATTICE, qk.QK_NATURAL, 2, 2, None, fake, fake)
+        return qk.Task(ps, qk.Kernel(qk.QK_SI, 1, 2, fake, 1.0), m, 1, 1e-8, fake, fake, None, fake, fake)
+
+    def bytes_of(tasks):
+        arr = (qk.Task * len(tasks))(*tasks)
+        out = C.c_size_t(0)
+        assert lib.qk_batch_workspace_bytes(arr, len(tasks), qk.QK_F32, C.byref(out)) == qk.QK_OK
+        return arr, out.value
+
+    arr, nb = bytes_of([lattice(14), net(12)])
+    assert lib.qk_batch_plan(arr, 2, qk.QK_F32, 1, ws, C.c_size_t(nb), None) == qk.QK_OK
+    assert lib.qk_batch_schedule(ws, C.c_size_t(nb), qk.QK_SCHED_PERSISTENT, 1) == qk.QK_EINVAL
+    assert "fused DSI net" in qk.last_error()
+    assert lib.qk_batch_schedule(ws, C.c_size_t(nb), qk.QK_SCHED_LAUNCHES, 0) == qk.QK_OK
+    _, nb_fused = bytes_of([lattice(14), net(12), net(16)])
+    assert nb_fused > nb
