@@ -45,7 +45,7 @@ UNIT = "points/s"
 # CUDA sources that capture ran (kernel_source_hash()).  A run whose sources differ reports
 # traffic null: the counters belong to another version of the kernels.
 NCU_TRAFFIC = {
-    "src_hash": "98279e7026e4",
+    "src_hash": "a3fa2874c89e",
     "bytes_r64": {"k_fused_A": 1283025408, "k_fused_B": 1294175744, "k_fused_C": 1053564672},
     "fwht_bytes": 589224704,
 }
@@ -89,7 +89,7 @@ def _code_only(text: bytes) -> bytes:
     """C / C++ source without its comments and blank lines (a comment never changes a kernel)."""
     t = re.sub(rb"/\*.*?\*/", b"", text, flags=re.S)
     t = re.sub(rb"//[^\n]*", b"", t)
-    return b"\n".join(line.rstrip() for line in t.splitlines() if line.strip())
+    return b"\n".join(b" ".join(line.split()) for line in t.splitlines() if line.strip())
 
 
 def kernel_source_hash() -> str:

@@ -45,3 +45,13 @@ def test_replica_seeds_draw_different_randomizations():
     a = inputs.make_net(wl.seed + bench.replica_seed_offset(0), wl.d, 4, wl.order)
     b = inputs.make_net(wl.seed + bench.replica_seed_offset(1), wl.d, 4, wl.order)
     assert not np.array_equal(a.S, b.S) and not np.array_equal(a.D, b.D)
+
+
+def test_kernel_source_hash_ignores_comments():
+    """The bench ties its ncu traffic figures to a hash of the kernel sources; comments and
+    blank lines do not enter it, code does."""
+    a = b"__global__ void k(float *x) {  // one\n  /* two\n three */ x[0] = 1.f;\n\n}\n"
+    b = b"__global__ void k(float *x) {\n  x[0] = 1.f;  // other words\n}\n"
+    c = b"__global__ void k(float *x) {\n  x[0] = 2.f;\n}\n"
+    assert bench._code_only(a) == bench._code_only(b)
+    assert bench._code_only(a) != bench._code_only(c)
